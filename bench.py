@@ -1,0 +1,461 @@
+#!/usr/bin/env python
+"""Throughput of the differentiable packed-mesh rasterizer + soft blends on GB300.
+
+One step = the whole differentiable path over one batch, through the C ABI:
+  rast_mesh_fwd (stage, bin count/scan/fill, fine top-K) -> blend_fwd (softmax
+  rgb + silhouette alpha) -> blend_bwd (upstream grad N(0,1)) -> rast_mesh_bwd
+  (grad to the packed vertices).
+Workload: 8 displaced icospheres of 5,120 faces (level 4), random cameras,
+256x256, K = 8, blur_radius = ln(1/1e-4 - 1) 1e-4, sigma = gamma = 1e-4.
+
+Each C-ABI call is captured in its own CUDA graph; a step replays the four
+graphs with CUDA events between them, so every stage's device time is
+measured live on the launching stream inside the timed region.  L2 is
+flushed (256 MiB write) between steps, outside the events.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank renders its own
+copy of the batch (independent replicas, no collective on the data path);
+value = all ranks' slots / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd raster+blend ms/batch & Mpix·K/s, % HBM roofline, vs per-mesh plain form"
+UNIT = "Mpix*K/s"
+WORKLOAD = "8 icospheres level 4 (5,120 faces each, radial N(0,0.05)), random cameras, 256x256, K=8, " \
+           "blur=ln(1/1e-4-1)*1e-4, softmax rgb + silhouette (sigma=gamma=1e-4), fwd+bwd to verts"
+KERNELS_PER_STEP = {"rast_fwd": 4, "blend_fwd": 1, "blend_bwd": 1, "rast_bwd": 2}
+# DRAM bytes per launch of the dominant stage from one ncu capture of this
+# workload (profiles/ summary named in the design doc); None until captured for the
+# current kernel source.
+TRAFFIC_BYTES = {}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-plain", action="store_true", help="skip timing the plain per-mesh form")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id=None):
+        self.proc = None
+        self.path = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu_id is not None:
+                cmd += ["-i", str(self.gpu_id)]
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=reasons, samples=len(rows))
+        return out
+
+
+# ---------------------------------------------------------------------------
+# our path
+# ---------------------------------------------------------------------------
+class Pipeline:
+    """Static device buffers + one CUDA graph per C-ABI call."""
+
+    def __init__(self, w, bin_size, max_faces_per_bin, device):
+        import torch
+        from paper_2007_08501_gb300 import ops
+        self.torch, self.ops = torch, ops
+        b = w.batch
+        self.N, self.S, self.K = b.N, w.image_size, w.K
+        self.dev = device
+        T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        self.verts, self.faces = T(b.verts), T(b.faces)
+        self.ff, self.nf, self.cams = T(b.first_face), T(b.num_faces), T(b.cams)
+        self.colors = T(b.colors)
+        self.gimg = T(workloads_upstream(w))
+        self.p = ops.make_rast_params(b.N, w.image_size, w.K, np.float32(w.blur_radius), bin_size,
+                                      max_faces_per_bin, w.perspective_correct, w.clip_barycentric_coords)
+        self.bp = ops.make_blend_params(w.sigma, w.gamma, w.znear, w.zfar, (1.0, 1.0, 1.0), 1e-10,
+                                        ops.BLEND_RGB if w.blend_mode == "rgb" else ops.BLEND_SIL)
+        self.rgb = w.blend_mode == "rgb"
+        self.ws = ops.alloc_workspace(self.p, b.V, b.F, device)
+        self.frag = ops.alloc_fragments(b.N, w.image_size, w.K, device)
+        self.img = torch.empty((b.N, w.image_size, w.image_size, 4), device=device)
+        p2f, zb, ba, di = self.frag
+        self.gz, self.gb, self.gd = torch.empty_like(zb), torch.empty_like(ba), torch.empty_like(di)
+        self.gc = torch.empty_like(self.colors)
+        self.gv = torch.empty_like(self.verts)
+        self.graphs = None
+
+    def stages(self):
+        ops, p2f, zb, ba, di = (self.ops, *self.frag)
+        N, S, K = self.N, self.S, self.K
+        rgb = self.rgb
+        return [
+            ("rast_fwd", lambda: ops.rast_mesh_fwd(self.p, self.verts, self.faces, self.ff, self.nf, self.cams,
+                                                   p2f, zb, ba, di, self.ws)),
+            ("blend_fwd", lambda: ops.blend_fwd(self.bp, N, S, K, p2f, zb, ba, di, self.faces, self.colors,
+                                                self.img)),
+            ("blend_bwd", lambda: ops.blend_bwd(self.bp, N, S, K, p2f, zb, ba, di, self.faces, self.colors,
+                                                self.gimg, self.gz if rgb else None, self.gb if rgb else None,
+                                                self.gd, self.gc if rgb else None)),
+            ("rast_bwd", lambda: ops.rast_mesh_bwd(self.p, self.verts, self.faces, self.ff, self.nf, self.cams,
+                                                   p2f, self.gz if rgb else None, self.gb if rgb else None,
+                                                   self.gd, self.gv, self.ws)),
+        ]
+
+    def run_eager(self):
+        for _, fn in self.stages():
+            fn()
+
+    def capture(self):
+        torch = self.torch
+        s = torch.cuda.Stream(self.dev)
+        s.wait_stream(torch.cuda.current_stream(self.dev))
+        with torch.cuda.stream(s):
+            for _ in range(2):
+                self.run_eager()
+        torch.cuda.current_stream(self.dev).wait_stream(s)
+        torch.cuda.synchronize(self.dev)
+        self.graphs = []
+        for name, fn in self.stages():
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                fn()
+            self.graphs.append((name, g))
+        torch.cuda.synchronize(self.dev)
+
+    def status(self):
+        return self.ops.rast_query_status(self.ws)
+
+
+def workloads_upstream(w):
+    from paper_2007_08501_gb300 import workloads
+    return workloads.upstream_grad(w.batch.N, w.image_size, w.grad_seed)
+
+
+def timed_steps(pipe, steps, warmup, flush, use_graph=True):
+    """Returns per-step dict of stage -> ms, measured with CUDA events."""
+    torch = pipe.torch
+    names = [n for n, _ in pipe.stages()]
+    fns = [g.replay for _, g in pipe.graphs] if use_graph else [fn for _, fn in pipe.stages()]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(fns) + 1)] for _ in range(steps)]
+    for i in range(warmup):
+        flush.zero_()
+        for fn in fns:
+            fn()
+    torch.cuda.synchronize()
+    for i in range(steps):
+        flush.zero_()
+        e = evs[i]
+        e[0].record()
+        for j, fn in enumerate(fns):
+            fn()
+            e[j + 1].record()
+    torch.cuda.synchronize()
+    out = []
+    for e in evs:
+        out.append({names[j]: e[j].elapsed_time(e[j + 1]) for j in range(len(fns))})
+    return out
+
+
+def algorithmic_bytes(w):
+    """Bytes each stage must move per launch (fragments materialised as the C ABI requires)."""
+    b = w.batch
+    N, S, K = b.N, w.image_size, w.K
+    slots, pix, V, F = N * S * S * K, N * S * S, b.V, b.F
+    cams = 64 * N
+    mesh_in = 12 * V + 24 * F + cams + 16 * N
+    rgb_extra = 24 * F + 12 * V          # faces + colours gathered by the rgb blend
+    return {
+        "rast_fwd": mesh_in + 28 * slots,                                  # write fragments
+        "blend_fwd": 28 * slots + 16 * pix + rgb_extra,                    # read fragments, write rgba
+        "blend_bwd": 28 * slots + 16 * pix + 20 * slots + rgb_extra + 12 * V,
+        "rast_bwd": mesh_in + 28 * slots + 12 * V,                         # ids + grad fragments
+    }
+
+
+def cpu_baseline(w, target_s=15.0):
+    """The FP64 oracle, as it stands, on a bounded pixel sample of the same workload
+    (single-threaded: rasterize + blend fwd/bwd + rasterizer adjoint)."""
+    import oracle
+    from paper_2007_08501_gb300 import workloads
+    m = oracle.Mesh.from_batch(w.batch)
+    blur = float(np.float32(w.blur_radius))
+    S, K = w.image_size, w.K
+    g_full = workloads.upstream_grad(w.batch.N, S, w.grad_seed)
+
+    def run(per_image, seed):
+        px = workloads.sample_pixels(w.batch.N, S, per_image, seed)
+        t0 = time.perf_counter()
+        fr = oracle.rasterize(m, S, K, blur, True, w.clip_barycentric_coords, pixels=px)
+        g = g_full[px[:, 0], px[:, 1], px[:, 2]]
+        mode = 1 if w.blend_mode == "rgb" else 0
+        oracle.blend_fwd(*fr, w.batch.faces, w.batch.colors, w.sigma, w.gamma, w.znear, w.zfar, mode=mode)
+        gz, gb, gd, _ = oracle.blend_bwd(*fr, w.batch.faces, w.batch.colors, g, w.sigma, w.gamma, w.znear,
+                                         w.zfar, mode=mode)
+        oracle.rast_bwd(m, S, K, fr[0], gz, gb, gd, blur, True, w.clip_barycentric_coords, pixels=px)
+        return px.shape[0], time.perf_counter() - t0
+
+    n0, t0 = run(32, 11)
+    per_image = int(max(32, min(S * S, 32 * target_s / max(t0, 1e-3))))
+    n, t = run(per_image, 12)
+    return {"value": n * K / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d pixels (%d per image, seeded) of the same batch through the FP64 oracle "
+                      "(rasterize all faces per pixel + blend fwd/bwd + adjoint), %.1f s" % (n, per_image, t)}
+
+
+def run_ours(args):
+    import torch
+    from paper_2007_08501_gb300 import ops, workloads
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    ops.load()
+    w = workloads.workload(1)
+    b = w.batch
+    slots = b.N * w.image_size * w.image_size * w.K
+
+    pipe = Pipeline(w, bin_size=16, max_faces_per_bin=2048, device=dev)
+    pipe.run_eager()
+    torch.cuda.synchronize()
+    st = pipe.status()
+    if st != 0:
+        raise RuntimeError("device status %d after the first step" % st)
+    mc, tot = ops.rast_bin_occupancy(pipe.p, b.V, b.F, pipe.ws)
+    pipe.capture()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    gpu_index = None
+    try:
+        gpu_index = torch.cuda.get_device_properties(dev).uuid
+        gpu_index = "GPU-" + str(gpu_index) if not str(gpu_index).startswith("GPU-") else str(gpu_index)
+    except Exception:
+        gpu_index = None
+    clocks = ClockSampler(gpu_index)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    per_step = timed_steps(pipe, args.steps, args.warmup, flush, use_graph=True)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    wall = time.perf_counter() - t_wall
+    clk = clocks.stop()
+    step_ms = [sum(s.values()) for s in per_step]
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / args.steps
+    value = world * slots / (ms / 1e3) / 1e6
+    st = pipe.status()
+
+    stages = {k: statistics.mean(s[k] for s in per_step) for k in per_step[0]}
+    dom = max(stages, key=stages.get)
+    alg = algorithmic_bytes(w)
+    peak, peak_kind = _peaks()
+    achieved = alg[dom] / (stages[dom] / 1e3) / 1e9
+    traffic = TRAFFIC_BYTES.get(dom)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom,
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
+                else "fallback 6.8 TB/s"}
+    stage_frac = {k: round(alg[k] / (stages[k] / 1e3) / 1e9 / peak, 4) for k in stages}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    pin = lambda t: t.cpu().pin_memory()
+    h_in = [(pipe.verts, pin(pipe.verts)), (pipe.faces, pin(pipe.faces)), (pipe.ff, pin(pipe.ff)),
+            (pipe.nf, pin(pipe.nf)), (pipe.cams, pin(pipe.cams)), (pipe.colors, pin(pipe.colors)),
+            (pipe.gimg, pin(pipe.gimg))]
+    h_out = [(pipe.img, torch.empty_like(pipe.img, device="cpu").pin_memory()),
+             (pipe.gv, torch.empty_like(pipe.gv, device="cpu").pin_memory())]
+    h2d = sum(h.numel() * h.element_size() for _, h in h_in)
+    d2h = sum(h.numel() * h.element_size() for _, h in h_out)
+    e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for d, h in h_in:
+            d.copy_(h, non_blocking=True)
+        for _, g in pipe.graphs:
+            g.replay()
+        for d, h in h_out:
+            h.copy_(d, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        if i >= args.warmup:
+            e_ms.append(e0.elapsed_time(e1))
+    e2e_ms = statistics.mean(e_ms)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": round(world * slots / (e2e_ms / 1e3) / 1e6, 1), "unit": UNIT,
+           "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    plain = None
+    if not args.no_plain:
+        pp = Pipeline(w, bin_size=0, max_faces_per_bin=1, device=dev)
+        pp.capture()
+        ps = timed_steps(pp, max(3, args.steps // 2), 2, flush, use_graph=True)
+        pms = statistics.mean(sum(s.values()) for s in ps)
+        pstages = {k: round(statistics.mean(s[k] for s in ps), 4) for k in ps[0]}
+        plain = {"ms_per_step": round(pms, 4), "value": round(slots / (pms / 1e3) / 1e6, 1),
+                 "rast_fwd_ms": pstages["rast_fwd"], "launches_per_step": b.N + 1 + 1 + 1 + 2,
+                 "speedup_of_binned": round(pms / ms, 3)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(w)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": b.N, "image_size": w.image_size, "K": w.K, "faces": b.F,
+                       "verts": b.V, "slots": slots, "blur_radius": float(np.float32(w.blur_radius)),
+                       "bin_size": 16, "max_faces_per_bin": 2048, "graph": "one CUDA graph per C-ABI call",
+                       "l2": "flushed between steps (256 MiB write), outside the timed events",
+                       "bin_occupancy": {"max_faces_in_a_bin": mc, "total_entries": tot},
+                       "parallelism": "replicas x%d" % world},
+            "roofline": roofline,
+            "stages_ms": {k: round(v, 4) for k, v in stages.items()},
+            "stages_hbm_frac": stage_frac,
+            "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": sum(KERNELS_PER_STEP.values()) * args.steps,
+            "clocks": clk, "plain_form": plain, "status": st,
+            "wall_s_timed_region": round(wall, 3),
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """The FP64 CPU oracle, timed on host cores on a bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2007_08501_gb300 import workloads
+    oracle.build()
+    w = workloads.workload(1)
+    m = oracle.Mesh.from_batch(w.batch)
+    blur = float(np.float32(w.blur_radius))
+    S, K = w.image_size, w.K
+    g_full = workloads.upstream_grad(w.batch.N, S, w.grad_seed)
+    per_image = 256
+
+    def step(seed):
+        px = workloads.sample_pixels(w.batch.N, S, per_image, seed)
+        fr = oracle.rasterize(m, S, K, blur, True, w.clip_barycentric_coords, pixels=px)
+        g = g_full[px[:, 0], px[:, 1], px[:, 2]]
+        oracle.blend_fwd(*fr, w.batch.faces, w.batch.colors, w.sigma, w.gamma, w.znear, w.zfar)
+        gz, gb, gd, _ = oracle.blend_bwd(*fr, w.batch.faces, w.batch.colors, g, w.sigma, w.gamma, w.znear, w.zfar)
+        oracle.rast_bwd(m, S, K, fr[0], gz, gb, gd, blur, True, w.clip_barycentric_coords, pixels=px)
+        return px.shape[0]
+
+    for i in range(args.warmup):
+        step(100 + i)
+    t0 = time.perf_counter()
+    n = 0
+    for i in range(args.steps):
+        n += step(1000 + i)
+    t = time.perf_counter() - t0
+    value = n * K / t / 1e6
+    sample = "%d pixels per step (%d per image, seeded), FP64 oracle: rasterize + blend fwd/bwd + adjoint" % (
+        per_image * w.batch.N, per_image)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get(
+            "WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+
+
+if __name__ == "__main__":
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

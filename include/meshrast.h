@@ -1,0 +1,201 @@
+/*
+ * meshrast.h -- C ABI of the GB300 (sm_103a) packed-mesh rasterizer and its
+ * soft blends.
+ *
+ * The operations are those of Section 3.2 of "Accelerating 3D Deep Learning
+ * with PyTorch3D" (Ravi et al., 2020), "Differentiable mesh renderer":
+ *   - the rasterizer maps meshes from world to view coordinates with a
+ *     camera, finds for every pixel the K nearest faces along z (per-pixel
+ *     priority queues), works in two passes (image tiles first, then pixels),
+ *     and returns Fragment data: face id, barycentric coordinates, z distance
+ *     and signed xy distance ("Rasterizer");
+ *   - shaders blend the K fragments of a pixel: Algorithm 1 (silhouette) and
+ *     Algorithm 2 (softmax) ("Shaders");
+ *   - the backward pass reuses the cached Fragment data instead of
+ *     recomputing face-pixel intersections.
+ * Conventions the paper leaves open are fixed here and restated per call.
+ *
+ * General rules
+ *   - Every pointer argument is DEVICE memory of the current CUDA device,
+ *     contiguous, row-major, owned by the caller.  The library never
+ *     allocates, never synchronises inside a forward/backward call and never
+ *     runs anything on the host CPU: the calls only enqueue kernels (and
+ *     cudaMemsetAsync) on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream), so a sequence of them can be captured in a CUDA graph.
+ *   - Return value: 0 on success, a negative MESHRAST_ERR_* code for a
+ *     synchronous argument error (nothing was enqueued) or a launch failure.
+ *   - Asynchronous problems found by the kernels set bits (MESHRAST_ST_*) in
+ *     a status word inside the workspace; outputs are then undefined.  Read
+ *     it with rast_query_status() after the stream (or graph) has run.
+ *   - Sizes are int64_t; face indices and pix_to_face are int64_t; all
+ *     floating point data is float32.
+ *
+ * Packed mesh batch (Section 3, "3D data structures": list/packed/padded)
+ *   verts      (V, 3)  world positions
+ *   faces      (F, 3)  vertex indices into verts; any face may use any vertex
+ *                      (several images may share vertices)
+ *   first_face (N,)    image n rasterizes faces [first_face[n], first_face[n] + num_faces[n]);
+ *   num_faces  (N,)    first_face must be non-decreasing and the ranges disjoint
+ *   cams       (N, 16) per image: R (3x3 row-major, world->view), C (camera
+ *                      centre), f = 1/tan(fov/2), znear, 0, 0.
+ *                      p_view = R (p_world - C); NDC x = f x/z, y = f y/z;
+ *                      the depth is the view z.  View +X is image-left,
+ *                      +Y image-up, +Z into the screen.
+ * Image: S x S pixels; pixel (row r, col c) has its centre at NDC
+ *   (1 - (2c+1)/S, 1 - (2r+1)/S); row 0 is the top row.
+ * Fragments, shape (N, S, S, K[, 3]), slot-major within a pixel:
+ *   pix_to_face  global packed face id of the k-th nearest face, or -1
+ *   zbuf         view depth at the pixel (-1 when empty)
+ *   bary         barycentrics (b0, b1, b2) after optional perspective
+ *                correction then optional clipping (-1 when empty)
+ *   dists        signed squared NDC distance from the pixel centre to the
+ *                face's nearest edge segment: negative inside (-1 when empty)
+ *   A face is a candidate for a pixel when the pixel lies in it (closed), or
+ *   blur_radius > 0 and the squared distance is < blur_radius; and its depth
+ *   there is finite and >= znear.  The K candidates with the smallest
+ *   (depth, face id) are kept in that order.  Faces with a corner nearer than
+ *   znear, or with |NDC double area| < 1e-12, are culled.  Both windings are
+ *   rasterized.
+ */
+#ifndef MESHRAST_H
+#define MESHRAST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MESHRAST_API __attribute__((visibility("default")))
+#else
+#define MESHRAST_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define MESHRAST_OK                 0
+#define MESHRAST_ERR_INVALID_ARG   (-1)   /* bad size, NULL pointer, bad flag */
+#define MESHRAST_ERR_WORKSPACE     (-2)   /* workspace too small or not 256-byte aligned */
+#define MESHRAST_ERR_UNSUPPORTED   (-3)   /* e.g. K > 64, bin_size not in {0, 8, 16} */
+#define MESHRAST_ERR_CUDA          (-4)   /* a kernel launch or memset failed */
+
+/* ---- status bits (asynchronous, in the workspace) -------------------- */
+#define MESHRAST_ST_BIN_OVERFLOW    1u    /* a bin held more than max_faces_per_bin faces,
+                                             or all bins together more than max_bin_entries */
+#define MESHRAST_ST_BAD_INDEX       2u    /* a face used a vertex index outside [0, V) */
+#define MESHRAST_ST_BAD_MESH_RANGE  4u    /* first_face / num_faces outside [0, F] or not packed */
+#define MESHRAST_ST_NONFINITE       8u    /* a face had a non-finite corner (face culled) */
+
+/* Rasterizer parameters (Section 3.2 "Rasterizer"). */
+typedef struct {
+    int32_t N;                    /* images (= meshes) in the batch, >= 0 */
+    int32_t image_size;           /* S, 1 .. 8192 */
+    int32_t faces_per_pixel;      /* K, 1 .. 64 */
+    int32_t bin_size;             /* 0: plain form, one unbinned launch per image;
+                                     8 or 16: coarse-to-fine with bins of bin_size^2 pixels */
+    int32_t max_faces_per_bin;    /* binned mode: capacity of one bin (> 0) */
+    int32_t perspective_correct;  /* 0/1: barycentrics of the 3D point on the face */
+    int32_t clip_barycentric_coords; /* 0/1: clamp at 0 and renormalise (after perspective) */
+    int32_t reserved;             /* must be 0 */
+    float   blur_radius;          /* >= 0, squared NDC units (same units as dists) */
+    float   reserved_f;           /* must be 0 */
+    int64_t max_bin_entries;      /* binned mode: capacity of all bin lists together;
+                                     0 means N * nb * nb * max_faces_per_bin, nb = ceil(S / bin_size) */
+} rast_params;
+
+/* Blend parameters (Algorithms 1 and 2; zfar, znear, sigma, gamma are the
+ * user hyper-parameters the paper names). */
+#define MESHRAST_BLEND_SIL 0      /* alpha only (Algorithm 1); rgb written as 0 */
+#define MESHRAST_BLEND_RGB 1      /* softmax rgb (Algorithm 2) + silhouette alpha */
+typedef struct {
+    float sigma;                  /* > 0 */
+    float gamma;                  /* > 0 */
+    float znear, zfar;            /* zfar > znear */
+    float bg[3];                  /* background colour of the softmax blend */
+    float eps;                    /* background depth term, e.g. 1e-10 */
+    int32_t mode;                 /* MESHRAST_BLEND_SIL or MESHRAST_BLEND_RGB */
+    int32_t reserved;             /* must be 0 */
+} blend_params;
+
+/* Bytes of device workspace that rast_mesh_fwd / rast_mesh_bwd need for
+ * these parameters and sizes (a multiple of 256).  Returns 0 for invalid
+ * parameters.  The workspace must be 256-byte aligned. */
+MESHRAST_API size_t rast_workspace_bytes(const rast_params *p, int64_t V, int64_t F);
+
+/* Forward rasterization (Section 3.2 "Rasterizer": camera transform, coarse
+ * binning into image tiles, per-pixel K nearest faces, Fragment data).
+ * Outputs (all overwritten, every slot written):
+ *   pix_to_face (N,S,S,K) int64, zbuf (N,S,S,K), bary (N,S,S,K,3), dists (N,S,S,K).
+ * Clears the workspace status word, then ORs MESHRAST_ST_* bits into it. */
+MESHRAST_API int rast_mesh_fwd(const rast_params *p,
+                  const float *verts, int64_t V,
+                  const int64_t *faces, int64_t F,
+                  const int64_t *first_face, const int64_t *num_faces,
+                  const float *cams,
+                  int64_t *pix_to_face, float *zbuf, float *bary, float *dists,
+                  void *workspace, size_t workspace_bytes, void *stream);
+
+/* Backward rasterization: dL/dverts from dL/d(zbuf, bary, dists), holding
+ * the face selection pix_to_face fixed.  Barycentrics, depth and distance of
+ * every non-empty slot are recomputed from pix_to_face and the geometry (the
+ * forward's bary/zbuf/dists are not needed).  grad_zbuf, grad_bary and
+ * grad_dists may each be NULL (taken as zero).  grad_verts (V, 3) is
+ * overwritten.  Gradients reach only the vertices (not the cameras).
+ * Leaves the status word as it is and ORs new bits into it. */
+MESHRAST_API int rast_mesh_bwd(const rast_params *p,
+                  const float *verts, int64_t V,
+                  const int64_t *faces, int64_t F,
+                  const int64_t *first_face, const int64_t *num_faces,
+                  const float *cams,
+                  const int64_t *pix_to_face,
+                  const float *grad_zbuf, const float *grad_bary, const float *grad_dists,
+                  float *grad_verts,
+                  void *workspace, size_t workspace_bytes, void *stream);
+
+/* Blend forward (Algorithm 1; Algorithm 2 when mode == MESHRAST_BLEND_RGB).
+ *   prob_k = sigmoid(-dists_k / sigma) over slots with pix_to_face >= 0;
+ *   alpha  = 1 - prod_k (1 - prob_k);
+ *   zinv_k = (zfar - zbuf_k)/(zfar - znear); m = max(eps, max_k zinv_k);
+ *   w_k = prob_k exp((zinv_k - m)/gamma); delta = exp((eps - m)/gamma);
+ *   rgb = (sum_k w_k c_k + delta bg)/(sum_k w_k + delta), where c_k is the
+ *   per-vertex colour of face pix_to_face_k interpolated with bary_k.
+ * image (N,S,S,4) = (r, g, b, alpha), overwritten.
+ * In MESHRAST_BLEND_SIL mode zbuf, bary, faces and vert_colors may be NULL. */
+MESHRAST_API int blend_fwd(const blend_params *bp, int64_t N, int64_t S, int64_t K,
+              const int64_t *pix_to_face, const float *zbuf, const float *bary,
+              const float *dists,
+              const int64_t *faces, int64_t F, const float *vert_colors, int64_t V,
+              float *image, void *stream);
+
+/* Blend backward: adjoint of blend_fwd for upstream grad_image (N,S,S,4).
+ * grad_dists (N,S,S,K) is overwritten.  In MESHRAST_BLEND_RGB mode
+ * grad_zbuf (N,S,S,K), grad_bary (N,S,S,K,3) and grad_vert_colors (V,3) are
+ * overwritten; in MESHRAST_BLEND_SIL mode they may be NULL (and are not
+ * touched when given). */
+MESHRAST_API int blend_bwd(const blend_params *bp, int64_t N, int64_t S, int64_t K,
+              const int64_t *pix_to_face, const float *zbuf, const float *bary,
+              const float *dists,
+              const int64_t *faces, int64_t F, const float *vert_colors, int64_t V,
+              const float *grad_image,
+              float *grad_zbuf, float *grad_bary, float *grad_dists, float *grad_vert_colors,
+              void *stream);
+
+/* Waits for `stream`, then copies the workspace status word to *status
+ * (host memory).  Returns MESHRAST_ERR_CUDA if the stream failed. */
+MESHRAST_API int rast_query_status(const void *workspace, uint32_t *status, void *stream);
+
+/* Waits for `stream`, then reports the bin occupancy of the last binned
+ * forward that ran on this workspace: the largest per-bin face count and the
+ * sum of all counts (both before any capacity clamp).  Used to size
+ * max_faces_per_bin and max_bin_entries. */
+MESHRAST_API int rast_bin_occupancy(const rast_params *p, int64_t V, int64_t F, const void *workspace,
+                       int32_t *max_count, int64_t *total_entries, void *stream);
+
+/* Static text for a MESHRAST_ERR_* code. */
+MESHRAST_API const char *rast_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MESHRAST_H */

@@ -1,0 +1,143 @@
+"""``torch.autograd.Function`` wrappers over the C ABI.
+
+``rasterize_meshes`` returns Fragment data (Section 3.2 "Rasterizer") and
+differentiates to the packed vertices through ``rast_mesh_bwd``, which
+recomputes barycentrics, depth and distance from ``pix_to_face`` instead of
+keeping them for the backward pass.  ``blend`` applies Algorithm 1
+(silhouette) or Algorithms 1 + 2 (softmax rgb + silhouette alpha) and
+differentiates through ``blend_bwd``.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import torch
+
+from . import ops
+
+
+@dataclass
+class RasterSettings:
+    image_size: int
+    faces_per_pixel: int = 1
+    blur_radius: float = 0.0
+    bin_size: int = 16               # 0: plain per-image form
+    max_faces_per_bin: int = 4096
+    max_bin_entries: int = 0
+    perspective_correct: bool = True
+    clip_barycentric_coords: bool = False
+
+    def params(self, N):
+        return ops.make_rast_params(N, self.image_size, self.faces_per_pixel, self.blur_radius, self.bin_size,
+                                    self.max_faces_per_bin, self.perspective_correct,
+                                    self.clip_barycentric_coords, self.max_bin_entries)
+
+
+@dataclass
+class BlendSettings:
+    sigma: float = 1e-4
+    gamma: float = 1e-4
+    znear: float = 0.1
+    zfar: float = 100.0
+    background: tuple = (1.0, 1.0, 1.0)
+    eps: float = 1e-10
+    rgb: bool = True
+
+    def params(self):
+        return ops.make_blend_params(self.sigma, self.gamma, self.znear, self.zfar, self.background, self.eps,
+                                     ops.BLEND_RGB if self.rgb else ops.BLEND_SIL)
+
+
+class Workspace:
+    """Device workspace reused across calls; grows when a call needs more."""
+
+    def __init__(self, device="cuda"):
+        self.device = device
+        self.buf = None
+
+    def get(self, p, V, F):
+        n = ops.rast_workspace_bytes(p, V, F)
+        if self.buf is None or self.buf.numel() < n:
+            self.buf = torch.empty(n, dtype=torch.uint8, device=self.device)
+        return self.buf
+
+    def status(self):
+        return 0 if self.buf is None else ops.rast_query_status(self.buf)
+
+
+class _Rasterize(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, verts, faces, first_face, num_faces, cams, settings, ws):
+        N = first_face.shape[0]
+        S, K = settings.image_size, settings.faces_per_pixel
+        p = settings.params(N)
+        buf = ws.get(p, verts.shape[0], faces.shape[0])
+        p2f, zbuf, bary, dists = ops.alloc_fragments(N, S, K, verts.device)
+        ops.rast_mesh_fwd(p, verts, faces, first_face, num_faces, cams, p2f, zbuf, bary, dists, buf)
+        ctx.save_for_backward(verts, faces, first_face, num_faces, cams, p2f)
+        ctx.settings = settings
+        ctx.ws = ws
+        ctx.mark_non_differentiable(p2f)
+        ctx.set_materialize_grads(False)
+        return p2f, zbuf, bary, dists
+
+    @staticmethod
+    def backward(ctx, g_p2f, g_zbuf, g_bary, g_dists):
+        verts, faces, first_face, num_faces, cams, p2f = ctx.saved_tensors
+        p = ctx.settings.params(first_face.shape[0])
+        buf = ctx.ws.get(p, verts.shape[0], faces.shape[0])
+        gv = torch.empty_like(verts)
+        c = lambda t: None if t is None else t.contiguous()
+        ops.rast_mesh_bwd(p, verts, faces, first_face, num_faces, cams, p2f, c(g_zbuf), c(g_bary), c(g_dists), gv,
+                          buf)
+        return gv, None, None, None, None, None, None
+
+
+def rasterize_meshes(verts, faces, first_face, num_faces, cams, settings: RasterSettings, ws: Workspace = None):
+    """Fragments (pix_to_face, zbuf, bary, dists) of a packed mesh batch."""
+    if ws is None:
+        ws = Workspace(verts.device)
+    return _Rasterize.apply(verts.contiguous(), faces.contiguous(), first_face.contiguous(),
+                            num_faces.contiguous(), cams.contiguous(), settings, ws)
+
+
+class _Blend(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, pix_to_face, zbuf, bary, dists, faces, colors, settings):
+        N, S, _, K = pix_to_face.shape
+        bp = settings.params()
+        img = torch.empty((N, S, S, 4), dtype=torch.float32, device=pix_to_face.device)
+        rgb = settings.rgb
+        ops.blend_fwd(bp, N, S, K, pix_to_face, zbuf if rgb else None, bary if rgb else None, dists,
+                      faces if rgb else None, colors if rgb else None, img)
+        ctx.save_for_backward(pix_to_face, zbuf, bary, dists, faces, colors)
+        ctx.settings = settings
+        return img
+
+    @staticmethod
+    def backward(ctx, g_img):
+        pix_to_face, zbuf, bary, dists, faces, colors = ctx.saved_tensors
+        s = ctx.settings
+        N, S, _, K = pix_to_face.shape
+        gd = torch.empty_like(dists)
+        if s.rgb:
+            gz = torch.empty_like(zbuf)
+            gb = torch.empty_like(bary)
+            gc = torch.empty_like(colors)
+            ops.blend_bwd(s.params(), N, S, K, pix_to_face, zbuf, bary, dists, faces, colors, g_img.contiguous(),
+                          gz, gb, gd, gc)
+            return None, gz, gb, gd, None, gc, None
+        ops.blend_bwd(s.params(), N, S, K, pix_to_face, None, None, dists, None, None, g_img.contiguous(), None,
+                      None, gd, None)
+        return None, None, None, gd, None, None, None
+
+
+def blend(pix_to_face, zbuf, bary, dists, faces=None, colors=None, settings: BlendSettings = None):
+    """RGBA image (N, S, S, 4): softmax rgb (if settings.rgb) and silhouette alpha."""
+    settings = settings or BlendSettings()
+    if settings.rgb:
+        if faces is None or colors is None:
+            raise ValueError("rgb blending needs faces and per-vertex colours")
+        return _Blend.apply(pix_to_face, zbuf, bary, dists, faces, colors, settings)
+    dummy = torch.zeros(0, device=pix_to_face.device)
+    return _Blend.apply(pix_to_face, zbuf, bary, dists, dummy, dummy, settings)

@@ -1,0 +1,413 @@
+// Soft blends for sm_103a: Algorithm 1 (silhouette) and Algorithm 2 (softmax
+// rgb) of the paper, forward and hand-written adjoint, one thread per pixel.
+//
+//   prob_k = sigmoid(-d_k / sigma),  1 - prob_k = sigmoid(d_k / sigma)
+//   alpha  = 1 - prod_k (1 - prob_k)
+//   zinv_k = (zfar - z_k)/(zfar - znear),  m = max(eps, max_k zinv_k)
+//   w_k    = prob_k exp((zinv_k - m)/gamma),  delta = exp((eps - m)/gamma)
+//   rgb    = (sum_k w_k c_k + delta bg)/(sum_k w_k + delta)
+// over the slots with pix_to_face >= 0; c_k is the per-vertex colour of the
+// slot's face interpolated with its barycentrics.  When m is a face's zinv
+// the exponent zinv_k - m is formed as (z_min - z_k)/(zfar - znear), which
+// is the same number without the cancellation of two values near 1.  The
+// adjoint treats m as a constant: rgb does not depend on it.
+#include <cuda_runtime.h>
+
+#include "rast_common.cuh"
+#include "rast_internal.h"
+
+namespace mr {
+
+__device__ __forceinline__ float sigmoidf_(float x) { return 1.f / (1.f + expf(-x)); }
+
+// face ids as int: negative -> -1 (empty), beyond int range -> INT_MAX (no colour)
+__device__ __forceinline__ int clamp_id(long long v) { return v < 0 ? -1 : (v > 0x7fffffffLL ? 0x7fffffff : (int)v); }
+
+template <int KM>
+struct SlotData {
+    float z[KM], d[KM];
+    int f[KM];
+};
+
+// load the K slots of pixel `pix` (KM == K)
+template <int KM>
+__device__ __forceinline__ void load_slots(const BlendArgs &a, int64_t pix, bool rgb, SlotData<KM> &S) {
+    const int64_t s0 = pix * KM;
+    if constexpr (KM % 4 == 0) {
+        const float4 *dp = reinterpret_cast<const float4 *>(a.dists + s0);
+#pragma unroll
+        for (int j = 0; j < KM / 4; ++j) {
+            float4 v = __ldg(dp + j);
+            S.d[4 * j] = v.x; S.d[4 * j + 1] = v.y; S.d[4 * j + 2] = v.z; S.d[4 * j + 3] = v.w;
+        }
+        if (rgb) {
+            const float4 *zp = reinterpret_cast<const float4 *>(a.zbuf + s0);
+#pragma unroll
+            for (int j = 0; j < KM / 4; ++j) {
+                float4 v = __ldg(zp + j);
+                S.z[4 * j] = v.x; S.z[4 * j + 1] = v.y; S.z[4 * j + 2] = v.z; S.z[4 * j + 3] = v.w;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            S.d[k] = __ldg(a.dists + s0 + k);
+            if (rgb) S.z[k] = __ldg(a.zbuf + s0 + k);
+        }
+    }
+    if constexpr (KM % 2 == 0) {
+        const longlong2 *fp = reinterpret_cast<const longlong2 *>(a.pix_to_face + s0);
+#pragma unroll
+        for (int j = 0; j < KM / 2; ++j) {
+            longlong2 v = __ldg(fp + j);
+            S.f[2 * j] = clamp_id(v.x);
+            S.f[2 * j + 1] = clamp_id(v.y);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < KM; ++k) S.f[k] = clamp_id(__ldg(a.pix_to_face + s0 + k));
+    }
+}
+
+__device__ __forceinline__ void slot_colour(const BlendArgs &a, int64_t s, int64_t f, float c[3], int64_t vi[3],
+                                            float b[3]) {
+    b[0] = __ldg(a.bary + 3 * s);
+    b[1] = __ldg(a.bary + 3 * s + 1);
+    b[2] = __ldg(a.bary + 3 * s + 2);
+    c[0] = c[1] = c[2] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        vi[i] = -1;
+        if (f >= a.F) continue;  // ids outside the batch contribute no colour
+        const int64_t v = __ldg(a.faces + 3 * (int64_t)f + i);
+        if (v < 0 || v >= a.V) continue;
+        vi[i] = v;
+        const float *col = a.colors + 3 * v;
+        c[0] += b[i] * __ldg(col);
+        c[1] += b[i] * __ldg(col + 1);
+        c[2] += b[i] * __ldg(col + 2);
+    }
+}
+
+__device__ __forceinline__ float3 vertex_colour(const BlendArgs &a, int64_t v) {
+    if (v < 0) return make_float3(0.f, 0.f, 0.f);
+    const float *col = a.colors + 3 * v;
+    return make_float3(__ldg(col), __ldg(col + 1), __ldg(col + 2));
+}
+
+// ---------------------------------------------------------------------------
+// register version (KM = K <= 16)
+// ---------------------------------------------------------------------------
+template <int KM>
+__global__ void __launch_bounds__(256) k_blend_fwd(BlendArgs a) {
+    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= a.P) return;
+    const bool rgb = a.mode == MESHRAST_BLEND_RGB;
+    SlotData<KM> S;
+    load_slots<KM>(a, pix, rgb, S);
+    float keep = 1.f;
+    float zmin = __int_as_float(0x7f800000);
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        if (S.f[k] < 0) continue;
+        keep *= sigmoidf_(S.d[k] / a.sigma);
+        if (rgb) zmin = fminf(zmin, S.z[k]);
+        any = true;
+    }
+    float4 out = make_float4(0.f, 0.f, 0.f, 1.f - keep);
+    if (rgb) {
+        const float range = a.zfar - a.znear;
+        const float ztop = any ? (a.zfar - zmin) / range : -__int_as_float(0x7f800000);
+        const bool face_max = any && ztop > a.eps;
+        const float m = face_max ? ztop : a.eps;
+        float num0 = 0.f, num1 = 0.f, num2 = 0.f, den = 0.f;
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            if (S.f[k] < 0) continue;
+            const float arg = face_max ? (zmin - S.z[k]) / (range * a.gamma)
+                                       : ((a.zfar - S.z[k]) / range - m) / a.gamma;
+            const float w = sigmoidf_(-S.d[k] / a.sigma) * expf(arg);
+            float c[3], b[3];
+            int64_t vi[3];
+            slot_colour(a, pix * KM + k, S.f[k], c, vi, b);
+            num0 += w * c[0];
+            num1 += w * c[1];
+            num2 += w * c[2];
+            den += w;
+        }
+        const float delta = expf((a.eps - m) / a.gamma);
+        const float D = den + delta;
+        out.x = (num0 + delta * a.bg0) / D;
+        out.y = (num1 + delta * a.bg1) / D;
+        out.z = (num2 + delta * a.bg2) / D;
+    }
+    reinterpret_cast<float4 *>(a.image)[pix] = out;
+}
+
+template <int KM>
+__global__ void __launch_bounds__(256) k_blend_bwd(BlendArgs a) {
+    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= a.P) return;
+    const bool rgb = a.mode == MESHRAST_BLEND_RGB;
+    SlotData<KM> S;
+    load_slots<KM>(a, pix, rgb, S);
+    const float4 g = reinterpret_cast<const float4 *>(a.grad_image)[pix];
+    float keep = 1.f;
+    float zmin = __int_as_float(0x7f800000);
+    bool any = false;
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        if (S.f[k] < 0) continue;
+        keep *= sigmoidf_(S.d[k] / a.sigma);
+        if (rgb) zmin = fminf(zmin, S.z[k]);
+        any = true;
+    }
+    float gd[KM];
+    // silhouette: d alpha / d d_k = -prob_k * prod_j (1 - prob_j) / sigma
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        gd[k] = (S.f[k] < 0) ? 0.f : g.w * (-sigmoidf_(-S.d[k] / a.sigma) * keep / a.sigma);
+    }
+    const int64_t s0 = pix * KM;
+    if (rgb) {
+        const float range = a.zfar - a.znear;
+        const float ztop = any ? (a.zfar - zmin) / range : -__int_as_float(0x7f800000);
+        const bool face_max = any && ztop > a.eps;
+        const float m = face_max ? ztop : a.eps;
+        float E[KM], W[KM];
+        float num0 = 0.f, num1 = 0.f, num2 = 0.f, den = 0.f;
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            E[k] = 0.f;
+            W[k] = 0.f;
+            if (S.f[k] < 0) continue;
+            const float arg = face_max ? (zmin - S.z[k]) / (range * a.gamma)
+                                       : ((a.zfar - S.z[k]) / range - m) / a.gamma;
+            E[k] = expf(arg);
+            W[k] = sigmoidf_(-S.d[k] / a.sigma) * E[k];
+            float c[3], b[3];
+            int64_t vi[3];
+            slot_colour(a, s0 + k, S.f[k], c, vi, b);
+            num0 += W[k] * c[0];
+            num1 += W[k] * c[1];
+            num2 += W[k] * c[2];
+            den += W[k];
+        }
+        const float delta = expf((a.eps - m) / a.gamma);
+        const float D = den + delta;
+        const float iD = 1.f / D;
+        const float rgb0 = (num0 + delta * a.bg0) * iD, rgb1 = (num1 + delta * a.bg1) * iD,
+                    rgb2 = (num2 + delta * a.bg2) * iD;
+#pragma unroll
+        for (int k = 0; k < KM; ++k) {
+            const int64_t s = s0 + k;
+            if (S.f[k] < 0) {
+                a.grad_zbuf[s] = 0.f;
+                a.grad_bary[3 * s] = 0.f;
+                a.grad_bary[3 * s + 1] = 0.f;
+                a.grad_bary[3 * s + 2] = 0.f;
+                continue;
+            }
+            float c[3], b[3];
+            int64_t vi[3];
+            slot_colour(a, s, S.f[k], c, vi, b);
+            const float gw = (g.x * (c[0] - rgb0) + g.y * (c[1] - rgb1) + g.z * (c[2] - rgb2)) * iD;
+            const float prob = sigmoidf_(-S.d[k] / a.sigma);
+            const float q = sigmoidf_(S.d[k] / a.sigma);
+            gd[k] += gw * E[k] * (-prob * q / a.sigma);
+            a.grad_zbuf[s] = gw * W[k] / a.gamma * (-1.f / range);
+            const float gc0 = g.x * W[k] * iD, gc1 = g.y * W[k] * iD, gc2 = g.z * W[k] * iD;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float3 col = vertex_colour(a, vi[i]);
+                a.grad_bary[3 * s + i] = gc0 * col.x + gc1 * col.y + gc2 * col.z;
+                if (vi[i] < 0) continue;
+                float *gcol = a.grad_colors + 3 * vi[i];
+                atomicAdd(gcol, gc0 * b[i]);
+                atomicAdd(gcol + 1, gc1 * b[i]);
+                atomicAdd(gcol + 2, gc2 * b[i]);
+            }
+        }
+    }
+    if constexpr (KM % 4 == 0) {
+        float4 *dp = reinterpret_cast<float4 *>(a.grad_dists + s0);
+#pragma unroll
+        for (int j = 0; j < KM / 4; ++j) dp[j] = make_float4(gd[4 * j], gd[4 * j + 1], gd[4 * j + 2], gd[4 * j + 3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < KM; ++k) a.grad_dists[s0 + k] = gd[k];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// generic version (any K): re-reads slots from global memory
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_blend_fwd_any(BlendArgs a) {
+    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= a.P) return;
+    const bool rgb = a.mode == MESHRAST_BLEND_RGB;
+    const int K = a.K;
+    const int64_t s0 = pix * K;
+    float keep = 1.f, zmin = __int_as_float(0x7f800000);
+    bool any = false;
+    for (int k = 0; k < K; ++k) {
+        if (a.pix_to_face[s0 + k] < 0) continue;
+        keep *= sigmoidf_(a.dists[s0 + k] / a.sigma);
+        if (rgb) zmin = fminf(zmin, a.zbuf[s0 + k]);
+        any = true;
+    }
+    float4 out = make_float4(0.f, 0.f, 0.f, 1.f - keep);
+    if (rgb) {
+        const float range = a.zfar - a.znear;
+        const float ztop = any ? (a.zfar - zmin) / range : -__int_as_float(0x7f800000);
+        const bool face_max = any && ztop > a.eps;
+        const float m = face_max ? ztop : a.eps;
+        float num0 = 0.f, num1 = 0.f, num2 = 0.f, den = 0.f;
+        for (int k = 0; k < K; ++k) {
+            const int64_t s = s0 + k;
+            const int64_t f = a.pix_to_face[s];
+            if (f < 0) continue;
+            const float z = a.zbuf[s];
+            const float arg = face_max ? (zmin - z) / (range * a.gamma) : ((a.zfar - z) / range - m) / a.gamma;
+            const float w = sigmoidf_(-a.dists[s] / a.sigma) * expf(arg);
+            float c[3], b[3];
+            int64_t vi[3];
+            slot_colour(a, s, f, c, vi, b);
+            num0 += w * c[0];
+            num1 += w * c[1];
+            num2 += w * c[2];
+            den += w;
+        }
+        const float delta = expf((a.eps - m) / a.gamma);
+        const float D = den + delta;
+        out.x = (num0 + delta * a.bg0) / D;
+        out.y = (num1 + delta * a.bg1) / D;
+        out.z = (num2 + delta * a.bg2) / D;
+    }
+    reinterpret_cast<float4 *>(a.image)[pix] = out;
+}
+
+__global__ void __launch_bounds__(256) k_blend_bwd_any(BlendArgs a) {
+    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (pix >= a.P) return;
+    const bool rgb = a.mode == MESHRAST_BLEND_RGB;
+    const int K = a.K;
+    const int64_t s0 = pix * K;
+    const float4 g = reinterpret_cast<const float4 *>(a.grad_image)[pix];
+    float keep = 1.f, zmin = __int_as_float(0x7f800000);
+    bool any = false;
+    for (int k = 0; k < K; ++k) {
+        if (a.pix_to_face[s0 + k] < 0) continue;
+        keep *= sigmoidf_(a.dists[s0 + k] / a.sigma);
+        if (rgb) zmin = fminf(zmin, a.zbuf[s0 + k]);
+        any = true;
+    }
+    float range = 0.f, m = 0.f, iD = 0.f, rgb0 = 0.f, rgb1 = 0.f, rgb2 = 0.f;
+    bool face_max = false;
+    if (rgb) {
+        range = a.zfar - a.znear;
+        const float ztop = any ? (a.zfar - zmin) / range : -__int_as_float(0x7f800000);
+        face_max = any && ztop > a.eps;
+        m = face_max ? ztop : a.eps;
+        float num0 = 0.f, num1 = 0.f, num2 = 0.f, den = 0.f;
+        for (int k = 0; k < K; ++k) {
+            const int64_t s = s0 + k;
+            const int64_t f = a.pix_to_face[s];
+            if (f < 0) continue;
+            const float z = a.zbuf[s];
+            const float arg = face_max ? (zmin - z) / (range * a.gamma) : ((a.zfar - z) / range - m) / a.gamma;
+            const float w = sigmoidf_(-a.dists[s] / a.sigma) * expf(arg);
+            float c[3], b[3];
+            int64_t vi[3];
+            slot_colour(a, s, f, c, vi, b);
+            num0 += w * c[0];
+            num1 += w * c[1];
+            num2 += w * c[2];
+            den += w;
+        }
+        const float delta = expf((a.eps - m) / a.gamma);
+        iD = 1.f / (den + delta);
+        rgb0 = (num0 + delta * a.bg0) * iD;
+        rgb1 = (num1 + delta * a.bg1) * iD;
+        rgb2 = (num2 + delta * a.bg2) * iD;
+    }
+    for (int k = 0; k < K; ++k) {
+        const int64_t s = s0 + k;
+        const int64_t f = a.pix_to_face[s];
+        if (f < 0) {
+            a.grad_dists[s] = 0.f;
+            if (rgb) {
+                a.grad_zbuf[s] = 0.f;
+                a.grad_bary[3 * s] = a.grad_bary[3 * s + 1] = a.grad_bary[3 * s + 2] = 0.f;
+            }
+            continue;
+        }
+        const float d = a.dists[s];
+        const float prob = sigmoidf_(-d / a.sigma);
+        float gd = g.w * (-prob * keep / a.sigma);
+        if (rgb) {
+            const float z = a.zbuf[s];
+            const float arg = face_max ? (zmin - z) / (range * a.gamma) : ((a.zfar - z) / range - m) / a.gamma;
+            const float E = expf(arg);
+            const float W = prob * E;
+            float c[3], b[3];
+            int64_t vi[3];
+            slot_colour(a, s, f, c, vi, b);
+            const float gw = (g.x * (c[0] - rgb0) + g.y * (c[1] - rgb1) + g.z * (c[2] - rgb2)) * iD;
+            gd += gw * E * (-prob * sigmoidf_(d / a.sigma) / a.sigma);
+            a.grad_zbuf[s] = gw * W / a.gamma * (-1.f / range);
+            const float gc0 = g.x * W * iD, gc1 = g.y * W * iD, gc2 = g.z * W * iD;
+            for (int i = 0; i < 3; ++i) {
+                const float3 col = vertex_colour(a, vi[i]);
+                a.grad_bary[3 * s + i] = gc0 * col.x + gc1 * col.y + gc2 * col.z;
+                if (vi[i] < 0) continue;
+                float *gcol = a.grad_colors + 3 * vi[i];
+                atomicAdd(gcol, gc0 * b[i]);
+                atomicAdd(gcol + 1, gc1 * b[i]);
+                atomicAdd(gcol + 2, gc2 * b[i]);
+            }
+        }
+        a.grad_dists[s] = gd;
+    }
+}
+
+// ---------------------------------------------------------------------------
+template <int KM>
+static void launch_fwd_t(const BlendArgs &a, int grid, cudaStream_t st) {
+    k_blend_fwd<KM><<<grid, 256, 0, st>>>(a);
+}
+template <int KM>
+static void launch_bwd_t(const BlendArgs &a, int grid, cudaStream_t st) {
+    k_blend_bwd<KM><<<grid, 256, 0, st>>>(a);
+}
+
+cudaError_t launch_blend_fwd(const BlendArgs &a, cudaStream_t st) {
+    if (a.P <= 0) return cudaSuccess;
+    const int grid = (int)((a.P + 255) / 256);
+    switch (a.K) {
+        case 1: launch_fwd_t<1>(a, grid, st); break;
+        case 2: launch_fwd_t<2>(a, grid, st); break;
+        case 4: launch_fwd_t<4>(a, grid, st); break;
+        case 8: launch_fwd_t<8>(a, grid, st); break;
+        case 16: launch_fwd_t<16>(a, grid, st); break;
+        default: k_blend_fwd_any<<<grid, 256, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blend_bwd(const BlendArgs &a, cudaStream_t st) {
+    if (a.P <= 0) return cudaSuccess;
+    const int grid = (int)((a.P + 255) / 256);
+    switch (a.K) {
+        case 1: launch_bwd_t<1>(a, grid, st); break;
+        case 2: launch_bwd_t<2>(a, grid, st); break;
+        case 4: launch_bwd_t<4>(a, grid, st); break;
+        case 8: launch_bwd_t<8>(a, grid, st); break;
+        case 16: launch_bwd_t<16>(a, grid, st); break;
+        default: k_blend_bwd_any<<<grid, 256, 0, st>>>(a); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace mr

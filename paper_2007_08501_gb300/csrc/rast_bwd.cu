@@ -1,0 +1,166 @@
+// Backward rasterization for sm_103a.
+//
+// Section 3.2 of the paper: the backward pass reuses the Fragment data (the
+// face id of each slot) instead of recomputing face-pixel intersections.  For
+// every non-empty slot this kernel recomputes the fragment of that face at
+// that pixel from the staged face record and pulls dL/d(bary, zbuf, dists)
+// back through clipping, perspective correction, the edge functions and the
+// nearest-segment distance to the three NDC corners, then through the
+// projection Jacobian and R^T to world-space vertices (atomic scatter).
+#include <cuda_runtime.h>
+
+#include "rast_common.cuh"
+#include "rast_internal.h"
+
+namespace mr {
+
+// gradient of e(p; a, b) = cross(b - a, p - a) with respect to a and b
+__device__ __forceinline__ void edge_grad(float ax, float ay, float bx, float by, float px, float py, float g,
+                                          float &gax, float &gay, float &gbx, float &gby) {
+    gax += g * (by - py);
+    gay += g * (px - bx);
+    gbx += g * (py - ay);
+    gby += g * (ax - px);
+}
+
+__global__ void __launch_bounds__(256) k_rast_bwd(RastBwdArgs a) {
+    const int *face_mesh = a.face_mesh;
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= a.slots) return;
+    const int64_t f = a.pix_to_face[s];
+    if (f < 0 || f >= a.F) return;  // empty slot (or an id outside the batch)
+    const int n_face = face_mesh[f];
+    if (n_face < 0) return;
+    const int64_t pix = s / a.K;
+    const int64_t SS = (int64_t)a.S * a.S;
+    const int rem = (int)(pix % SS);
+    const int r = rem / a.S, c = rem % a.S;
+    const PixC p = pixel_centre(r, c, a.S);
+
+    FaceRec R;
+    {
+        const float4 *src = reinterpret_cast<const float4 *>(a.rec + f);
+        R.a = __ldg(src);
+        R.b = __ldg(src + 1);
+        R.c = __ldg(src + 2);
+        R.d = __ldg(src + 3);
+    }
+    float gz = a.grad_zbuf ? a.grad_zbuf[s] : 0.f;
+    float gd = a.grad_dists ? a.grad_dists[s] : 0.f;
+    float gbp0 = 0.f, gbp1 = 0.f, gbp2 = 0.f;
+    if (a.grad_bary) {
+        gbp0 = a.grad_bary[3 * s];
+        gbp1 = a.grad_bary[3 * s + 1];
+        gbp2 = a.grad_bary[3 * s + 2];
+    }
+    if (gz == 0.f && gd == 0.f && gbp0 == 0.f && gbp1 == 0.f && gbp2 == 0.f) return;
+
+    // ---- forward recompute (corner-0-relative coordinates) ----
+    float qx, qy;
+    local_q(R, p, qx, qy);
+    float b[3];
+    screen_bary(R, qx, qy, b[0], b[1], b[2]);
+    const bool inside = (b[0] >= 0.f) && (b[1] >= 0.f) && (b[2] >= 0.f);
+    int edge;
+    float tseg;
+    (void)nearest_edge(R, qx, qy, edge, tseg);
+    const float iz[3] = {R.d.y, R.d.z, R.d.w};
+    const float zc[3] = {1.f / iz[0], 1.f / iz[1], 1.f / iz[2]};
+    float bt[3], T = 1.f;
+    if (a.fl.persp) {
+        float t[3];
+        for (int i = 0; i < 3; ++i) t[i] = b[i] * iz[i];
+        T = t[0] + t[1] + t[2];
+        for (int i = 0; i < 3; ++i) bt[i] = t[i] / T;
+    } else {
+        for (int i = 0; i < 3; ++i) bt[i] = b[i];
+    }
+    float bp[3], cs = 1.f;
+    if (a.fl.clip) {
+        float cc[3];
+        for (int i = 0; i < 3; ++i) cc[i] = fmaxf(bt[i], 0.f);
+        cs = cc[0] + cc[1] + cc[2];
+        for (int i = 0; i < 3; ++i) bp[i] = cc[i] / cs;
+    } else {
+        for (int i = 0; i < 3; ++i) bp[i] = bt[i];
+    }
+
+    // ---- adjoint ----
+    float gbp[3] = {gbp0, gbp1, gbp2};
+    float gZ[3];
+    for (int i = 0; i < 3; ++i) {  // z = sum b'_i z_i
+        gbp[i] += gz * zc[i];
+        gZ[i] = gz * bp[i];
+    }
+    float gbt[3];
+    if (a.fl.clip) {
+        const float dot = gbp[0] * bp[0] + gbp[1] * bp[1] + gbp[2] * bp[2];
+        for (int i = 0; i < 3; ++i) gbt[i] = (bt[i] > 0.f) ? (gbp[i] - dot) / cs : 0.f;
+    } else {
+        for (int i = 0; i < 3; ++i) gbt[i] = gbp[i];
+    }
+    float gb[3];
+    if (a.fl.persp) {
+        // t_i = b_i / z_i, b~_i = t_i / T:  dt_i/db_i = iz_i, dt_i/dz_i = -b_i iz_i^2
+        const float dot = gbt[0] * bt[0] + gbt[1] * bt[1] + gbt[2] * bt[2];
+        for (int i = 0; i < 3; ++i) {
+            const float gt = (gbt[i] - dot) / T;
+            gb[i] = gt * iz[i];
+            gZ[i] -= gt * b[i] * iz[i] * iz[i];
+        }
+    } else {
+        for (int i = 0; i < 3; ++i) gb[i] = gbt[i];
+    }
+    const float invA = R.d.x;
+    float gA = 0.f, ge[3];
+    for (int i = 0; i < 3; ++i) {
+        ge[i] = gb[i] * invA;
+        gA -= gb[i] * b[i] * invA;
+    }
+    // local corner positions: P0 = 0, P1 = u, P2 = w; pixel = q
+    const float Px[3] = {0.f, R.b.x, R.b.z}, Py[3] = {0.f, R.b.y, R.b.w};
+    float gx[3] = {0.f, 0.f, 0.f}, gy[3] = {0.f, 0.f, 0.f};
+    // e0 = e(p; P1, P2), e1 = e(p; P2, P0), e2 = e(p; P0, P1)
+    edge_grad(Px[1], Py[1], Px[2], Py[2], qx, qy, ge[0], gx[1], gy[1], gx[2], gy[2]);
+    edge_grad(Px[2], Py[2], Px[0], Py[0], qx, qy, ge[1], gx[2], gy[2], gx[0], gy[0]);
+    edge_grad(Px[0], Py[0], Px[1], Py[1], qx, qy, ge[2], gx[0], gy[0], gx[1], gy[1]);
+    // A = e(P2; P0, P1)
+    edge_grad(Px[0], Py[0], Px[1], Py[1], Px[2], Py[2], gA, gx[0], gy[0], gx[1], gy[1]);
+    gx[2] += gA * (Py[0] - Py[1]);
+    gy[2] += gA * (Px[1] - Px[0]);
+    // distance to the nearest segment
+    const float gs = inside ? -gd : gd;
+    if (gs != 0.f) {
+        const int ia = edge, ib = (edge == 2) ? 0 : edge + 1;
+        const float rx = qx - (Px[ia] + tseg * (Px[ib] - Px[ia]));
+        const float ry = qy - (Py[ia] + tseg * (Py[ib] - Py[ia]));
+        gx[ia] += gs * (-2.f * rx * (1.f - tseg));
+        gy[ia] += gs * (-2.f * ry * (1.f - tseg));
+        gx[ib] += gs * (-2.f * rx * tseg);
+        gy[ib] += gs * (-2.f * ry * tseg);
+    }
+    // NDC -> view -> world
+    const float *cam = a.cams + 16 * n_face;
+    const float fo = cam[12];
+    const float v0x = R.a.x + R.a.z, v0y = R.a.y + R.a.w;
+    for (int i = 0; i < 3; ++i) {
+        const float xn = v0x + Px[i], yn = v0y + Py[i], z = zc[i];
+        const float gxv = gx[i] * fo / z;
+        const float gyv = gy[i] * fo / z;
+        const float gzv = gZ[i] - (gx[i] * xn + gy[i] * yn) / z;
+        const int64_t vi = a.faces[3 * f + i];
+        float *gv = a.grad_verts + 3 * vi;
+        atomicAdd(gv + 0, cam[0] * gxv + cam[3] * gyv + cam[6] * gzv);
+        atomicAdd(gv + 1, cam[1] * gxv + cam[4] * gyv + cam[7] * gzv);
+        atomicAdd(gv + 2, cam[2] * gxv + cam[5] * gyv + cam[8] * gzv);
+    }
+}
+
+cudaError_t launch_rast_bwd(const RastBwdArgs &a, cudaStream_t st) {
+    if (a.slots <= 0) return cudaSuccess;
+    const int64_t grid = (a.slots + 255) / 256;
+    k_rast_bwd<<<(unsigned)grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mr

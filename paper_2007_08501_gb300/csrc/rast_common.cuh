@@ -1,0 +1,330 @@
+// Shared device code of the sm_103a mesh rasterizer: the staged face record,
+// double-float helpers, pixel centres and the per-(pixel, face) evaluation
+// used by the fine pass, the plain per-image pass and the backward pass.
+//
+// Geometry follows Section 3.2 of the paper ("Rasterizer"): perspective
+// camera to NDC, per-pixel K nearest faces along z, Fragment data (face id,
+// barycentrics, z, signed xy distance).  The conventions are the ones stated
+// in include/meshrast.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "meshrast.h"
+
+namespace mr {
+
+constexpr float kCullArea = 1e-12f;
+constexpr int kMaxK = 64;
+
+// ---------------------------------------------------------------------------
+// Staged face record: 64 bytes, four float4, written once per face by the
+// staging kernel and read by the fine, plain and backward kernels.
+//   a = (v0x_hi, v0y_hi, v0x_lo, v0y_lo)   corner 0 in NDC as a double-float
+//   b = (ux, uy, wx, wy)                   u = v1 - v0, w = v2 - v0 (NDC)
+//   c = (xmin, xmax, ymin, ymax)           bbox inflated by sqrt(blur), rounded outward;
+//                                          culled faces have xmin = +inf, xmax = -inf
+//   d = (1/A, 1/z0, 1/z1, 1/z2)            A = cross(u, w), z_i = view depth of corner i
+// Storing corner 0 as hi + lo and the other corners relative to it keeps
+// pixel-relative coordinates exact to ~1e-14 even for sub-pixel faces, so
+// fp32 barycentrics stay within ~1e-7 of the FP64 values.
+// ---------------------------------------------------------------------------
+struct __align__(16) FaceRec {
+    float4 a, b, c, d;
+};
+static_assert(sizeof(FaceRec) == 64, "face record is 64 bytes");
+
+// ---------------------------------------------------------------------------
+// double-float (unevaluated sum hi + lo) arithmetic, error-free transforms
+// of Knuth (two-sum) and Dekker (two-product via fma).
+// ---------------------------------------------------------------------------
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+__device__ __forceinline__ df quick_two_sum(float a, float b) {  // |a| >= |b|
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df two_prod(float a, float b) {
+    float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    df s = two_sum(a.hi, b.hi);
+    df t = two_sum(a.lo, b.lo);
+    float lo = __fadd_rn(s.lo, t.hi);
+    df u = quick_two_sum(s.hi, lo);
+    return quick_two_sum(u.hi, __fadd_rn(u.lo, t.lo));
+}
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+    df p = two_prod(a.hi, b);
+    return quick_two_sum(p.hi, __fmaf_rn(a.lo, b, p.lo));
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+    df p = two_prod(a.hi, b.hi);
+    float lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, p.lo));
+    return quick_two_sum(p.hi, lo);
+}
+__device__ __forceinline__ df df_div(df a, df b) {
+    float q1 = __fdiv_rn(a.hi, b.hi);
+    df r = df_sub(a, df_mul_f(b, q1));
+    float q2 = __fdiv_rn(r.hi, b.hi);
+    df q = quick_two_sum(q1, q2);
+    r = df_sub(a, df_mul(b, q));
+    return df_add(q, {__fdiv_rn(r.hi, b.hi), 0.f});
+}
+// rounding a double-float down / up to a float (outward rounding of bboxes)
+__device__ __forceinline__ float df_round_down(df a) { return (a.lo < 0.f) ? nextafterf(a.hi, -INFINITY) : a.hi; }
+__device__ __forceinline__ float df_round_up(df a) { return (a.lo > 0.f) ? nextafterf(a.hi, INFINITY) : a.hi; }
+
+// ---------------------------------------------------------------------------
+// pixel centres: x = 1 - (2c+1)/S = (S - 2c - 1)/S, as a double-float
+// ---------------------------------------------------------------------------
+struct PixC {
+    float xh, xl, yh, yl;
+};
+__device__ __forceinline__ void pix_coord(int i, int S, float &h, float &l) {
+    float num = (float)(S - 2 * i - 1);  // exact for S < 2^24
+    float Sf = (float)S;
+    h = __fdiv_rn(num, Sf);
+    l = __fdiv_rn(__fmaf_rn(-h, Sf, num), Sf);
+}
+__device__ __forceinline__ PixC pixel_centre(int r, int c, int S) {
+    PixC p;
+    pix_coord(c, S, p.xh, p.xl);
+    pix_coord(r, S, p.yh, p.yl);
+    return p;
+}
+
+// ---------------------------------------------------------------------------
+// per-(pixel, face) evaluation
+// ---------------------------------------------------------------------------
+struct EvalFlags {
+    int persp, clip;
+    float blur, znear;
+};
+
+__device__ __forceinline__ bool in_bbox(const FaceRec &r, const PixC &p) {
+    return p.xh >= r.c.x && p.xh <= r.c.y && p.yh >= r.c.z && p.yh <= r.c.w;
+}
+
+// pixel position relative to corner 0
+__device__ __forceinline__ void local_q(const FaceRec &r, const PixC &p, float &qx, float &qy) {
+    qx = __fadd_rn(__fsub_rn(p.xh, r.a.x), __fsub_rn(p.xl, r.a.z));
+    qy = __fadd_rn(__fsub_rn(p.yh, r.a.y), __fsub_rn(p.yl, r.a.w));
+}
+
+// screen barycentrics from the edge functions
+//   e0 = cross(v2 - v1, p - v1), e1 = cross(v0 - v2, p - v2), e2 = cross(v1 - v0, p - v0)
+// in corner-0-relative coordinates (v0 = 0, v1 = u, v2 = w, p = q).
+__device__ __forceinline__ void screen_bary(const FaceRec &r, float qx, float qy, float &b0, float &b1,
+                                            float &b2) {
+    const float ux = r.b.x, uy = r.b.y, wx = r.b.z, wy = r.b.w;
+    float e2 = __fmaf_rn(ux, qy, -__fmul_rn(uy, qx));
+    float e1 = __fmaf_rn(qx, wy, -__fmul_rn(qy, wx));
+    float ax = __fsub_rn(wx, ux), ay = __fsub_rn(wy, uy);
+    float rx = __fsub_rn(qx, ux), ry = __fsub_rn(qy, uy);
+    float e0 = __fmaf_rn(ax, ry, -__fmul_rn(ay, rx));
+    b0 = __fmul_rn(e0, r.d.x);
+    b1 = __fmul_rn(e1, r.d.x);
+    b2 = __fmul_rn(e2, r.d.x);
+}
+
+// squared distance from (qx,qy) to segment a + t e, t in [0,1]; returns s, t
+__device__ __forceinline__ float seg_dist2(float ax, float ay, float ex, float ey, float qx, float qy,
+                                           float &t) {
+    float l2 = __fmaf_rn(ex, ex, __fmul_rn(ey, ey));
+    float px = __fsub_rn(qx, ax), py = __fsub_rn(qy, ay);
+    float dot = __fmaf_rn(px, ex, __fmul_rn(py, ey));
+    t = (l2 > 0.f) ? __fdiv_rn(dot, l2) : 0.f;
+    t = fminf(fmaxf(t, 0.f), 1.f);
+    float rx = __fsub_rn(px, __fmul_rn(t, ex)), ry = __fsub_rn(py, __fmul_rn(t, ey));
+    return __fmaf_rn(rx, rx, __fmul_rn(ry, ry));
+}
+
+// nearest edge segment (0: v0v1, 1: v1v2, 2: v2v0; ties to the lower index)
+__device__ __forceinline__ float nearest_edge(const FaceRec &r, float qx, float qy, int &edge, float &t) {
+    const float ux = r.b.x, uy = r.b.y, wx = r.b.z, wy = r.b.w;
+    float t0, t1, t2;
+    float s0 = seg_dist2(0.f, 0.f, ux, uy, qx, qy, t0);
+    float s1 = seg_dist2(ux, uy, __fsub_rn(wx, ux), __fsub_rn(wy, uy), qx, qy, t1);
+    float s2 = seg_dist2(wx, wy, -wx, -wy, qx, qy, t2);
+    float s = s0;
+    edge = 0;
+    t = t0;
+    if (s1 < s) { s = s1; edge = 1; t = t1; }
+    if (s2 < s) { s = s2; edge = 2; t = t2; }
+    return s;
+}
+
+// Lower bound on the squared distance for an outside pixel: the distance to
+// the line of any violated edge.  Edge i here is the one opposite corner i.
+__device__ __forceinline__ bool beyond_blur_lines(const FaceRec &r, float qx, float qy, float b0, float b1,
+                                                  float b2, float blur) {
+    // e_i = b_i * A; squared distance to that edge's line = e_i^2 / |edge_i|^2
+    const float ux = r.b.x, uy = r.b.y, wx = r.b.z, wy = r.b.w;
+    const float A = 1.f / r.d.x;  // only used in a conservative test
+    float l0 = (wx - ux) * (wx - ux) + (wy - uy) * (wy - uy);
+    float l1 = wx * wx + wy * wy;
+    float l2 = ux * ux + uy * uy;
+    float m = 0.f;
+    float A2 = A * A;
+    // compare with a 1e-3 relative slack so rounding never rejects a true candidate
+    if (b0 < 0.f) m = fmaxf(m, b0 * b0 * A2 / l0);
+    if (b1 < 0.f) m = fmaxf(m, b1 * b1 * A2 / l1);
+    if (b2 < 0.f) m = fmaxf(m, b2 * b2 * A2 / l2);
+    return m > blur * 1.001f;
+}
+
+// Depth of a face at a pixel and final barycentrics, in the order
+// perspective correction -> clipping -> z = sum b'_i z_i.
+template <bool WANT_BARY>
+__device__ __forceinline__ float face_depth(const FaceRec &r, int persp, int clip, bool inside, float b0,
+                                            float b1, float b2, float *bp) {
+    float t0 = b0, t1 = b1, t2 = b2;
+    if (persp) {
+        t0 = __fmul_rn(b0, r.d.y);
+        t1 = __fmul_rn(b1, r.d.z);
+        t2 = __fmul_rn(b2, r.d.w);
+        float T = __fadd_rn(__fadd_rn(t0, t1), t2);
+        if (!clip || inside) {
+            // b~ = t / T; z = sum b~_i z_i = 1 / T
+            if (WANT_BARY) {
+                float iT = __fdiv_rn(1.f, T);
+                bp[0] = __fmul_rn(t0, iT);
+                bp[1] = __fmul_rn(t1, iT);
+                bp[2] = __fmul_rn(t2, iT);
+            }
+            return __fdiv_rn(1.f, T);
+        }
+        float iT = __fdiv_rn(1.f, T);
+        t0 = __fmul_rn(t0, iT);
+        t1 = __fmul_rn(t1, iT);
+        t2 = __fmul_rn(t2, iT);
+    } else if (!clip || inside) {
+        if (WANT_BARY) { bp[0] = b0; bp[1] = b1; bp[2] = b2; }
+        return __fadd_rn(__fadd_rn(__fmul_rn(b0, __frcp_rn(r.d.y)), __fmul_rn(b1, __frcp_rn(r.d.z))),
+                         __fmul_rn(b2, __frcp_rn(r.d.w)));
+    }
+    // clipping: c_i = max(b~_i, 0) / sum
+    float c0 = fmaxf(t0, 0.f), c1 = fmaxf(t1, 0.f), c2 = fmaxf(t2, 0.f);
+    float cs = __fadd_rn(__fadd_rn(c0, c1), c2);
+    float ic = __fdiv_rn(1.f, cs);
+    c0 = __fmul_rn(c0, ic);
+    c1 = __fmul_rn(c1, ic);
+    c2 = __fmul_rn(c2, ic);
+    if (WANT_BARY) { bp[0] = c0; bp[1] = c1; bp[2] = c2; }
+    return __fadd_rn(__fadd_rn(__fmul_rn(c0, __frcp_rn(r.d.y)), __fmul_rn(c1, __frcp_rn(r.d.z))),
+                     __fmul_rn(c2, __frcp_rn(r.d.w)));
+}
+
+// Candidate test + sort key for the K-nearest pass.  Returns true and the
+// depth when the face is a candidate for the pixel.
+__device__ __forceinline__ bool face_key(const FaceRec &r, const PixC &p, const EvalFlags &fl, float &z) {
+    if (!in_bbox(r, p)) return false;
+    float qx, qy;
+    local_q(r, p, qx, qy);
+    float b0, b1, b2;
+    screen_bary(r, qx, qy, b0, b1, b2);
+    bool inside = (b0 >= 0.f) && (b1 >= 0.f) && (b2 >= 0.f);
+    if (!inside) {
+        if (!(fl.blur > 0.f)) return false;
+        if (beyond_blur_lines(r, qx, qy, b0, b1, b2, fl.blur)) return false;
+        int e;
+        float t;
+        float s = nearest_edge(r, qx, qy, e, t);
+        if (!(s < fl.blur)) return false;
+    }
+    z = face_depth<false>(r, fl.persp, fl.clip, inside, b0, b1, b2, nullptr);
+    return isfinite(z) && z >= fl.znear;
+}
+
+// Full fragment (for a face already known to be a candidate).
+__device__ __forceinline__ void face_fragment(const FaceRec &r, const PixC &p, const EvalFlags &fl, float *bp,
+                                              float &dist) {
+    float qx, qy;
+    local_q(r, p, qx, qy);
+    float b0, b1, b2;
+    screen_bary(r, qx, qy, b0, b1, b2);
+    bool inside = (b0 >= 0.f) && (b1 >= 0.f) && (b2 >= 0.f);
+    int e;
+    float t;
+    float s = nearest_edge(r, qx, qy, e, t);
+    dist = inside ? -s : s;
+    (void)face_depth<true>(r, fl.persp, fl.clip, inside, b0, b1, b2, bp);
+}
+
+// strict total order on (depth, face id)
+__device__ __forceinline__ bool key_less(float za, int fa, float zb, int fb) {
+    return za < zb || (za == zb && fa < fb);
+}
+
+// Register-resident top-K (KM slots, sorted ascending).  Slots beyond the
+// runtime K are kept too: the first K of the top KM are the top K.
+template <int KM>
+struct TopK {
+    float z[KM];
+    int f[KM];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int k = 0; k < KM; ++k) { z[k] = __int_as_float(0x7f800000); f[k] = 0x7fffffff; }
+    }
+    __device__ __forceinline__ bool admits(float zz, int ff) const { return key_less(zz, ff, z[KM - 1], f[KM - 1]); }
+    __device__ __forceinline__ void insert(float zz, int ff) {
+        z[KM - 1] = zz;
+        f[KM - 1] = ff;
+#pragma unroll
+        for (int k = KM - 1; k > 0; --k) {
+            bool sw = key_less(z[k], f[k], z[k - 1], f[k - 1]);
+            float tz = z[k - 1];
+            int tf = f[k - 1];
+            z[k - 1] = sw ? z[k] : tz;
+            f[k - 1] = sw ? f[k] : tf;
+            z[k] = sw ? tz : z[k];
+            f[k] = sw ? tf : f[k];
+        }
+    }
+};
+
+__device__ __forceinline__ void set_status(unsigned *status, unsigned bits) {
+    if (bits) atomicOr(status, bits);
+}
+
+// ---------------------------------------------------------------------------
+// workspace layout (host and device agree through this struct)
+// ---------------------------------------------------------------------------
+struct WsLayout {
+    size_t status;      // uint32 status word
+    size_t queue;       // uint32 work-queue head of the fine pass
+    size_t total;       // int64 sum of raw bin counts
+    size_t maxcount;    // int32 largest raw bin count
+    size_t records;     // F x FaceRec
+    size_t face_mesh;   // F x int32
+    size_t counts;      // NB x int32 raw counts
+    size_t eff;         // NB x int32 counts clamped to capacity
+    size_t offsets;     // (NB + 1) x int32
+    size_t cursor;      // NB x int32
+    size_t lists;       // capacity x int32 face ids
+    int64_t nb;         // bins per side
+    int64_t NB;         // N * nb * nb
+    int64_t capacity;   // entries in lists
+    size_t bytes;       // total
+};
+
+}  // namespace mr
+
+// host-side helpers shared by the translation units
+namespace mr_host {
+bool ws_layout(const rast_params *p, int64_t V, int64_t F, mr::WsLayout *L);
+int num_sms();
+}

@@ -1,0 +1,609 @@
+// Forward rasterization kernels for sm_103a.
+//
+// Section 3.2 of the paper ("Rasterizer"): camera transform to NDC, a
+// two-pass approach that first assigns faces to image tiles (bins) and then
+// finds, per pixel, the K nearest faces along z with a priority queue, and the
+// Fragment data of those faces.  Launch sequence of one binned forward:
+//   k_stage     one thread per face: double-float projection, 64-byte face
+//               record, warp-aggregated bin counts
+//   k_scan      one block: clamp counts to capacity, exclusive scan -> offsets
+//   k_fill      one thread per face: warp-aggregated atomic append into lists
+//   k_fine      persistent blocks pull (image, bin) items from a global queue,
+//               stage each bin's face records in shared memory, keep a
+//               register-resident top-K per pixel, write the fragments
+// The plain form (bin_size 0) replaces scan/fill/fine by k_naive, one launch
+// per image, every pixel against every face of its image.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+
+#include "rast_common.cuh"
+#include "rast_internal.h"
+
+namespace mr {
+
+// ---------------------------------------------------------------------------
+// staging
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int find_mesh(const int64_t *first_face, int N, int64_t f) {
+    int lo = 0, hi = N - 1, ans = -1;
+    while (lo <= hi) {
+        int mid = (lo + hi) >> 1;
+        if (first_face[mid] <= f) { ans = mid; lo = mid + 1; } else { hi = mid - 1; }
+    }
+    return ans;
+}
+
+// world -> view -> NDC of one corner, in double-float arithmetic
+__device__ __forceinline__ void project_corner(const float *cam, float px, float py, float pz, df &X, df &Y,
+                                               df &Z) {
+    df d0 = two_sum(px, -cam[9]), d1 = two_sum(py, -cam[10]), d2 = two_sum(pz, -cam[11]);
+    df x = df_add(df_add(df_mul_f(d0, cam[0]), df_mul_f(d1, cam[1])), df_mul_f(d2, cam[2]));
+    df y = df_add(df_add(df_mul_f(d0, cam[3]), df_mul_f(d1, cam[4])), df_mul_f(d2, cam[5]));
+    df z = df_add(df_add(df_mul_f(d0, cam[6]), df_mul_f(d1, cam[7])), df_mul_f(d2, cam[8]));
+    float f = cam[12];
+    X = df_div(df_mul_f(x, f), z);
+    Y = df_div(df_mul_f(y, f), z);
+    Z = z;
+}
+
+__device__ __forceinline__ df df_min(df a, df b) { return (a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo)) ? a : b; }
+__device__ __forceinline__ df df_max(df a, df b) { return (a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo)) ? a : b; }
+
+// Build the record of face f; returns the mesh index or -1 when culled.
+__device__ int stage_face(const StageArgs &a, int64_t f, FaceRec &R) {
+    const float kInf = __int_as_float(0x7f800000);
+    R.a = make_float4(0.f, 0.f, 0.f, 0.f);
+    R.b = make_float4(0.f, 0.f, 0.f, 0.f);
+    R.c = make_float4(kInf, -kInf, kInf, -kInf);
+    R.d = make_float4(0.f, 1.f, 1.f, 1.f);
+    int n = find_mesh(a.first_face, a.N, f);
+    if (n < 0 || f >= a.first_face[n] + a.num_faces[n]) return -1;
+    unsigned bad = 0;
+    int64_t vi[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        vi[i] = a.faces[3 * f + i];
+        if (vi[i] < 0 || vi[i] >= a.V) bad |= MESHRAST_ST_BAD_INDEX;
+    }
+    if (bad) { set_status(a.status, bad); return -1; }
+    const float *cam = a.cams + 16 * n;
+    df X[3], Y[3], Z[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        float px = a.verts[3 * vi[i]], py = a.verts[3 * vi[i] + 1], pz = a.verts[3 * vi[i] + 2];
+        if (!(isfinite(px) && isfinite(py) && isfinite(pz))) bad |= MESHRAST_ST_NONFINITE;
+        project_corner(cam, px, py, pz, X[i], Y[i], Z[i]);
+    }
+    if (bad) { set_status(a.status, bad); return -1; }
+    const float znear = cam[13];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        // z < znear (as a double-float) culls the face
+        if (Z[i].hi < znear || (Z[i].hi == znear && Z[i].lo < 0.f) || !isfinite(Z[i].hi)) return -1;
+        if (!isfinite(X[i].hi) || !isfinite(Y[i].hi)) return -1;
+    }
+    df Ux = df_sub(X[1], X[0]), Uy = df_sub(Y[1], Y[0]);
+    df Wx = df_sub(X[2], X[0]), Wy = df_sub(Y[2], Y[0]);
+    // culling area in double-float (matches an FP64 evaluation to ~1e-14)
+    df Adf = df_sub(df_mul(Ux, Wy), df_mul(Uy, Wx));
+    if (!(fabsf(Adf.hi) >= kCullArea)) return -1;
+    // barycentric normalisation uses the area of the ROUNDED edges, so that the
+    // three fp32 barycentrics describe one (slightly perturbed) triangle
+    float ux = Ux.hi, uy = Uy.hi, wx = Wx.hi, wy = Wy.hi;
+    float p1 = __fmul_rn(uy, wx);
+    float A = __fadd_rn(__fmaf_rn(ux, wy, -p1), __fmaf_rn(-uy, wx, p1));  // ux*wy - uy*wx, Kahan
+    if (A == 0.f) return -1;
+    float r = (a.blur > 0.f) ? sqrtf(a.blur) : 0.f;
+    df xmin = df_min(df_min(X[0], X[1]), X[2]), xmax = df_max(df_max(X[0], X[1]), X[2]);
+    df ymin = df_min(df_min(Y[0], Y[1]), Y[2]), ymax = df_max(df_max(Y[0], Y[1]), Y[2]);
+    R.a = make_float4(X[0].hi, Y[0].hi, X[0].lo, Y[0].lo);
+    R.b = make_float4(ux, uy, wx, wy);
+    R.c = make_float4(df_round_down(df_add(xmin, {-r, 0.f})), df_round_up(df_add(xmax, {r, 0.f})),
+                      df_round_down(df_add(ymin, {-r, 0.f})), df_round_up(df_add(ymax, {r, 0.f})));
+    R.d = make_float4(__fdiv_rn(1.f, A), __fdiv_rn(1.f, Z[0].hi), __fdiv_rn(1.f, Z[1].hi),
+                      __fdiv_rn(1.f, Z[2].hi));
+    return n;
+}
+
+// Columns (or rows) whose fp32 pixel centre lies in [lo, hi]: first index
+// with centre <= hi, last index with centre >= lo (centres decrease with the
+// index).  Exactly the comparisons the fine pass makes.
+__device__ __forceinline__ float pc_hi(int i, int S) {
+    float h, l;
+    pix_coord(i, S, h, l);
+    return h;
+}
+__device__ __forceinline__ void centre_range(float lo, float hi, int S, int &i0, int &i1) {
+    float Sf = (float)S;
+    int a = (int)ceilf(fminf(fmaxf(((Sf - 1.f) - hi * Sf) * 0.5f, -1.f), Sf));
+    a = max(0, min(a, S));
+    while (a > 0 && pc_hi(a - 1, S) <= hi) --a;
+    while (a < S && pc_hi(a, S) > hi) ++a;
+    int b = (int)floorf(fminf(fmaxf(((Sf - 1.f) - lo * Sf) * 0.5f, -1.f), Sf));
+    b = max(-1, min(b, S - 1));
+    while (b < S - 1 && pc_hi(b + 1, S) >= lo) ++b;
+    while (b >= 0 && pc_hi(b, S) < lo) --b;
+    i0 = a;
+    i1 = b;
+}
+
+// Bins (bx0..bx1, by0..by1) of a face: the bin's pixel-centre span meets the
+// inflated bbox.  Empty when bx0 > bx1 or by0 > by1.
+__device__ __forceinline__ void bin_rect(const FaceRec &R, int S, int bin, int &bx0, int &bx1, int &by0,
+                                         int &by1) {
+    if (!(R.c.x <= R.c.y) || !(R.c.z <= R.c.w)) { bx0 = 1; bx1 = 0; by0 = 1; by1 = 0; return; }
+    int c0, c1, r0, r1;
+    centre_range(R.c.x, R.c.y, S, c0, c1);
+    centre_range(R.c.z, R.c.w, S, r0, r1);
+    if (c0 > S - 1 || c1 < 0 || r0 > S - 1 || r1 < 0) { bx0 = 1; bx1 = 0; by0 = 1; by1 = 0; return; }
+    bx0 = c0 / bin;
+    bx1 = c1 / bin;
+    by0 = r0 / bin;
+    by1 = r1 / bin;
+}
+
+__global__ void __launch_bounds__(256) k_stage(StageArgs a) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    FaceRec R;
+    int n = -1;
+    if (f < a.F) {
+        n = stage_face(a, f, R);
+        float4 *dst = reinterpret_cast<float4 *>(a.rec + f);
+        dst[0] = R.a;
+        dst[1] = R.b;
+        dst[2] = R.c;
+        dst[3] = R.d;
+        if (a.face_mesh) a.face_mesh[f] = n;
+    }
+    if (!a.do_count) return;
+    // warp-aggregated bin counting; every lane of the warp takes part
+    int bx0 = 1, bx1 = 0, by0 = 1, by1 = 0;
+    if (n >= 0) bin_rect(R, a.S, a.bin, bx0, bx1, by0, by1);
+    const int nbx = max(0, bx1 - bx0 + 1), nby = max(0, by1 - by0 + 1);
+    const int cnt = nbx * nby;
+    const int wmax = __reduce_max_sync(0xffffffffu, cnt);
+    const int lane = threadIdx.x & 31;
+    for (int i = 0; i < wmax; ++i) {
+        int key = -1;
+        if (i < cnt) key = (n * a.nb + by0 + i / nbx) * a.nb + bx0 + i % nbx;
+        unsigned grp = __match_any_sync(0xffffffffu, key);
+        if (key >= 0 && lane == __ffs(grp) - 1) atomicAdd(a.counts + key, __popc(grp));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// scan: one block; clamps counts, exclusive scan, resets cursors and queue
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_scan(ScanArgs a) {
+    __shared__ int warp_sums[32];
+    __shared__ int carry_s;
+    __shared__ int maxc_s;
+    __shared__ unsigned long long tot_s;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) {
+        carry_s = 0;
+        maxc_s = 0;
+        tot_s = 0ull;
+        *a.queue = 0u;
+        // packed-layout validation of first_face / num_faces
+        unsigned bad = 0;
+        int64_t prev_end = 0;
+        for (int n = 0; n < a.N; ++n) {
+            int64_t lo = a.first_face[n], cnt = a.num_faces[n];
+            if (lo < 0 || cnt < 0 || lo + cnt > a.F || lo < prev_end) bad |= MESHRAST_ST_BAD_MESH_RANGE;
+            prev_end = lo + (cnt > 0 ? cnt : 0);
+        }
+        set_status(a.status, bad);
+    }
+    __syncthreads();
+    bool overflow = false;
+    int local_max = 0;
+    unsigned long long local_tot = 0;
+    for (int64_t base = 0; base < a.NB; base += 1024) {
+        const int64_t b = base + tid;
+        int c = (b < a.NB) ? a.counts[b] : 0;
+        local_max = max(local_max, c);
+        local_tot += (unsigned long long)c;
+        int e = c;
+        if (e > a.max_per_bin) { e = a.max_per_bin; overflow = true; }
+        // block exclusive scan of e
+        int x = e;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) warp_sums[wid] = x;
+        __syncthreads();
+        if (wid == 0) {
+            int s = warp_sums[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, s, o);
+                if (lane >= o) s += y;
+            }
+            warp_sums[lane] = s;
+        }
+        __syncthreads();
+        const int carry = carry_s;
+        int excl = carry + (wid ? warp_sums[wid - 1] : 0) + x - e;
+        if (b < a.NB) {
+            int64_t room = a.capacity - (int64_t)excl;
+            if ((int64_t)e > room) { e = (int)max((int64_t)0, room); overflow = true; }
+            a.offsets[b] = excl;
+            a.eff[b] = e;
+            a.cursor[b] = 0;
+        }
+        __syncthreads();
+        if (tid == 1023) carry_s = (int)min((int64_t)carry + warp_sums[31], (int64_t)0x7fffffff);
+        __syncthreads();
+    }
+    atomicMax(&maxc_s, local_max);
+    atomicAdd(&tot_s, local_tot);
+    if (overflow) set_status(a.status, MESHRAST_ST_BIN_OVERFLOW);
+    __syncthreads();
+    if (tid == 0) {
+        a.offsets[a.NB] = carry_s;
+        *a.maxcount = maxc_s;
+        *a.total = (long long)tot_s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fill: warp-aggregated atomic append into the per-bin lists
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_fill(FillArgs a) {
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int n = -1;
+    FaceRec R;
+    if (f < a.F) {
+        n = a.face_mesh[f];
+        if (n >= 0) {
+            const float4 *src = reinterpret_cast<const float4 *>(a.rec + f);
+            R.c = src[2];
+        }
+    }
+    int bx0 = 1, bx1 = 0, by0 = 1, by1 = 0;
+    if (n >= 0) bin_rect(R, a.S, a.bin, bx0, bx1, by0, by1);
+    const int nbx = max(0, bx1 - bx0 + 1), nby = max(0, by1 - by0 + 1);
+    const int cnt = nbx * nby;
+    const int wmax = __reduce_max_sync(0xffffffffu, cnt);
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int i = 0; i < wmax; ++i) {
+        int key = -1;
+        if (i < cnt) key = (n * a.nb + by0 + i / nbx) * a.nb + bx0 + i % nbx;
+        unsigned grp = __match_any_sync(0xffffffffu, key);
+        int leader = __ffs(grp) - 1;
+        int base = 0;
+        if (key >= 0 && lane == leader) base = atomicAdd(a.cursor + key, __popc(grp));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (key >= 0) {
+            int slot = base + __popc(grp & lt);
+            if (slot < a.eff[key]) a.lists[a.offsets[key] + slot] = (int)f;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// output of one pixel's K fragments
+// ---------------------------------------------------------------------------
+template <int KM>
+__device__ __forceinline__ void write_pixel(const FineOut &o, int64_t pix, int K, const TopK<KM> &tk,
+                                            const FaceRec *rec, const PixC &p, const EvalFlags &fl) {
+    const int64_t s0 = pix * (int64_t)K;
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        if (k >= K) break;
+        const int64_t s = s0 + k;
+        const int f = tk.f[k];
+        if (f == 0x7fffffff) {
+            o.pix_to_face[s] = -1;
+            o.zbuf[s] = -1.f;
+            o.bary[3 * s] = -1.f;
+            o.bary[3 * s + 1] = -1.f;
+            o.bary[3 * s + 2] = -1.f;
+            o.dists[s] = -1.f;
+        } else {
+            FaceRec R;
+            const float4 *src = reinterpret_cast<const float4 *>(rec + f);
+            R.a = __ldg(src);
+            R.b = __ldg(src + 1);
+            R.c = __ldg(src + 2);
+            R.d = __ldg(src + 3);
+            float bp[3], d;
+            face_fragment(R, p, fl, bp, d);
+            o.pix_to_face[s] = f;
+            o.zbuf[s] = tk.z[k];
+            o.bary[3 * s] = bp[0];
+            o.bary[3 * s + 1] = bp[1];
+            o.bary[3 * s + 2] = bp[2];
+            o.dists[s] = d;
+        }
+    }
+}
+
+// large-K variant: per-thread sorted lists in shared memory, [k][thread]
+struct SmemTopK {
+    float *z;
+    int *f;
+    int stride, K;
+    __device__ __forceinline__ void init() {
+        for (int k = 0; k < K; ++k) { z[k * stride] = __int_as_float(0x7f800000); f[k * stride] = 0x7fffffff; }
+    }
+    __device__ __forceinline__ bool admits(float zz, int ff) const {
+        return key_less(zz, ff, z[(K - 1) * stride], f[(K - 1) * stride]);
+    }
+    __device__ __forceinline__ void insert(float zz, int ff) {
+        int k = K - 1;
+        while (k > 0) {
+            float zp = z[(k - 1) * stride];
+            int fp = f[(k - 1) * stride];
+            if (!key_less(zz, ff, zp, fp)) break;
+            z[k * stride] = zp;
+            f[k * stride] = fp;
+            --k;
+        }
+        z[k * stride] = zz;
+        f[k * stride] = ff;
+    }
+};
+
+__device__ __forceinline__ void write_pixel_smem(const FineOut &o, int64_t pix, int K, const SmemTopK &tk,
+                                                 const FaceRec *rec, const PixC &p, const EvalFlags &fl) {
+    const int64_t s0 = pix * (int64_t)K;
+    for (int k = 0; k < K; ++k) {
+        const int64_t s = s0 + k;
+        const int f = tk.f[k * tk.stride];
+        if (f == 0x7fffffff) {
+            o.pix_to_face[s] = -1;
+            o.zbuf[s] = -1.f;
+            o.bary[3 * s] = -1.f;
+            o.bary[3 * s + 1] = -1.f;
+            o.bary[3 * s + 2] = -1.f;
+            o.dists[s] = -1.f;
+        } else {
+            FaceRec R;
+            const float4 *src = reinterpret_cast<const float4 *>(rec + f);
+            R.a = __ldg(src);
+            R.b = __ldg(src + 1);
+            R.c = __ldg(src + 2);
+            R.d = __ldg(src + 3);
+            float bp[3], d;
+            face_fragment(R, p, fl, bp, d);
+            o.pix_to_face[s] = f;
+            o.zbuf[s] = tk.z[k * tk.stride];
+            o.bary[3 * s] = bp[0];
+            o.bary[3 * s + 1] = bp[1];
+            o.bary[3 * s + 2] = bp[2];
+            o.dists[s] = d;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// fine pass: persistent blocks, one bin (bin x bin pixels = block) per item
+// ---------------------------------------------------------------------------
+template <int KM, int BS>
+__global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
+    constexpr int BD = BS * BS;
+    __shared__ FaceRec s_rec[BD];
+    __shared__ int s_id[BD];
+    __shared__ int s_item;
+    extern __shared__ unsigned char s_dyn[];
+    const int tid = threadIdx.x;
+    const int ty = tid / BS, tx = tid % BS;
+    EvalFlags fl = a.fl;
+    const int nb2 = a.nb * a.nb;
+    while (true) {
+        if (tid == 0) s_item = (int)atomicAdd(a.queue, 1u);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= a.items) break;
+        const int n = item / nb2, rem = item - n * nb2;
+        const int by = rem / a.nb, bx = rem - by * a.nb;
+        const int r = by * BS + ty, c = bx * BS + tx;
+        fl.znear = __ldg(a.cams + 16 * n + 13);
+        const bool valid = (r < a.S) && (c < a.S);
+        const PixC p = pixel_centre(r, c, a.S);
+        const int cnt = a.eff[item];
+        const int off = a.offsets[item];
+        TopK<(KM > 0 ? KM : 1)> tk;
+        SmemTopK stk;
+        if constexpr (KM > 0) {
+            tk.init();
+        } else {
+            stk.z = reinterpret_cast<float *>(s_dyn) + tid;
+            stk.f = reinterpret_cast<int *>(s_dyn) + BD * a.K + tid;
+            stk.stride = BD;
+            stk.K = a.K;
+            stk.init();
+        }
+        for (int base = 0; base < cnt; base += BD) {
+            const int j = base + tid;
+            if (j < cnt) {
+                const int fid = a.lists[off + j];
+                s_id[tid] = fid;
+                const float4 *src = reinterpret_cast<const float4 *>(a.rec + fid);
+                float4 *dst = reinterpret_cast<float4 *>(s_rec + tid);
+                dst[0] = __ldg(src);
+                dst[1] = __ldg(src + 1);
+                dst[2] = __ldg(src + 2);
+                dst[3] = __ldg(src + 3);
+            }
+            __syncthreads();
+            const int m = min(BD, cnt - base);
+            if (valid) {
+                for (int jj = 0; jj < m; ++jj) {
+                    const FaceRec R = s_rec[jj];
+                    float z;
+                    if (face_key(R, p, fl, z)) {
+                        const int fid = s_id[jj];
+                        if constexpr (KM > 0) {
+                            if (tk.admits(z, fid)) tk.insert(z, fid);
+                        } else {
+                            if (stk.admits(z, fid)) stk.insert(z, fid);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (valid) {
+            const int64_t pix = ((int64_t)n * a.S + r) * a.S + c;
+            if constexpr (KM > 0) write_pixel(a.out, pix, a.K, tk, a.rec, p, fl);
+            else write_pixel_smem(a.out, pix, a.K, stk, a.rec, p, fl);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// plain form: one launch per image, every pixel against every face
+// ---------------------------------------------------------------------------
+template <int KM>
+__global__ void __launch_bounds__(256) k_naive(NaiveArgs a, int n) {
+    extern __shared__ unsigned char s_dyn[];
+    const int64_t pidx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = pidx < (int64_t)a.S * a.S;
+    const int r = (int)(pidx / a.S), c = (int)(pidx % a.S);
+    const PixC p = pixel_centre(r, c, a.S);
+    EvalFlags fl = a.fl;
+    fl.znear = __ldg(a.cams + 16 * n + 13);
+    int64_t lo = a.first_face[n], hi = lo + a.num_faces[n];
+    lo = max(lo, (int64_t)0);
+    hi = min(hi, a.F);
+    TopK<(KM > 0 ? KM : 1)> tk;
+    SmemTopK stk;
+    if constexpr (KM > 0) {
+        tk.init();
+    } else {
+        stk.z = reinterpret_cast<float *>(s_dyn) + threadIdx.x;
+        stk.f = reinterpret_cast<int *>(s_dyn) + blockDim.x * a.K + threadIdx.x;
+        stk.stride = blockDim.x;
+        stk.K = a.K;
+        stk.init();
+    }
+    if (!valid) return;
+    for (int64_t f = lo; f < hi; ++f) {
+        FaceRec R;
+        const float4 *src = reinterpret_cast<const float4 *>(a.rec + f);
+        R.a = __ldg(src);
+        R.b = __ldg(src + 1);
+        R.c = __ldg(src + 2);
+        R.d = __ldg(src + 3);
+        float z;
+        if (face_key(R, p, fl, z)) {
+            if constexpr (KM > 0) {
+                if (tk.admits(z, (int)f)) tk.insert(z, (int)f);
+            } else {
+                if (stk.admits(z, (int)f)) stk.insert(z, (int)f);
+            }
+        }
+    }
+    const int64_t pix = (int64_t)n * a.S * a.S + pidx;
+    if constexpr (KM > 0) write_pixel(a.out, pix, a.K, tk, a.rec, p, fl);
+    else write_pixel_smem(a.out, pix, a.K, stk, a.rec, p, fl);
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+static int km_for(int K) {
+    if (K <= 1) return 1;
+    if (K <= 2) return 2;
+    if (K <= 4) return 4;
+    if (K <= 8) return 8;
+    if (K <= 16) return 16;
+    return 0;  // shared-memory lists
+}
+
+template <int KM, int BS>
+static cudaError_t launch_fine_t(const FineArgs &a, cudaStream_t st) {
+    constexpr int BD = BS * BS;
+    size_t dyn = (KM > 0) ? 0 : (size_t)BD * a.K * 8;
+    auto kern = k_fine<KM, BS>;
+    static int blocks_per_sm[2] = {-1, -1};
+    int &bps = blocks_per_sm[KM > 0 ? 0 : 1];
+    if (KM == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+        int b = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, BD, dyn);
+        if (e != cudaSuccess) return e;
+        bps = b;
+    } else if (bps < 0) {
+        int b = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, BD, 0);
+        if (e != cudaSuccess) return e;
+        bps = b;
+    }
+    int grid = std::max(1, std::min<int>(a.items, mr_host::num_sms() * std::max(1, bps)));
+    kern<<<grid, BD, dyn, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fine(const FineArgs &a, int bin, cudaStream_t st) {
+    const int km = km_for(a.K);
+#define MR_FINE(KM_)                                              \
+    if (km == KM_) {                                              \
+        if (bin == 8) return launch_fine_t<KM_, 8>(a, st);        \
+        if (bin == 16) return launch_fine_t<KM_, 16>(a, st);      \
+    }
+    MR_FINE(1) MR_FINE(2) MR_FINE(4) MR_FINE(8) MR_FINE(16) MR_FINE(0)
+#undef MR_FINE
+    return cudaErrorInvalidValue;
+}
+
+template <int KM>
+static cudaError_t launch_naive_t(const NaiveArgs &a, int N, cudaStream_t st) {
+    const int BD = 256;
+    size_t dyn = (KM > 0) ? 0 : (size_t)BD * a.K * 8;
+    auto kern = k_naive<KM>;
+    if (KM == 0) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t P = (int64_t)a.S * a.S;
+    const int grid = (int)((P + BD - 1) / BD);
+    for (int n = 0; n < N; ++n) {
+        kern<<<grid, BD, dyn, st>>>(a, n);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_naive(const NaiveArgs &a, int N, cudaStream_t st) {
+    switch (km_for(a.K)) {
+        case 1: return launch_naive_t<1>(a, N, st);
+        case 2: return launch_naive_t<2>(a, N, st);
+        case 4: return launch_naive_t<4>(a, N, st);
+        case 8: return launch_naive_t<8>(a, N, st);
+        case 16: return launch_naive_t<16>(a, N, st);
+        default: return launch_naive_t<0>(a, N, st);
+    }
+}
+
+cudaError_t launch_stage(const StageArgs &a, cudaStream_t st) {
+    if (a.F <= 0) return cudaSuccess;
+    const int grid = (int)((a.F + 255) / 256);
+    k_stage<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const ScanArgs &a, cudaStream_t st) {
+    k_scan<<<1, 1024, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill(const FillArgs &a, cudaStream_t st) {
+    if (a.F <= 0) return cudaSuccess;
+    const int grid = (int)((a.F + 255) / 256);
+    k_fill<<<grid, 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace mr

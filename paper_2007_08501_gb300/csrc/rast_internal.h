@@ -1,0 +1,117 @@
+// Kernel argument blocks and host launchers shared between the translation
+// units of libmeshrast (not part of the public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rast_common.cuh"
+
+namespace mr {
+
+struct StageArgs {
+    const float *verts;
+    int64_t V;
+    const int64_t *faces;
+    int64_t F;
+    const int64_t *first_face;
+    const int64_t *num_faces;
+    int N;
+    const float *cams;
+    float blur;
+    int S, bin, nb, do_count;
+    FaceRec *rec;
+    int *face_mesh;
+    int *counts;
+    unsigned *status;
+};
+
+struct ScanArgs {
+    const int *counts;
+    int *eff, *offsets, *cursor;
+    int64_t NB, capacity;
+    int max_per_bin;
+    unsigned *queue, *status;
+    long long *total;
+    int *maxcount;
+    const int64_t *first_face, *num_faces;
+    int N;
+    int64_t F;
+};
+
+struct FillArgs {
+    const FaceRec *rec;
+    const int *face_mesh;
+    int64_t F;
+    int S, bin, nb;
+    int *cursor;
+    const int *eff, *offsets;
+    int *lists;
+};
+
+struct FineOut {
+    int64_t *pix_to_face;
+    float *zbuf, *bary, *dists;
+};
+
+struct FineArgs {
+    const FaceRec *rec;
+    const float *cams;
+    const int *lists, *eff, *offsets;
+    unsigned *queue;
+    int items, nb, S, K;
+    EvalFlags fl;
+    FineOut out;
+};
+
+struct NaiveArgs {
+    const FaceRec *rec;
+    const float *cams;
+    const int64_t *first_face, *num_faces;
+    int64_t F;
+    int S, K;
+    EvalFlags fl;
+    FineOut out;
+};
+
+struct RastBwdArgs {
+    const FaceRec *rec;
+    const int *face_mesh;
+    const int64_t *faces;
+    const float *verts;
+    const float *cams;
+    const int64_t *pix_to_face;
+    const float *grad_zbuf, *grad_bary, *grad_dists;
+    float *grad_verts;
+    int64_t F, V;
+    int64_t slots;  // N * S * S * K
+    int S, K;
+    EvalFlags fl;
+};
+
+struct BlendArgs {
+    int64_t P;  // pixels
+    int64_t F, V;
+    int K;
+    const int64_t *pix_to_face;
+    const float *zbuf, *bary, *dists;
+    const int64_t *faces;
+    const float *colors;
+    float sigma, gamma, znear, zfar, eps;
+    float bg0, bg1, bg2;
+    int mode;
+    float *image;
+    const float *grad_image;
+    float *grad_zbuf, *grad_bary, *grad_dists, *grad_colors;
+};
+
+cudaError_t launch_stage(const StageArgs &a, cudaStream_t st);
+cudaError_t launch_scan(const ScanArgs &a, cudaStream_t st);
+cudaError_t launch_fill(const FillArgs &a, cudaStream_t st);
+cudaError_t launch_fine(const FineArgs &a, int bin, cudaStream_t st);
+cudaError_t launch_naive(const NaiveArgs &a, int N, cudaStream_t st);
+cudaError_t launch_rast_bwd(const RastBwdArgs &a, cudaStream_t st);
+cudaError_t launch_blend_fwd(const BlendArgs &a, cudaStream_t st);
+cudaError_t launch_blend_bwd(const BlendArgs &a, cudaStream_t st);
+
+}  // namespace mr

@@ -1,0 +1,240 @@
+"""Thin ctypes binding of ``libmeshrast.so`` (C ABI: ``include/meshrast.h``).
+
+Argument marshalling only: every function takes torch CUDA tensors (used as
+device memory), checks dtype/device/contiguity, and passes raw pointers and
+the current CUDA stream to the entry point of the same name.  All arithmetic
+happens in the library's kernels.  There is no CPU fallback: a missing or
+unloadable library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+MESHRAST_OK = 0
+MESHRAST_ERR_INVALID_ARG = -1
+MESHRAST_ERR_WORKSPACE = -2
+MESHRAST_ERR_UNSUPPORTED = -3
+MESHRAST_ERR_CUDA = -4
+
+ST_BIN_OVERFLOW = 1
+ST_BAD_INDEX = 2
+ST_BAD_MESH_RANGE = 4
+ST_NONFINITE = 8
+
+BLEND_SIL = 0
+BLEND_RGB = 1
+
+EXPORTED = ("rast_workspace_bytes", "rast_mesh_fwd", "rast_mesh_bwd", "blend_fwd", "blend_bwd",
+            "rast_query_status", "rast_bin_occupancy", "rast_strerror")
+
+
+class rast_params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("image_size", ctypes.c_int32), ("faces_per_pixel", ctypes.c_int32),
+                ("bin_size", ctypes.c_int32), ("max_faces_per_bin", ctypes.c_int32),
+                ("perspective_correct", ctypes.c_int32), ("clip_barycentric_coords", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("blur_radius", ctypes.c_float), ("reserved_f", ctypes.c_float),
+                ("max_bin_entries", ctypes.c_int64)]
+
+
+class blend_params(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_float), ("gamma", ctypes.c_float), ("znear", ctypes.c_float),
+                ("zfar", ctypes.c_float), ("bg", ctypes.c_float * 3), ("eps", ctypes.c_float),
+                ("mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class MeshRastError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Open the library (optionally building it first).  Raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise MeshRastError("libmeshrast.so is not built (run __graft_entry__.build()); "
+                                "there is no fallback implementation")
+        _build.build()
+    L = ctypes.CDLL(path)
+    vp, i64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t
+    P = ctypes.POINTER(rast_params)
+    B = ctypes.POINTER(blend_params)
+    L.rast_workspace_bytes.argtypes = [P, i64, i64]
+    L.rast_workspace_bytes.restype = sz
+    L.rast_mesh_fwd.argtypes = [P, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.rast_mesh_fwd.restype = ctypes.c_int
+    L.rast_mesh_bwd.argtypes = [P, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.rast_mesh_bwd.restype = ctypes.c_int
+    L.blend_fwd.argtypes = [B, i64, i64, i64, vp, vp, vp, vp, vp, i64, vp, i64, vp, vp]
+    L.blend_fwd.restype = ctypes.c_int
+    L.blend_bwd.argtypes = [B, i64, i64, i64, vp, vp, vp, vp, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp]
+    L.blend_bwd.restype = ctypes.c_int
+    L.rast_query_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), vp]
+    L.rast_query_status.restype = ctypes.c_int
+    L.rast_bin_occupancy.argtypes = [P, i64, i64, vp, ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(ctypes.c_int64), vp]
+    L.rast_bin_occupancy.restype = ctypes.c_int
+    L.rast_strerror.argtypes = [ctypes.c_int]
+    L.rast_strerror.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != MESHRAST_OK:
+        msg = load().rast_strerror(rc).decode()
+        raise MeshRastError("%s failed: %s (%d)" % (what, msg, rc))
+
+
+def _ptr(t, dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise MeshRastError("%s must be a CUDA tensor" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise MeshRastError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise MeshRastError("%s must be contiguous" % name)
+    return t.data_ptr() if t.numel() > 0 else None
+
+
+def _stream(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return s.cuda_stream
+
+
+def make_rast_params(N, image_size, K, blur_radius=0.0, bin_size=16, max_faces_per_bin=1024,
+                     perspective_correct=True, clip_barycentric_coords=False, max_bin_entries=0):
+    p = rast_params()
+    p.N, p.image_size, p.faces_per_pixel = int(N), int(image_size), int(K)
+    p.bin_size, p.max_faces_per_bin = int(bin_size), int(max_faces_per_bin)
+    p.perspective_correct = int(bool(perspective_correct))
+    p.clip_barycentric_coords = int(bool(clip_barycentric_coords))
+    p.reserved = 0
+    p.blur_radius = float(blur_radius)
+    p.reserved_f = 0.0
+    p.max_bin_entries = int(max_bin_entries)
+    return p
+
+
+def make_blend_params(sigma=1e-4, gamma=1e-4, znear=0.1, zfar=100.0, bg=(1.0, 1.0, 1.0), eps=1e-10,
+                      mode=BLEND_RGB):
+    b = blend_params()
+    b.sigma, b.gamma, b.znear, b.zfar = float(sigma), float(gamma), float(znear), float(zfar)
+    b.bg[0], b.bg[1], b.bg[2] = (float(x) for x in bg)
+    b.eps = float(eps)
+    b.mode = int(mode)
+    b.reserved = 0
+    return b
+
+
+# ---------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+def rast_workspace_bytes(p: rast_params, V: int, F: int) -> int:
+    n = load().rast_workspace_bytes(ctypes.byref(p), int(V), int(F))
+    if n == 0:
+        raise MeshRastError("rast_workspace_bytes: invalid or unsupported parameters")
+    return int(n)
+
+
+def rast_mesh_fwd(p, verts, faces, first_face, num_faces, cams, pix_to_face, zbuf, bary, dists, workspace,
+                  stream=None):
+    rc = load().rast_mesh_fwd(
+        ctypes.byref(p), _ptr(verts, torch.float32, "verts"), verts.shape[0],
+        _ptr(faces, torch.int64, "faces"), faces.shape[0],
+        _ptr(first_face, torch.int64, "first_face"), _ptr(num_faces, torch.int64, "num_faces"),
+        _ptr(cams, torch.float32, "cams"),
+        _ptr(pix_to_face, torch.int64, "pix_to_face"), _ptr(zbuf, torch.float32, "zbuf"),
+        _ptr(bary, torch.float32, "bary"), _ptr(dists, torch.float32, "dists"),
+        _ptr(workspace, None, "workspace"), workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "rast_mesh_fwd")
+
+
+def rast_mesh_bwd(p, verts, faces, first_face, num_faces, cams, pix_to_face, grad_zbuf, grad_bary, grad_dists,
+                  grad_verts, workspace, stream=None):
+    rc = load().rast_mesh_bwd(
+        ctypes.byref(p), _ptr(verts, torch.float32, "verts"), verts.shape[0],
+        _ptr(faces, torch.int64, "faces"), faces.shape[0],
+        _ptr(first_face, torch.int64, "first_face"), _ptr(num_faces, torch.int64, "num_faces"),
+        _ptr(cams, torch.float32, "cams"), _ptr(pix_to_face, torch.int64, "pix_to_face"),
+        _ptr(grad_zbuf, torch.float32, "grad_zbuf"), _ptr(grad_bary, torch.float32, "grad_bary"),
+        _ptr(grad_dists, torch.float32, "grad_dists"), _ptr(grad_verts, torch.float32, "grad_verts"),
+        _ptr(workspace, None, "workspace"), workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "rast_mesh_bwd")
+
+
+def blend_fwd(bp, N, S, K, pix_to_face, zbuf, bary, dists, faces, vert_colors, image, stream=None):
+    F = faces.shape[0] if faces is not None else 0
+    V = vert_colors.shape[0] if vert_colors is not None else 0
+    rc = load().blend_fwd(ctypes.byref(bp), int(N), int(S), int(K), _ptr(pix_to_face, torch.int64, "pix_to_face"),
+                          _ptr(zbuf, torch.float32, "zbuf"), _ptr(bary, torch.float32, "bary"),
+                          _ptr(dists, torch.float32, "dists"), _ptr(faces, torch.int64, "faces"), F,
+                          _ptr(vert_colors, torch.float32, "vert_colors"), V, _ptr(image, torch.float32, "image"),
+                          _stream(stream))
+    _check(rc, "blend_fwd")
+
+
+def blend_bwd(bp, N, S, K, pix_to_face, zbuf, bary, dists, faces, vert_colors, grad_image, grad_zbuf, grad_bary,
+              grad_dists, grad_vert_colors, stream=None):
+    F = faces.shape[0] if faces is not None else 0
+    V = vert_colors.shape[0] if vert_colors is not None else 0
+    rc = load().blend_bwd(ctypes.byref(bp), int(N), int(S), int(K), _ptr(pix_to_face, torch.int64, "pix_to_face"),
+                          _ptr(zbuf, torch.float32, "zbuf"), _ptr(bary, torch.float32, "bary"),
+                          _ptr(dists, torch.float32, "dists"), _ptr(faces, torch.int64, "faces"), F,
+                          _ptr(vert_colors, torch.float32, "vert_colors"), V,
+                          _ptr(grad_image, torch.float32, "grad_image"), _ptr(grad_zbuf, torch.float32, "grad_zbuf"),
+                          _ptr(grad_bary, torch.float32, "grad_bary"), _ptr(grad_dists, torch.float32, "grad_dists"),
+                          _ptr(grad_vert_colors, torch.float32, "grad_vert_colors"), _stream(stream))
+    _check(rc, "blend_bwd")
+
+
+def rast_query_status(workspace, stream=None) -> int:
+    v = ctypes.c_uint32(0)
+    _check(load().rast_query_status(_ptr(workspace, None, "workspace"), ctypes.byref(v), _stream(stream)),
+           "rast_query_status")
+    return int(v.value)
+
+
+def rast_bin_occupancy(p, V, F, workspace, stream=None):
+    mc = ctypes.c_int32(0)
+    tot = ctypes.c_int64(0)
+    _check(load().rast_bin_occupancy(ctypes.byref(p), int(V), int(F), _ptr(workspace, None, "workspace"),
+                                     ctypes.byref(mc), ctypes.byref(tot), _stream(stream)), "rast_bin_occupancy")
+    return int(mc.value), int(tot.value)
+
+
+def rast_strerror(code: int) -> str:
+    return load().rast_strerror(int(code)).decode()
+
+
+# ---------------------------------------------------------------------------
+# allocation helpers (torch is the device-memory allocator)
+# ---------------------------------------------------------------------------
+def alloc_workspace(p, V, F, device="cuda"):
+    n = rast_workspace_bytes(p, V, F)
+    # uint8 storage from the caching allocator is 512-byte aligned
+    ws = torch.empty(n, dtype=torch.uint8, device=device)
+    assert ws.data_ptr() % 256 == 0
+    return ws
+
+
+def alloc_fragments(N, S, K, device="cuda"):
+    return (torch.empty((N, S, S, K), dtype=torch.int64, device=device),
+            torch.empty((N, S, S, K), dtype=torch.float32, device=device),
+            torch.empty((N, S, S, K, 3), dtype=torch.float32, device=device),
+            torch.empty((N, S, S, K), dtype=torch.float32, device=device))

@@ -1,0 +1,85 @@
+"""Helpers for the GPU parity tests: run the C-ABI path on a packed batch and
+compare it with the FP64 oracle on the same inputs."""
+import numpy as np
+import torch
+
+import oracle
+from paper_2007_08501_gb300 import ops
+
+DEV = "cuda"
+
+
+def to_dev(b):
+    """numpy batch (dict or MeshBatch) -> CUDA tensors"""
+    g = (lambda k: b[k]) if isinstance(b, dict) else (lambda k: getattr(b, k))
+    return dict(verts=torch.from_numpy(np.ascontiguousarray(g("verts"), np.float32)).to(DEV),
+                faces=torch.from_numpy(np.ascontiguousarray(g("faces"), np.int64)).to(DEV),
+                first_face=torch.from_numpy(np.ascontiguousarray(g("first_face"), np.int64)).to(DEV),
+                num_faces=torch.from_numpy(np.ascontiguousarray(g("num_faces"), np.int64)).to(DEV),
+                cams=torch.from_numpy(np.ascontiguousarray(g("cams"), np.float32)).to(DEV))
+
+
+def oracle_mesh(b):
+    """The oracle sees exactly the fp32 values the GPU sees, upcast."""
+    g = (lambda k: b[k]) if isinstance(b, dict) else (lambda k: getattr(b, k))
+    return oracle.Mesh(np.asarray(g("verts"), np.float32), g("faces"), g("first_face"), g("num_faces"),
+                       np.asarray(g("cams"), np.float32))
+
+
+def gpu_fwd(d, S, K, blur, bin_size=16, persp=True, clip=False, max_faces_per_bin=4096, max_bin_entries=0):
+    N = d["first_face"].shape[0]
+    p = ops.make_rast_params(N, S, K, np.float32(blur), bin_size, max_faces_per_bin, persp, clip, max_bin_entries)
+    ws = ops.alloc_workspace(p, d["verts"].shape[0], d["faces"].shape[0])
+    p2f, zb, ba, di = ops.alloc_fragments(N, S, K)
+    ops.rast_mesh_fwd(p, d["verts"], d["faces"], d["first_face"], d["num_faces"], d["cams"], p2f, zb, ba, di, ws)
+    status = ops.rast_query_status(ws)
+    return (p2f, zb, ba, di), status, p, ws
+
+
+def np_frags(fr):
+    return [t.detach().cpu().numpy() for t in fr]
+
+
+def compare_frags(gpu, orc, amb, atol=1e-5):
+    """pix_to_face bit-exact on unambiguous pixels; zbuf, bary, dists within atol
+    wherever the face ids agree.  Returns (#ambiguous, #mismatched unambiguous)."""
+    gp, gz, gb, gd = [np.asarray(x) for x in gpu]
+    op, oz, ob, od = orc
+    P, K = op.shape
+    gp = gp.reshape(P, K)
+    gz = gz.reshape(P, K)
+    gb = gb.reshape(P, K, 3)
+    gd = gd.reshape(P, K)
+    ok = amb == 0
+    bad = np.nonzero(np.any(gp[ok] != op[ok], axis=1))[0]
+    same = gp == op
+    # empty slots carry exactly -1
+    empty = op < 0
+    assert np.all(gz[empty & same] == -1) and np.all(gd[empty & same] == -1)
+    v = same & ~empty
+    if v.any():
+        ez = np.max(np.abs(gz[v] - oz[v]))
+        eb = np.max(np.abs(gb[v] - ob[v]))
+        ed = np.max(np.abs(gd[v] - od[v]))
+        assert ez <= atol, ("zbuf", ez)
+        assert eb <= atol, ("bary", eb)
+        assert ed <= atol, ("dists", ed)
+    return int((~ok).sum()), int(bad.size)
+
+
+def pick(fr, pixels, S):
+    """select (n, r, c) pixels out of full (N,S,S,K...) fragments"""
+    n, r, c = pixels[:, 0], pixels[:, 1], pixels[:, 2]
+    return [np.asarray(x)[n, r, c] for x in fr]
+
+
+def grad_close(g, ref, rel=1e-4):
+    """per component |g - ref| <= rel * max(|ref|, 1e-2 rms(ref)), and the global
+    relative 2-norm error <= rel.  Returns (worst ratio, global rel err)."""
+    g = np.asarray(g, np.float64)
+    ref = np.asarray(ref, np.float64)
+    rms = np.sqrt(np.mean(ref ** 2)) if ref.size else 0.0
+    den = np.maximum(np.abs(ref), 1e-2 * rms) + 1e-30
+    worst = float(np.max(np.abs(g - ref) / den)) / rel if ref.size else 0.0
+    glob = float(np.linalg.norm(g - ref) / (np.linalg.norm(ref) + 1e-30))
+    return worst, glob

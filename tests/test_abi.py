@@ -1,0 +1,71 @@
+"""The C ABI library builds for sm_103a, loads, and exports every symbol that
+include/*.h declares; the binding's structs match the header's layout.
+No GPU is needed (no compute calls)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        txt = open(h).read()
+        names |= set(re.findall(r"MESHRAST_API\s+[\w\s\*]+?\b(\w+)\s*\(", txt))
+    return names
+
+
+def test_header_declares_the_entry_points():
+    names = _declared()
+    for n in ("rast_mesh_fwd", "rast_mesh_bwd", "blend_fwd", "blend_bwd", "rast_workspace_bytes",
+              "rast_query_status", "rast_strerror"):
+        assert n in names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2007_08501_gb300 import build
+    build.build()
+    return ctypes.CDLL(build.LIB)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2007_08501_gb300 import ops
+    for n in _declared():
+        assert hasattr(lib, n), n
+    assert set(ops.EXPORTED) == _declared()
+
+
+def test_pure_host_entry_points(lib):
+    from paper_2007_08501_gb300 import ops
+    ops._lib = None
+    L = ops.load()
+    assert L.rast_strerror(-2).decode().startswith("workspace")
+    p = ops.make_rast_params(2, 64, 4, 1e-3, 16, 128)
+    n = L.rast_workspace_bytes(ctypes.byref(p), 100, 200)
+    assert n > 0 and n % 256 == 0
+    # a larger batch never needs less workspace
+    assert L.rast_workspace_bytes(ctypes.byref(p), 100, 400) >= n
+    bad = ops.make_rast_params(2, 64, 65, 1e-3, 16, 128)       # K > 64
+    assert L.rast_workspace_bytes(ctypes.byref(bad), 100, 200) == 0
+    bad = ops.make_rast_params(2, 64, 4, 1e-3, 12, 128)        # bin size 12
+    assert L.rast_workspace_bytes(ctypes.byref(bad), 100, 200) == 0
+    bad = ops.make_rast_params(2, 64, 4, -1.0, 16, 128)        # negative blur
+    assert L.rast_workspace_bytes(ctypes.byref(bad), 100, 200) == 0
+    # argument errors are reported before anything touches a device
+    assert L.rast_mesh_fwd(ctypes.byref(bad), None, 0, None, 0, None, None, None, None, None, None, None,
+                           None, 0, None) == ops.MESHRAST_ERR_INVALID_ARG
+    bp = ops.make_blend_params(sigma=-1.0)
+    assert L.blend_fwd(ctypes.byref(bp), 1, 4, 1, None, None, None, None, None, 0, None, 0, None,
+                       None) == ops.MESHRAST_ERR_INVALID_ARG
+
+
+def test_struct_layouts_match_header():
+    from paper_2007_08501_gb300 import ops
+    assert ctypes.sizeof(ops.rast_params) == 48
+    assert ops.rast_params.max_bin_entries.offset == 40
+    assert ctypes.sizeof(ops.blend_params) == 40

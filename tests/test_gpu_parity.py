@@ -1,0 +1,234 @@
+"""CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Fragments: pix_to_face bit-exact on every pixel whose depth / edge / blur /
+cull margins exceed 1e-6 (the rest are counted); zbuf, bary and dists within
+1e-5 absolute.  Blends within 1e-5.  Gradients within 1e-4 relative of the
+oracle adjoint conditioned on the same face selection.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from _gpu import compare_frags, gpu_fwd, grad_close, np_frags, oracle_mesh, pick, to_dev
+from _scenes import ndc_triangle, random_small_mesh, scene
+from paper_2007_08501_gb300 import ops, workloads
+from paper_2007_08501_gb300.workloads import BLUR_SIGMA_1E4
+
+pytestmark = pytest.mark.gpu
+
+BLUR = float(np.float32(BLUR_SIGMA_1E4))
+
+
+def _full_check(batch, S, K, blur, bin_size, persp=True, clip=False, max_amb_frac=0.02):
+    d = to_dev(batch)
+    fr, status, _, _ = gpu_fwd(d, S, K, blur, bin_size, persp, clip)
+    assert status == 0
+    m = oracle_mesh(batch)
+    orc = oracle.rasterize(m, S, K, blur, persp, clip)
+    amb = oracle.margins(m, S, K, blur, persp, clip) & oracle.FWD_AMBIGUOUS
+    n_amb, n_bad = compare_frags(np_frags(fr), orc, amb)
+    assert n_bad == 0
+    assert n_amb <= max_amb_frac * amb.size
+    return fr
+
+
+def test_config0_plain_form_full_image():
+    w = workloads.workload(0)
+    _full_check(w.batch, w.image_size, w.K, w.blur_radius, bin_size=0)
+
+
+@pytest.mark.parametrize("bin_size", [8, 16])
+def test_config0_binned_full_image(bin_size):
+    w = workloads.workload(0)
+    _full_check(w.batch, w.image_size, w.K, 0.0, bin_size)
+
+
+@pytest.mark.parametrize("S,K,blur,bin_size,persp,clip", [
+    (76, 4, BLUR, 16, True, True),     # ragged tail: 76 = 4*16 + 12
+    (76, 3, BLUR, 8, True, False),     # K not a power of two, ragged 76 = 9*8 + 4
+    (64, 1, 0.0, 16, False, False),    # hard, affine barycentrics
+    (40, 8, BLUR, 8, False, True),
+])
+def test_small_multi_mesh_full_image(S, K, blur, bin_size, persp, clip):
+    b = workloads.sphere_batch([3, 2, 3], 0.05, seed_base=77)
+    _full_check(b, S, K, blur, bin_size, persp, clip)
+
+
+def test_large_k_shared_memory_path():
+    b = workloads.sphere_batch([3, 3], 0.05, seed_base=91)
+    for bs in (0, 8):
+        _full_check(b, 48, 50, BLUR, bs, True, True)
+
+
+@pytest.mark.parametrize("K", [2, 16, 20])
+def test_binned_equals_plain_bitwise(K):
+    b = workloads.sphere_batch([4, 3, 5], 0.05, seed_base=5)
+    d = to_dev(b)
+    S = 100
+    ref = np_frags(gpu_fwd(d, S, K, BLUR, 0, True, True)[0])
+    for bs in (8, 16):
+        got = np_frags(gpu_fwd(d, S, K, BLUR, bs, True, True)[0])
+        for x, y in zip(ref, got):
+            np.testing.assert_array_equal(x, y)
+
+
+def test_config1_sampled_pixels_at_full_size():
+    w = workloads.workload(1)
+    d = to_dev(w.batch)
+    fr, status, p, ws = gpu_fwd(d, w.image_size, w.K, np.float32(w.blur_radius), 16, True, True)
+    assert status == 0
+    px = workloads.sample_pixels(w.batch.N, w.image_size, 256, seed=1)
+    m = oracle_mesh(w.batch)
+    orc = oracle.rasterize(m, w.image_size, w.K, np.float32(w.blur_radius), True, True, pixels=px)
+    amb = oracle.margins(m, w.image_size, w.K, np.float32(w.blur_radius), True, True, pixels=px) \
+        & oracle.FWD_AMBIGUOUS
+    n_amb, n_bad = compare_frags(pick(np_frags(fr), px, w.image_size), orc, amb)
+    assert n_bad == 0
+    # invariants at every pixel: sorted depths, valid slots first, bary sums to 1
+    p2f, zb, ba, di = np_frags(fr)
+    valid = p2f >= 0
+    assert np.all(valid[..., 1:] <= valid[..., :-1])
+    z = np.where(valid, zb, np.inf)
+    assert np.all(np.diff(z, axis=-1)[valid[..., 1:]] >= 0)
+    assert np.allclose(ba[valid].sum(-1), 1.0, atol=1e-5)
+    assert np.all(di[valid] < np.float32(w.blur_radius))
+
+
+def test_blend_matches_oracle_on_same_fragments():
+    w = workloads.workload(1)
+    d = to_dev(w.batch)
+    fr, _, _, _ = gpu_fwd(d, w.image_size, w.K, np.float32(w.blur_radius), 16, True, True)
+    p2f, zb, ba, di = fr
+    faces = d["faces"]
+    colors = torch.from_numpy(w.batch.colors).cuda()
+    N, S, K = w.batch.N, w.image_size, w.K
+    for mode in (ops.BLEND_SIL, ops.BLEND_RGB):
+        bp = ops.make_blend_params(w.sigma, w.gamma, w.znear, w.zfar, (1.0, 1.0, 1.0), 1e-10, mode)
+        img = torch.empty((N, S, S, 4), device="cuda")
+        ops.blend_fwd(bp, N, S, K, p2f, zb, ba, di, faces, colors, img)
+        fn = [x.cpu().numpy() for x in (p2f, zb, ba, di)]
+        ref = oracle.blend_fwd(*fn, w.batch.faces, w.batch.colors, float(np.float32(w.sigma)),
+                               float(np.float32(w.gamma)), float(np.float32(w.znear)), float(np.float32(w.zfar)),
+                               mode=mode)
+        err = np.max(np.abs(img.cpu().numpy() - ref))
+        assert err <= 1e-5, err
+        # backward: same fragments, same upstream gradient
+        g = torch.from_numpy(workloads.upstream_grad(N, S, 3)).cuda()
+        gd = torch.empty_like(di)
+        gz = torch.empty_like(zb) if mode else None
+        gb = torch.empty_like(ba) if mode else None
+        gc = torch.empty_like(colors) if mode else None
+        ops.blend_bwd(bp, N, S, K, p2f, zb, ba, di, faces, colors, g, gz, gb, gd, gc)
+        rz, rb, rd, rc = oracle.blend_bwd(*fn, w.batch.faces, w.batch.colors, g.cpu().numpy(),
+                                          float(np.float32(w.sigma)), float(np.float32(w.gamma)),
+                                          float(np.float32(w.znear)), float(np.float32(w.zfar)), mode=mode)
+        worst, glob = grad_close(gd.cpu().numpy(), rd)
+        assert worst <= 1 and glob <= 1e-4, (worst, glob)
+        if mode:
+            for a, r in ((gz, rz), (gb, rb), (gc, rc)):
+                worst, glob = grad_close(a.cpu().numpy(), r)
+                assert worst <= 1 and glob <= 1e-4, (worst, glob)
+
+
+def _rast_bwd_check(batch, S, K, blur, bin_size, persp, clip, seed=0):
+    d = to_dev(batch)
+    fr, _, p, ws = gpu_fwd(d, S, K, blur, bin_size, persp, clip)
+    p2f = fr[0]
+    N = batch["first_face"].shape[0] if isinstance(batch, dict) else batch.N
+    m = oracle_mesh(batch)
+    amb = oracle.margins(m, S, K, blur, persp, clip) & oracle.GRAD_AMBIGUOUS
+    rng = np.random.default_rng(seed)
+    P = N * S * S
+    gz = rng.normal(size=(P, K)).astype(np.float32)
+    gb = rng.normal(size=(P, K, 3)).astype(np.float32)
+    gd = (rng.normal(size=(P, K)) * 1e3).astype(np.float32)
+    for g in (gz, gb, gd):
+        g[amb != 0] = 0
+    gv = torch.empty_like(d["verts"])
+    T = lambda a: torch.from_numpy(a).cuda().reshape(*p2f.shape, *a.shape[2:])
+    ops.rast_mesh_bwd(p, d["verts"], d["faces"], d["first_face"], d["num_faces"], d["cams"], p2f, T(gz), T(gb),
+                      T(gd), gv, ws)
+    ref = oracle.rast_bwd(m, S, K, p2f.cpu().numpy().reshape(P, K), gz, gb, gd, blur, persp, clip)
+    worst, glob = grad_close(gv.cpu().numpy(), ref)
+    assert worst <= 1 and glob <= 1e-4, (worst, glob)
+
+
+@pytest.mark.parametrize("persp,clip,blur", [(True, True, BLUR), (True, False, BLUR), (False, True, BLUR),
+                                             (True, False, 0.0)])
+def test_rast_bwd_matches_oracle_adjoint(persp, clip, blur):
+    b = workloads.sphere_batch([3, 2], 0.05, seed_base=123)
+    _rast_bwd_check(b, 48, 4, blur, 16, persp, clip)
+
+
+def test_rast_bwd_shared_vertices_across_images():
+    # two images of ONE mesh: both images' faces index the same vertices
+    v, f = workloads.displaced_sphere(2, 0.05, np.random.default_rng(3))
+    cams = [workloads.look_at_camera(2.7, 10.0, 30.0), workloads.look_at_camera(2.7, -20.0, 200.0)]
+    b = dict(verts=v.astype(np.float32), faces=np.concatenate([f, f]).astype(np.int64),
+             first_face=np.array([0, f.shape[0]], np.int64), num_faces=np.array([f.shape[0]] * 2, np.int64),
+             cams=np.stack(cams))
+    _rast_bwd_check(b, 40, 3, BLUR, 8, True, True)
+
+
+def test_status_bits_and_degenerate_inputs():
+    b = workloads.sphere_batch([2, 2], 0.05, seed_base=9)
+    # bad vertex index
+    bb = dict(verts=b.verts, faces=b.faces.copy(), first_face=b.first_face, num_faces=b.num_faces, cams=b.cams)
+    bb["faces"][3, 1] = b.V + 5
+    _, st, _, _ = gpu_fwd(to_dev(bb), 32, 2, BLUR, 16)
+    assert st & ops.ST_BAD_INDEX
+    # non-finite vertex
+    bb = dict(verts=b.verts.copy(), faces=b.faces, first_face=b.first_face, num_faces=b.num_faces, cams=b.cams)
+    bb["verts"][4, 0] = np.nan
+    fr, st, _, _ = gpu_fwd(to_dev(bb), 32, 2, BLUR, 16)
+    assert st & ops.ST_NONFINITE
+    assert np.isfinite(np_frags(fr)[1]).all()
+    # bin overflow with a tiny capacity: error bit, no fault
+    _, st, _, _ = gpu_fwd(to_dev(b), 64, 2, BLUR, 16, max_faces_per_bin=2)
+    assert st & ops.ST_BIN_OVERFLOW
+    _, st, _, _ = gpu_fwd(to_dev(b), 64, 2, BLUR, 16, max_faces_per_bin=4096, max_bin_entries=10)
+    assert st & ops.ST_BIN_OVERFLOW
+    # bad packing
+    bb = dict(verts=b.verts, faces=b.faces, first_face=np.array([0, 10], np.int64),
+              num_faces=np.array([20, 20], np.int64), cams=b.cams)
+    _, st, _, _ = gpu_fwd(to_dev(bb), 32, 2, BLUR, 16)
+    assert st & ops.ST_BAD_MESH_RANGE
+
+
+def test_empty_batches_and_zero_face_meshes():
+    b = workloads.sphere_batch([2], 0.05, seed_base=4)
+    two = dict(verts=b.verts, faces=b.faces, first_face=np.array([0, 0], np.int64),
+               num_faces=np.array([0, b.F], np.int64), cams=np.concatenate([b.cams, b.cams]))
+    fr, st, _, _ = gpu_fwd(to_dev(two), 32, 2, BLUR, 16)
+    assert st == 0
+    p2f = np_frags(fr)[0]
+    assert (p2f[0] == -1).all() and (p2f[1] >= 0).any()
+    none = dict(verts=b.verts, faces=np.zeros((0, 3), np.int64), first_face=np.array([0], np.int64),
+                num_faces=np.array([0], np.int64), cams=b.cams)
+    fr, st, _, _ = gpu_fwd(to_dev(none), 16, 1, 0.0, 8)
+    assert (np_frags(fr)[0] == -1).all()
+    # N = 0: nothing to do, still a valid call
+    zero = dict(verts=b.verts, faces=b.faces, first_face=np.zeros(0, np.int64), num_faces=np.zeros(0, np.int64),
+                cams=np.zeros((0, 16), np.float32))
+    gpu_fwd(to_dev(zero), 16, 1, 0.0, 8)
+
+
+def test_sub_pixel_faces_keep_bary_precision():
+    # a face spanning ~2 pixels at 1024^2 placed away from the origin: fp32
+    # projection alone would lose ~1e-4 in the barycentrics
+    S = 1024
+    c = lambda i: 1.0 - (2.0 * i + 1.0) / S
+    tri = ndc_triangle((c(700.3), c(300.2)), (c(702.9), c(300.6)), (c(701.1), c(302.8)), 2.7)
+    tri = tri.astype(np.float32)
+    sc = scene([tri])
+    sc["cams"] = sc["cams"].astype(np.float32)
+    d = to_dev(sc)
+    fr, st, _, _ = gpu_fwd(d, S, 1, 0.0, 16, True, False)
+    px = np.array([[0, r, cc] for r in range(298, 306) for cc in range(698, 706)])
+    m = oracle_mesh(sc)
+    orc = oracle.rasterize(m, S, 1, 0.0, True, False, pixels=px)
+    amb = oracle.margins(m, S, 1, 0.0, True, False, pixels=px) & oracle.FWD_AMBIGUOUS
+    n_amb, n_bad = compare_frags(pick(np_frags(fr), px, S), orc, amb, atol=2e-6)
+    assert n_bad == 0
+    assert (orc[0] >= 0).sum() >= 2
