@@ -89,7 +89,7 @@ extern "C" {
 
 /* Rasterizer parameters (Section 3.2 "Rasterizer"). */
 typedef struct {
-    int32_t N;                    /* images (= meshes) in the batch, >= 0 */
+    int32_t N;                    /* images (= meshes) in the batch, 0 .. 65535 */
     int32_t image_size;           /* S, 1 .. 8192 */
     int32_t faces_per_pixel;      /* K, 1 .. 64 */
     int32_t bin_size;             /* 0: plain form, one unbinned launch per image;

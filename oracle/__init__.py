@@ -38,27 +38,65 @@ def build(force: bool = False) -> str:
     return _LIB_PATH
 
 
+def _open(path):
+    L = ctypes.CDLL(path)
+    L.orc_rasterize.argtypes = [_f64p, _i64, _i64p, _i64, _i64p, _i64p, _i64, _f64p, _i64, _i64,
+                                _dbl, _int, _int, _i64p, _i64, _i64p, _f64p, _f64p, _f64p]
+    L.orc_pixel_candidates.argtypes = [_f64p, _i64, _i64p, _i64, _i64p, _i64p, _f64p, _i64, _dbl,
+                                       _int, _int, _i64, _i64, _i64, _i64p, _f64p, _i64]
+    L.orc_pixel_candidates.restype = _i64
+    L.orc_margins.argtypes = [_f64p, _i64, _i64p, _i64, _i64p, _i64p, _i64, _f64p, _i64, _i64,
+                              _dbl, _int, _int, _i64p, _i64, _dbl, _u8p]
+    L.orc_bins.argtypes = [_f64p, _i64, _i64p, _i64, _i64p, _i64p, _i64, _f64p, _i64, _i64, _dbl,
+                           _dbl, _i64p, _i64p, _i64p, _u8p]
+    L.orc_blend_fwd.argtypes = [_i64, _i64, _i64p, _f64p, _f64p, _f64p, _i64p, _f64p, _dbl, _dbl,
+                                _dbl, _dbl, _f64p, _int, _dbl, _f64p]
+    L.orc_blend_bwd.argtypes = [_i64, _i64, _i64p, _f64p, _f64p, _f64p, _i64p, _f64p, _dbl, _dbl,
+                                _dbl, _dbl, _f64p, _int, _dbl, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
+    L.orc_rast_bwd.argtypes = [_f64p, _i64, _i64p, _i64, _i64p, _i64p, _i64, _f64p, _i64, _i64,
+                               _dbl, _int, _int, _i64p, _i64, _i64p, _f64p, _f64p, _f64p, _f64p, _f64p]
+    return L
+
+
 def _load():
     global _lib
     if _lib is None:
-        _lib = ctypes.CDLL(build())
-        L = _lib
-        L.orc_rasterize.argtypes = [_f64p, _i64, _i64p, _i64, _i64p, _i64p, _i64, _f64p, _i64, _i64,
-                                    _dbl, _int, _int, _i64p, _i64, _i64p, _f64p, _f64p, _f64p]
-        L.orc_pixel_candidates.argtypes = [_f64p, _i64, _i64p, _i64, _i64p, _i64p, _f64p, _i64, _dbl,
-                                           _int, _int, _i64, _i64, _i64, _i64p, _f64p, _i64]
-        L.orc_pixel_candidates.restype = _i64
-        L.orc_margins.argtypes = [_f64p, _i64, _i64p, _i64, _i64p, _i64p, _i64, _f64p, _i64, _i64,
-                                  _dbl, _int, _int, _i64p, _i64, _dbl, _u8p]
-        L.orc_bins.argtypes = [_f64p, _i64, _i64p, _i64, _i64p, _i64p, _i64, _f64p, _i64, _i64, _dbl,
-                               _dbl, _i64p, _i64p, _i64p, _u8p]
-        L.orc_blend_fwd.argtypes = [_i64, _i64, _i64p, _f64p, _f64p, _f64p, _i64p, _f64p, _dbl, _dbl,
-                                    _dbl, _dbl, _f64p, _int, _dbl, _f64p]
-        L.orc_blend_bwd.argtypes = [_i64, _i64, _i64p, _f64p, _f64p, _f64p, _i64p, _f64p, _dbl, _dbl,
-                                    _dbl, _dbl, _f64p, _int, _dbl, _f64p, _f64p, _f64p, _f64p, _f64p]
-        L.orc_rast_bwd.argtypes = [_f64p, _i64, _i64p, _i64, _i64p, _i64p, _i64, _f64p, _i64, _i64,
-                                   _dbl, _int, _int, _i64p, _i64, _i64p, _f64p, _f64p, _f64p, _f64p]
+        _lib = _open(build())
     return _lib
+
+
+class use_library:
+    """Context manager: run the wrappers against another build of oracle.c
+    (the mutation tests plant mistakes in a copy and check that the pins fail)."""
+
+    def __init__(self, path):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.prev = _load()
+        _lib = _open(self.path)
+        return self
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self.prev
+        return False
+
+
+def compile_source(src_text, out_path):
+    """Compile C source text of the oracle into a shared library at out_path."""
+    c_path = out_path + ".c"
+    with open(c_path, "w") as f:
+        f.write(src_text)
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-o",
+                           out_path, c_path, "-lm"])
+    return out_path
+
+
+def source_text():
+    with open(_SRC) as f:
+        return f.read()
 
 
 def _d(a):
@@ -185,8 +223,9 @@ def blend_fwd(pix_to_face, zbuf, bary, dists, faces, colors, sigma, gamma, znear
 
 
 def blend_bwd(pix_to_face, zbuf, bary, dists, faces, colors, grad_rgba, sigma, gamma, znear, zfar,
-              bg=(1.0, 1.0, 1.0), mode=1, eps=1e-10, V=None):
-    """Adjoint of ``blend_fwd``: returns (grad_zbuf, grad_bary, grad_dists, grad_colors)."""
+              bg=(1.0, 1.0, 1.0), mode=1, eps=1e-10, V=None, with_abs=False):
+    """Adjoint of ``blend_fwd``: returns (grad_zbuf, grad_bary, grad_dists, grad_colors), plus the
+    per-component sums of |contribution| to grad_colors when ``with_abs``."""
     L = _load()
     p2f = _i(pix_to_face)
     K = p2f.shape[-1]
@@ -199,15 +238,18 @@ def blend_bwd(pix_to_face, zbuf, bary, dists, faces, colors, grad_rgba, sigma, g
     bgv = _d(bg)
     gz = np.empty((P, K)); gb = np.empty((P, K, 3)); gd = np.empty((P, K))
     gc = np.zeros((co.shape[0] if V is None else V, 3))
+    ga = np.zeros_like(gc) if with_abs else None
     L.orc_blend_bwd(P, K, _p(p2f, _i64p), _p(zb, _f64p), _p(ba, _f64p), _p(di, _f64p), _p(fa, _i64p),
                     _p(co, _f64p), sigma, gamma, znear, zfar, _p(bgv, _f64p), int(mode), eps,
-                    _p(g, _f64p), _p(gz, _f64p), _p(gb, _f64p), _p(gd, _f64p), _p(gc, _f64p))
-    return gz.reshape(*lead, K), gb.reshape(*lead, K, 3), gd.reshape(*lead, K), gc
+                    _p(g, _f64p), _p(gz, _f64p), _p(gb, _f64p), _p(gd, _f64p), _p(gc, _f64p), _p(ga, _f64p))
+    out = (gz.reshape(*lead, K), gb.reshape(*lead, K, 3), gd.reshape(*lead, K), gc)
+    return out + (ga,) if with_abs else out
 
 
 def rast_bwd(m: Mesh, S, K, pix_to_face, grad_zbuf, grad_bary, grad_dists, blur=0.0, persp=True,
-             clip=False, pixels=None):
-    """Adjoint of ``rasterize`` conditioned on ``pix_to_face``; returns grad_verts (V, 3)."""
+             clip=False, pixels=None, with_abs=False):
+    """Adjoint of ``rasterize`` conditioned on ``pix_to_face``; returns grad_verts (V, 3)
+    (and the per-component sums of |contribution| when ``with_abs``)."""
     L = _load()
     px, P = _pixels(pixels)
     if px is None:
@@ -217,7 +259,8 @@ def rast_bwd(m: Mesh, S, K, pix_to_face, grad_zbuf, grad_bary, grad_dists, blur=
     gb = None if grad_bary is None else _d(grad_bary).reshape(P, K, 3)
     gd = None if grad_dists is None else _d(grad_dists).reshape(P, K)
     gv = np.zeros_like(m.verts)
+    ga = np.zeros_like(gv) if with_abs else None
     L.orc_rast_bwd(*m._head(), m.N, _p(m.cams, _f64p), S, K, float(blur), int(persp), int(clip),
                    _p(px, _i64p), P, _p(p2f, _i64p), _p(gz, _f64p), _p(gb, _f64p), _p(gd, _f64p),
-                   _p(gv, _f64p))
-    return gv
+                   _p(gv, _f64p), _p(ga, _f64p))
+    return (gv, ga) if with_abs else gv

@@ -466,13 +466,15 @@ int orc_blend_fwd(int64_t P, int64_t K, const int64_t *pix_to_face, const double
 
 /* Adjoint of orc_blend_fwd.  Outputs are overwritten: grad_zbuf, grad_dists
  * (P x K), grad_bary (P x K x 3); grad_colors (V x 3) is ACCUMULATED into
- * (caller zeroes it).  zinv_max is treated as a constant: rgb does not depend
+ * (caller zeroes it); grad_colors_abs (optional) accumulates the absolute
+ * values of the same contributions (the scale of each sum, for tolerances).  zinv_max is treated as a constant: rgb does not depend
  * on it (it cancels between numerator and denominator). */
 int orc_blend_bwd(int64_t P, int64_t K, const int64_t *pix_to_face, const double *zbuf,
                   const double *bary, const double *dists, const int64_t *faces,
                   const double *colors, double sigma, double gamma, double znear, double zfar,
                   const double *bg, int mode, double eps, const double *grad_rgba,
-                  double *grad_zbuf, double *grad_bary, double *grad_dists, double *grad_colors) {
+                  double *grad_zbuf, double *grad_bary, double *grad_dists, double *grad_colors,
+                  double *grad_colors_abs) {
     double *q = (double *)malloc(sizeof(double) * (size_t)(K > 0 ? K : 1));
     for (int64_t p = 0; p < P; p++) {
         for (int64_t k = 0; k < K; k++) {
@@ -542,6 +544,7 @@ int orc_blend_bwd(int64_t P, int64_t K, const int64_t *pix_to_face, const double
                     int64_t v = faces[3 * f + i];
                     grad_bary[3 * s + i] += gc * colors[3 * v + ch];
                     grad_colors[3 * v + ch] += gc * bary[3 * s + i];
+                    if (grad_colors_abs) grad_colors_abs[3 * v + ch] += fabs(gc * bary[3 * s + i]);
                 }
             }
             /* w = prob E: d/dprob = E, d/dzinv = w/gamma, dzinv/dz = -1/(zfar - znear) */
@@ -571,13 +574,14 @@ static void orc_edge_grad(const double *a, const double *b, double px, double py
  * through clipping, perspective correction, the edge functions and the
  * segment distance to the three NDC corners, then through the projection
  * Jacobian and R^T to world-space vertex positions.  grad_zbuf, grad_bary,
- * grad_dists may be NULL (zero).  grad_verts (V x 3) is ACCUMULATED into. */
+ * grad_dists may be NULL (zero).  grad_verts (V x 3) is ACCUMULATED into;
+ * grad_verts_abs (optional) accumulates |contribution| per component. */
 int orc_rast_bwd(const double *verts, int64_t V, const int64_t *faces, int64_t F,
                  const int64_t *first_face, const int64_t *num_faces, int64_t N,
                  const double *cams, int64_t S, int64_t K, double blur, int persp, int clip,
                  const int64_t *pixels, int64_t P, const int64_t *pix_to_face,
                  const double *grad_zbuf, const double *grad_bary, const double *grad_dists,
-                 double *grad_verts) {
+                 double *grad_verts, double *grad_verts_abs) {
     (void)first_face; (void)num_faces; (void)F;
     if (!pixels) P = N * S * S;
     for (int64_t p = 0; p < P; p++) {
@@ -664,8 +668,11 @@ int orc_rast_bwd(const double *verts, int64_t V, const int64_t *faces, int64_t F
                 double gyv = gP[i][1] * fo / pv[2];
                 double gzv = gP[i][2] - gP[i][0] * fo * pv[0] / (pv[2] * pv[2])
                                       - gP[i][1] * fo * pv[1] / (pv[2] * pv[2]);
-                for (int j = 0; j < 3; j++)
-                    grad_verts[3 * vi + j] += R[j] * gxv + R[3 + j] * gyv + R[6 + j] * gzv;
+                for (int j = 0; j < 3; j++) {
+                    double c = R[j] * gxv + R[3 + j] * gyv + R[6 + j] * gzv;
+                    grad_verts[3 * vi + j] += c;
+                    if (grad_verts_abs) grad_verts_abs[3 * vi + j] += fabs(c);
+                }
             }
         }
     }

@@ -66,7 +66,7 @@ int num_sms() {
 
 static bool check_params(const rast_params *p, int64_t V, int64_t F) {
     if (!p) return false;
-    if (p->N < 0 || p->image_size < 1 || p->image_size > 8192) return false;
+    if (p->N < 0 || p->N > 65535 || p->image_size < 1 || p->image_size > 8192) return false;
     if (p->faces_per_pixel < 1) return false;
     if (!(p->blur_radius >= 0.f) || !(p->blur_radius < 4.f)) return false;
     if (p->perspective_correct != 0 && p->perspective_correct != 1) return false;
@@ -257,12 +257,13 @@ int rast_mesh_bwd(const rast_params *p, const float *verts, int64_t V, const int
     a.fl.clip = p->clip_barycentric_coords;
     a.fl.blur = p->blur_radius;
     a.fl.znear = 0.f;
-    return mr::launch_rast_bwd(a, st) == cudaSuccess ? MESHRAST_OK : MESHRAST_ERR_CUDA;
+    return mr::launch_rast_bwd(a, p->N, st) == cudaSuccess ? MESHRAST_OK : MESHRAST_ERR_CUDA;
 }
 
 static int check_blend(const blend_params *bp, int64_t N, int64_t S, int64_t K) {
     if (!bp) return MESHRAST_ERR_INVALID_ARG;
-    if (N < 0 || S < 0 || K < 1 || K > mr::kMaxK) return K > mr::kMaxK ? MESHRAST_ERR_UNSUPPORTED : MESHRAST_ERR_INVALID_ARG;
+    if (N < 0 || N > 65535 || S < 0 || S > 8192 || K < 1 || K > mr::kMaxK)
+        return K > mr::kMaxK ? MESHRAST_ERR_UNSUPPORTED : MESHRAST_ERR_INVALID_ARG;
     if (!(bp->sigma > 0.f) || !(bp->gamma > 0.f) || !(bp->zfar > bp->znear)) return MESHRAST_ERR_INVALID_ARG;
     if (bp->mode != MESHRAST_BLEND_SIL && bp->mode != MESHRAST_BLEND_RGB) return MESHRAST_ERR_INVALID_ARG;
     if (bp->reserved != 0) return MESHRAST_ERR_INVALID_ARG;
@@ -274,6 +275,8 @@ static void fill_blend(mr::BlendArgs &a, const blend_params *bp, int64_t N, int6
                        const int64_t *faces, int64_t F, const float *colors, int64_t V) {
     std::memset(&a, 0, sizeof(a));
     a.P = N * S * S;
+    a.N = (int)N;
+    a.S = (int)S;
     a.F = F;
     a.V = V;
     a.K = (int)K;

@@ -145,14 +145,46 @@ __global__ void __launch_bounds__(256) k_blend_fwd(BlendArgs a) {
     reinterpret_cast<float4 *>(a.image)[pix] = out;
 }
 
+// pixel of a thread in the 16 x 16 tiled launch used by the backward kernels
+__device__ __forceinline__ bool tile_pixel(const BlendArgs &a, int64_t &pix) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int r = blockIdx.y * 16 + ty, c = blockIdx.x * 16 + tx;
+    pix = ((int64_t)blockIdx.z * a.S + r) * a.S + c;
+    return r < a.S && c < a.S;
+}
+
+// colour-gradient contributions of one slot (3 vertices x 3 channels), summed
+// over the warp's lanes that hold the same face; one lane per face adds them
+__device__ __forceinline__ void scatter_colour_grads(const BlendArgs &a, int key, const int64_t vi[3],
+                                                     float (&gcv)[9]) {
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    group_sum<9>(peers, gcv);
+    if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (vi[i] < 0) continue;
+            float *gcol = a.grad_colors + 3 * vi[i];
+            atomicAdd(gcol, gcv[3 * i]);
+            atomicAdd(gcol + 1, gcv[3 * i + 1]);
+            atomicAdd(gcol + 2, gcv[3 * i + 2]);
+        }
+    }
+}
+
 template <int KM>
 __global__ void __launch_bounds__(256) k_blend_bwd(BlendArgs a) {
-    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pix >= a.P) return;
+    int64_t pix;
+    const bool valid = tile_pixel(a, pix);
     const bool rgb = a.mode == MESHRAST_BLEND_RGB;
     SlotData<KM> S;
-    load_slots<KM>(a, pix, rgb, S);
-    const float4 g = reinterpret_cast<const float4 *>(a.grad_image)[pix];
+    float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (valid) {
+        load_slots<KM>(a, pix, rgb, S);
+        g = reinterpret_cast<const float4 *>(a.grad_image)[pix];
+    } else {
+#pragma unroll
+        for (int k = 0; k < KM; ++k) { S.f[k] = -1; S.d[k] = 0.f; S.z[k] = 0.f; }
+    }
     float keep = 1.f;
     float zmin = __int_as_float(0x7f800000);
     bool any = false;
@@ -202,34 +234,41 @@ __global__ void __launch_bounds__(256) k_blend_bwd(BlendArgs a) {
 #pragma unroll
         for (int k = 0; k < KM; ++k) {
             const int64_t s = s0 + k;
-            if (S.f[k] < 0) {
-                a.grad_zbuf[s] = 0.f;
-                a.grad_bary[3 * s] = 0.f;
-                a.grad_bary[3 * s + 1] = 0.f;
-                a.grad_bary[3 * s + 2] = 0.f;
-                continue;
-            }
-            float c[3], b[3];
-            int64_t vi[3];
-            slot_colour(a, s, S.f[k], c, vi, b);
-            const float gw = (g.x * (c[0] - rgb0) + g.y * (c[1] - rgb1) + g.z * (c[2] - rgb2)) * iD;
-            const float prob = sigmoidf_(-S.d[k] / a.sigma);
-            const float q = sigmoidf_(S.d[k] / a.sigma);
-            gd[k] += gw * E[k] * (-prob * q / a.sigma);
-            a.grad_zbuf[s] = gw * W[k] / a.gamma * (-1.f / range);
-            const float gc0 = g.x * W[k] * iD, gc1 = g.y * W[k] * iD, gc2 = g.z * W[k] * iD;
+            float gcv[9];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const float3 col = vertex_colour(a, vi[i]);
-                a.grad_bary[3 * s + i] = gc0 * col.x + gc1 * col.y + gc2 * col.z;
-                if (vi[i] < 0) continue;
-                float *gcol = a.grad_colors + 3 * vi[i];
-                atomicAdd(gcol, gc0 * b[i]);
-                atomicAdd(gcol + 1, gc1 * b[i]);
-                atomicAdd(gcol + 2, gc2 * b[i]);
+            for (int j = 0; j < 9; ++j) gcv[j] = 0.f;
+            int64_t vi[3] = {-1, -1, -1};
+            int key = -1;
+            if (S.f[k] < 0) {
+                if (valid) {
+                    a.grad_zbuf[s] = 0.f;
+                    a.grad_bary[3 * s] = 0.f;
+                    a.grad_bary[3 * s + 1] = 0.f;
+                    a.grad_bary[3 * s + 2] = 0.f;
+                }
+            } else {
+                key = S.f[k];
+                float c[3], b[3];
+                slot_colour(a, s, S.f[k], c, vi, b);
+                const float gw = (g.x * (c[0] - rgb0) + g.y * (c[1] - rgb1) + g.z * (c[2] - rgb2)) * iD;
+                const float prob = sigmoidf_(-S.d[k] / a.sigma);
+                const float q = sigmoidf_(S.d[k] / a.sigma);
+                gd[k] += gw * E[k] * (-prob * q / a.sigma);
+                a.grad_zbuf[s] = gw * W[k] / a.gamma * (-1.f / range);
+                const float gc0 = g.x * W[k] * iD, gc1 = g.y * W[k] * iD, gc2 = g.z * W[k] * iD;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const float3 col = vertex_colour(a, vi[i]);
+                    a.grad_bary[3 * s + i] = gc0 * col.x + gc1 * col.y + gc2 * col.z;
+                    gcv[3 * i] = gc0 * b[i];
+                    gcv[3 * i + 1] = gc1 * b[i];
+                    gcv[3 * i + 2] = gc2 * b[i];
+                }
             }
+            scatter_colour_grads(a, key, vi, gcv);
         }
     }
+    if (!valid) return;
     if constexpr (KM % 4 == 0) {
         float4 *dp = reinterpret_cast<float4 *>(a.grad_dists + s0);
 #pragma unroll
@@ -289,15 +328,15 @@ __global__ void __launch_bounds__(256) k_blend_fwd_any(BlendArgs a) {
 }
 
 __global__ void __launch_bounds__(256) k_blend_bwd_any(BlendArgs a) {
-    const int64_t pix = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (pix >= a.P) return;
+    int64_t pix;
+    const bool valid = tile_pixel(a, pix);
     const bool rgb = a.mode == MESHRAST_BLEND_RGB;
     const int K = a.K;
     const int64_t s0 = pix * K;
-    const float4 g = reinterpret_cast<const float4 *>(a.grad_image)[pix];
+    const float4 g = valid ? reinterpret_cast<const float4 *>(a.grad_image)[pix] : make_float4(0.f, 0.f, 0.f, 0.f);
     float keep = 1.f, zmin = __int_as_float(0x7f800000);
     bool any = false;
-    for (int k = 0; k < K; ++k) {
+    for (int k = 0; valid && k < K; ++k) {
         if (a.pix_to_face[s0 + k] < 0) continue;
         keep *= sigmoidf_(a.dists[s0 + k] / a.sigma);
         if (rgb) zmin = fminf(zmin, a.zbuf[s0 + k]);
@@ -311,7 +350,7 @@ __global__ void __launch_bounds__(256) k_blend_bwd_any(BlendArgs a) {
         face_max = any && ztop > a.eps;
         m = face_max ? ztop : a.eps;
         float num0 = 0.f, num1 = 0.f, num2 = 0.f, den = 0.f;
-        for (int k = 0; k < K; ++k) {
+        for (int k = 0; valid && k < K; ++k) {
             const int64_t s = s0 + k;
             const int64_t f = a.pix_to_face[s];
             if (f < 0) continue;
@@ -332,43 +371,49 @@ __global__ void __launch_bounds__(256) k_blend_bwd_any(BlendArgs a) {
         rgb1 = (num1 + delta * a.bg1) * iD;
         rgb2 = (num2 + delta * a.bg2) * iD;
     }
-    for (int k = 0; k < K; ++k) {
+    for (int k = 0; k < K; ++k) {  // uniform trip count: every lane reaches the warp aggregation
         const int64_t s = s0 + k;
-        const int64_t f = a.pix_to_face[s];
-        if (f < 0) {
-            a.grad_dists[s] = 0.f;
-            if (rgb) {
-                a.grad_zbuf[s] = 0.f;
-                a.grad_bary[3 * s] = a.grad_bary[3 * s + 1] = a.grad_bary[3 * s + 2] = 0.f;
+        const int64_t f = valid ? a.pix_to_face[s] : -1;
+        float gcv[9];
+        for (int j = 0; j < 9; ++j) gcv[j] = 0.f;
+        int64_t vi[3] = {-1, -1, -1};
+        int key = -1;
+        if (valid) {
+            if (f < 0) {
+                a.grad_dists[s] = 0.f;
+                if (rgb) {
+                    a.grad_zbuf[s] = 0.f;
+                    a.grad_bary[3 * s] = a.grad_bary[3 * s + 1] = a.grad_bary[3 * s + 2] = 0.f;
+                }
+            } else {
+                const float d = a.dists[s];
+                const float prob = sigmoidf_(-d / a.sigma);
+                float gd = g.w * (-prob * keep / a.sigma);
+                if (rgb) {
+                    key = clamp_id(f);
+                    const float z = a.zbuf[s];
+                    const float arg = face_max ? (zmin - z) / (range * a.gamma)
+                                               : ((a.zfar - z) / range - m) / a.gamma;
+                    const float E = expf(arg);
+                    const float W = prob * E;
+                    float c[3], b[3];
+                    slot_colour(a, s, f, c, vi, b);
+                    const float gw = (g.x * (c[0] - rgb0) + g.y * (c[1] - rgb1) + g.z * (c[2] - rgb2)) * iD;
+                    gd += gw * E * (-prob * sigmoidf_(d / a.sigma) / a.sigma);
+                    a.grad_zbuf[s] = gw * W / a.gamma * (-1.f / range);
+                    const float gc0 = g.x * W * iD, gc1 = g.y * W * iD, gc2 = g.z * W * iD;
+                    for (int i = 0; i < 3; ++i) {
+                        const float3 col = vertex_colour(a, vi[i]);
+                        a.grad_bary[3 * s + i] = gc0 * col.x + gc1 * col.y + gc2 * col.z;
+                        gcv[3 * i] = gc0 * b[i];
+                        gcv[3 * i + 1] = gc1 * b[i];
+                        gcv[3 * i + 2] = gc2 * b[i];
+                    }
+                }
+                a.grad_dists[s] = gd;
             }
-            continue;
         }
-        const float d = a.dists[s];
-        const float prob = sigmoidf_(-d / a.sigma);
-        float gd = g.w * (-prob * keep / a.sigma);
-        if (rgb) {
-            const float z = a.zbuf[s];
-            const float arg = face_max ? (zmin - z) / (range * a.gamma) : ((a.zfar - z) / range - m) / a.gamma;
-            const float E = expf(arg);
-            const float W = prob * E;
-            float c[3], b[3];
-            int64_t vi[3];
-            slot_colour(a, s, f, c, vi, b);
-            const float gw = (g.x * (c[0] - rgb0) + g.y * (c[1] - rgb1) + g.z * (c[2] - rgb2)) * iD;
-            gd += gw * E * (-prob * sigmoidf_(d / a.sigma) / a.sigma);
-            a.grad_zbuf[s] = gw * W / a.gamma * (-1.f / range);
-            const float gc0 = g.x * W * iD, gc1 = g.y * W * iD, gc2 = g.z * W * iD;
-            for (int i = 0; i < 3; ++i) {
-                const float3 col = vertex_colour(a, vi[i]);
-                a.grad_bary[3 * s + i] = gc0 * col.x + gc1 * col.y + gc2 * col.z;
-                if (vi[i] < 0) continue;
-                float *gcol = a.grad_colors + 3 * vi[i];
-                atomicAdd(gcol, gc0 * b[i]);
-                atomicAdd(gcol + 1, gc1 * b[i]);
-                atomicAdd(gcol + 2, gc2 * b[i]);
-            }
-        }
-        a.grad_dists[s] = gd;
+        if (rgb) scatter_colour_grads(a, key, vi, gcv);
     }
 }
 
@@ -378,7 +423,7 @@ static void launch_fwd_t(const BlendArgs &a, int grid, cudaStream_t st) {
     k_blend_fwd<KM><<<grid, 256, 0, st>>>(a);
 }
 template <int KM>
-static void launch_bwd_t(const BlendArgs &a, int grid, cudaStream_t st) {
+static void launch_bwd_t(const BlendArgs &a, dim3 grid, cudaStream_t st) {
     k_blend_bwd<KM><<<grid, 256, 0, st>>>(a);
 }
 
@@ -398,7 +443,8 @@ cudaError_t launch_blend_fwd(const BlendArgs &a, cudaStream_t st) {
 
 cudaError_t launch_blend_bwd(const BlendArgs &a, cudaStream_t st) {
     if (a.P <= 0) return cudaSuccess;
-    const int grid = (int)((a.P + 255) / 256);
+    const unsigned tiles = (unsigned)((a.S + 15) / 16);
+    const dim3 grid(tiles, tiles, (unsigned)a.N);
     switch (a.K) {
         case 1: launch_bwd_t<1>(a, grid, st); break;
         case 2: launch_bwd_t<2>(a, grid, st); break;

@@ -23,38 +23,10 @@ __device__ __forceinline__ void edge_grad(float ax, float ay, float bx, float by
     gby += g * (ax - px);
 }
 
-__global__ void __launch_bounds__(256) k_rast_bwd(RastBwdArgs a) {
-    const int *face_mesh = a.face_mesh;
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= a.slots) return;
-    const int64_t f = a.pix_to_face[s];
-    if (f < 0 || f >= a.F) return;  // empty slot (or an id outside the batch)
-    const int n_face = face_mesh[f];
-    if (n_face < 0) return;
-    const int64_t pix = s / a.K;
-    const int64_t SS = (int64_t)a.S * a.S;
-    const int rem = (int)(pix % SS);
-    const int r = rem / a.S, c = rem % a.S;
-    const PixC p = pixel_centre(r, c, a.S);
-
-    FaceRec R;
-    {
-        const float4 *src = reinterpret_cast<const float4 *>(a.rec + f);
-        R.a = __ldg(src);
-        R.b = __ldg(src + 1);
-        R.c = __ldg(src + 2);
-        R.d = __ldg(src + 3);
-    }
-    float gz = a.grad_zbuf ? a.grad_zbuf[s] : 0.f;
-    float gd = a.grad_dists ? a.grad_dists[s] : 0.f;
-    float gbp0 = 0.f, gbp1 = 0.f, gbp2 = 0.f;
-    if (a.grad_bary) {
-        gbp0 = a.grad_bary[3 * s];
-        gbp1 = a.grad_bary[3 * s + 1];
-        gbp2 = a.grad_bary[3 * s + 2];
-    }
-    if (gz == 0.f && gd == 0.f && gbp0 == 0.f && gbp1 == 0.f && gbp2 == 0.f) return;
-
+// NDC-space corner gradients of one slot: g[3*i + {0,1,2}] = dL/d(x_i, y_i, z_i)
+// of corner i (NDC x, NDC y, view depth).  Returns false for an empty slot.
+__device__ __forceinline__ void slot_corner_grads(const FaceRec &R, const PixC &p, const EvalFlags &fl, float gz,
+                                                  float gd, float gbp0, float gbp1, float gbp2, float (&g)[9]) {
     // ---- forward recompute (corner-0-relative coordinates) ----
     float qx, qy;
     local_q(R, p, qx, qy);
@@ -67,16 +39,15 @@ __global__ void __launch_bounds__(256) k_rast_bwd(RastBwdArgs a) {
     const float iz[3] = {R.d.y, R.d.z, R.d.w};
     const float zc[3] = {1.f / iz[0], 1.f / iz[1], 1.f / iz[2]};
     float bt[3], T = 1.f;
-    if (a.fl.persp) {
-        float t[3];
-        for (int i = 0; i < 3; ++i) t[i] = b[i] * iz[i];
-        T = t[0] + t[1] + t[2];
-        for (int i = 0; i < 3; ++i) bt[i] = t[i] / T;
+    if (fl.persp) {
+        // 1/z is affine in the pixel position: T = iz0 + b1 (iz1 - iz0) + b2 (iz2 - iz0)
+        T = iz[0] + b[1] * (iz[1] - iz[0]) + b[2] * (iz[2] - iz[0]);
+        for (int i = 0; i < 3; ++i) bt[i] = b[i] * iz[i] / T;
     } else {
         for (int i = 0; i < 3; ++i) bt[i] = b[i];
     }
     float bp[3], cs = 1.f;
-    if (a.fl.clip) {
+    if (fl.clip) {
         float cc[3];
         for (int i = 0; i < 3; ++i) cc[i] = fmaxf(bt[i], 0.f);
         cs = cc[0] + cc[1] + cc[2];
@@ -93,14 +64,14 @@ __global__ void __launch_bounds__(256) k_rast_bwd(RastBwdArgs a) {
         gZ[i] = gz * bp[i];
     }
     float gbt[3];
-    if (a.fl.clip) {
+    if (fl.clip) {
         const float dot = gbp[0] * bp[0] + gbp[1] * bp[1] + gbp[2] * bp[2];
         for (int i = 0; i < 3; ++i) gbt[i] = (bt[i] > 0.f) ? (gbp[i] - dot) / cs : 0.f;
     } else {
         for (int i = 0; i < 3; ++i) gbt[i] = gbp[i];
     }
     float gb[3];
-    if (a.fl.persp) {
+    if (fl.persp) {
         // t_i = b_i / z_i, b~_i = t_i / T:  dt_i/db_i = iz_i, dt_i/dz_i = -b_i iz_i^2
         const float dot = gbt[0] * bt[0] + gbt[1] * bt[1] + gbt[2] * bt[2];
         for (int i = 0; i < 3; ++i) {
@@ -139,27 +110,83 @@ __global__ void __launch_bounds__(256) k_rast_bwd(RastBwdArgs a) {
         gx[ib] += gs * (-2.f * rx * tseg);
         gy[ib] += gs * (-2.f * ry * tseg);
     }
-    // NDC -> view -> world
-    const float *cam = a.cams + 16 * n_face;
-    const float fo = cam[12];
-    const float v0x = R.a.x + R.a.z, v0y = R.a.y + R.a.w;
     for (int i = 0; i < 3; ++i) {
-        const float xn = v0x + Px[i], yn = v0y + Py[i], z = zc[i];
-        const float gxv = gx[i] * fo / z;
-        const float gyv = gy[i] * fo / z;
-        const float gzv = gZ[i] - (gx[i] * xn + gy[i] * yn) / z;
-        const int64_t vi = a.faces[3 * f + i];
-        float *gv = a.grad_verts + 3 * vi;
-        atomicAdd(gv + 0, cam[0] * gxv + cam[3] * gyv + cam[6] * gzv);
-        atomicAdd(gv + 1, cam[1] * gxv + cam[4] * gyv + cam[7] * gzv);
-        atomicAdd(gv + 2, cam[2] * gxv + cam[5] * gyv + cam[8] * gzv);
+        g[3 * i] = gx[i];
+        g[3 * i + 1] = gy[i];
+        g[3 * i + 2] = gZ[i];
     }
 }
 
-cudaError_t launch_rast_bwd(const RastBwdArgs &a, cudaStream_t st) {
-    if (a.slots <= 0) return cudaSuccess;
-    const int64_t grid = (a.slots + 255) / 256;
-    k_rast_bwd<<<(unsigned)grid, 256, 0, st>>>(a);
+// One block = a 16 x 16 pixel tile of one image; each thread loops over its
+// pixel's K slots.  For every k the warp (2 rows x 16 pixels) sums the corner
+// gradients of lanes that hold the same face, and one lane per face applies
+// the projection Jacobian and R^T and issues the atomics.
+__global__ void __launch_bounds__(256) k_rast_bwd(RastBwdArgs a) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int n = blockIdx.z;
+    const int r = blockIdx.y * 16 + ty, c = blockIdx.x * 16 + tx;
+    const bool valid = (r < a.S) && (c < a.S);
+    const PixC p = pixel_centre(r, c, a.S);
+    const int64_t pix = ((int64_t)n * a.S + r) * a.S + c;
+    for (int k = 0; k < a.K; ++k) {
+        const int64_t s = pix * a.K + k;
+        int64_t f = valid ? a.pix_to_face[s] : -1;
+        if (f >= a.F) f = -1;  // an id outside the batch contributes nothing
+        int nf = (f >= 0) ? a.face_mesh[f] : -1;
+        if (nf < 0) f = -1;
+        float g[9];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) g[j] = 0.f;
+        FaceRec R;
+        if (f >= 0) {
+            const float4 *src = reinterpret_cast<const float4 *>(a.rec + f);
+            R.a = __ldg(src);
+            R.b = __ldg(src + 1);
+            R.c = __ldg(src + 2);
+            R.d = __ldg(src + 3);
+            const float gz = a.grad_zbuf ? a.grad_zbuf[s] : 0.f;
+            const float gd = a.grad_dists ? a.grad_dists[s] : 0.f;
+            float gb0 = 0.f, gb1 = 0.f, gb2 = 0.f;
+            if (a.grad_bary) {
+                gb0 = a.grad_bary[3 * s];
+                gb1 = a.grad_bary[3 * s + 1];
+                gb2 = a.grad_bary[3 * s + 2];
+            }
+            if (gz != 0.f || gd != 0.f || gb0 != 0.f || gb1 != 0.f || gb2 != 0.f)
+                slot_corner_grads(R, p, a.fl, gz, gd, gb0, gb1, gb2, g);
+            else
+                f = -1;
+        }
+        const int key = (int)f;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        group_sum<9>(peers, g);
+        if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+            // NDC -> view -> world, once per face and warp
+            const float *cam = a.cams + 16 * nf;
+            const float fo = cam[12];
+            const float v0x = R.a.x + R.a.z, v0y = R.a.y + R.a.w;
+            const float Px[3] = {0.f, R.b.x, R.b.z}, Py[3] = {0.f, R.b.y, R.b.w};
+            const float iz[3] = {R.d.y, R.d.z, R.d.w};
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float xn = v0x + Px[i], yn = v0y + Py[i], z = 1.f / iz[i];
+                const float gxv = g[3 * i] * fo / z;
+                const float gyv = g[3 * i + 1] * fo / z;
+                const float gzv = g[3 * i + 2] - (g[3 * i] * xn + g[3 * i + 1] * yn) / z;
+                const int64_t vi = a.faces[3 * f + i];
+                float *gv = a.grad_verts + 3 * vi;
+                atomicAdd(gv + 0, cam[0] * gxv + cam[3] * gyv + cam[6] * gzv);
+                atomicAdd(gv + 1, cam[1] * gxv + cam[4] * gyv + cam[7] * gzv);
+                atomicAdd(gv + 2, cam[2] * gxv + cam[5] * gyv + cam[8] * gzv);
+            }
+        }
+    }
+}
+
+cudaError_t launch_rast_bwd(const RastBwdArgs &a, int N, cudaStream_t st) {
+    if (a.slots <= 0 || N <= 0) return cudaSuccess;
+    const unsigned tiles = (unsigned)((a.S + 15) / 16);
+    k_rast_bwd<<<dim3(tiles, tiles, (unsigned)N), 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -188,44 +188,47 @@ __device__ __forceinline__ bool beyond_blur_lines(const FaceRec &r, float qx, fl
 
 // Depth of a face at a pixel and final barycentrics, in the order
 // perspective correction -> clipping -> z = sum b'_i z_i.
+// With perspective correction 1/z is affine in the pixel position:
+// T = sum b_i / z_i = iz0 + b1 (iz1 - iz0) + b2 (iz2 - iz0), which keeps its
+// accuracy when extrapolated outside the face.  A clipped depth is formed as
+// z_j + sum_i c_i (z_i - z_j) / sum c with j the largest weight, so a pixel
+// clipped to a shared vertex gets exactly that vertex's depth from every face.
+__device__ __forceinline__ float clipped_depth(float c0, float c1, float c2, const float z[3], float *bp,
+                                               bool want) {
+    float cs = __fadd_rn(__fadd_rn(c0, c1), c2);
+    float ic = __fdiv_rn(1.f, cs);
+    float w0 = __fmul_rn(c0, ic), w1 = __fmul_rn(c1, ic), w2 = __fmul_rn(c2, ic);
+    if (want) { bp[0] = w0; bp[1] = w1; bp[2] = w2; }
+    if (c0 >= c1 && c0 >= c2)
+        return __fadd_rn(z[0], __fadd_rn(__fmul_rn(w1, __fsub_rn(z[1], z[0])), __fmul_rn(w2, __fsub_rn(z[2], z[0]))));
+    if (c1 >= c2)
+        return __fadd_rn(z[1], __fadd_rn(__fmul_rn(w0, __fsub_rn(z[0], z[1])), __fmul_rn(w2, __fsub_rn(z[2], z[1]))));
+    return __fadd_rn(z[2], __fadd_rn(__fmul_rn(w0, __fsub_rn(z[0], z[2])), __fmul_rn(w1, __fsub_rn(z[1], z[2]))));
+}
+
 template <bool WANT_BARY>
 __device__ __forceinline__ float face_depth(const FaceRec &r, int persp, int clip, bool inside, float b0,
                                             float b1, float b2, float *bp) {
-    float t0 = b0, t1 = b1, t2 = b2;
+    const float z[3] = {__frcp_rn(r.d.y), __frcp_rn(r.d.z), __frcp_rn(r.d.w)};
     if (persp) {
-        t0 = __fmul_rn(b0, r.d.y);
-        t1 = __fmul_rn(b1, r.d.z);
-        t2 = __fmul_rn(b2, r.d.w);
-        float T = __fadd_rn(__fadd_rn(t0, t1), t2);
+        const float T = __fadd_rn(r.d.y, __fadd_rn(__fmul_rn(b1, __fsub_rn(r.d.z, r.d.y)),
+                                                   __fmul_rn(b2, __fsub_rn(r.d.w, r.d.y))));
+        const float iT = __fdiv_rn(1.f, T);
+        const float t0 = __fmul_rn(__fmul_rn(b0, r.d.y), iT);
+        const float t1 = __fmul_rn(__fmul_rn(b1, r.d.z), iT);
+        const float t2 = __fmul_rn(__fmul_rn(b2, r.d.w), iT);
         if (!clip || inside) {
-            // b~ = t / T; z = sum b~_i z_i = 1 / T
-            if (WANT_BARY) {
-                float iT = __fdiv_rn(1.f, T);
-                bp[0] = __fmul_rn(t0, iT);
-                bp[1] = __fmul_rn(t1, iT);
-                bp[2] = __fmul_rn(t2, iT);
-            }
-            return __fdiv_rn(1.f, T);
+            // b~ = (b_i / z_i) / T; z = 1 / T
+            if (WANT_BARY) { bp[0] = t0; bp[1] = t1; bp[2] = t2; }
+            return iT;
         }
-        float iT = __fdiv_rn(1.f, T);
-        t0 = __fmul_rn(t0, iT);
-        t1 = __fmul_rn(t1, iT);
-        t2 = __fmul_rn(t2, iT);
-    } else if (!clip || inside) {
-        if (WANT_BARY) { bp[0] = b0; bp[1] = b1; bp[2] = b2; }
-        return __fadd_rn(__fadd_rn(__fmul_rn(b0, __frcp_rn(r.d.y)), __fmul_rn(b1, __frcp_rn(r.d.z))),
-                         __fmul_rn(b2, __frcp_rn(r.d.w)));
+        return clipped_depth(fmaxf(t0, 0.f), fmaxf(t1, 0.f), fmaxf(t2, 0.f), z, bp, WANT_BARY);
     }
-    // clipping: c_i = max(b~_i, 0) / sum
-    float c0 = fmaxf(t0, 0.f), c1 = fmaxf(t1, 0.f), c2 = fmaxf(t2, 0.f);
-    float cs = __fadd_rn(__fadd_rn(c0, c1), c2);
-    float ic = __fdiv_rn(1.f, cs);
-    c0 = __fmul_rn(c0, ic);
-    c1 = __fmul_rn(c1, ic);
-    c2 = __fmul_rn(c2, ic);
-    if (WANT_BARY) { bp[0] = c0; bp[1] = c1; bp[2] = c2; }
-    return __fadd_rn(__fadd_rn(__fmul_rn(c0, __frcp_rn(r.d.y)), __fmul_rn(c1, __frcp_rn(r.d.z))),
-                     __fmul_rn(c2, __frcp_rn(r.d.w)));
+    if (!clip || inside) {
+        if (WANT_BARY) { bp[0] = b0; bp[1] = b1; bp[2] = b2; }
+        return __fadd_rn(z[0], __fadd_rn(__fmul_rn(b1, __fsub_rn(z[1], z[0])), __fmul_rn(b2, __fsub_rn(z[2], z[0]))));
+    }
+    return clipped_depth(fmaxf(b0, 0.f), fmaxf(b1, 0.f), fmaxf(b2, 0.f), z, bp, WANT_BARY);
 }
 
 // Candidate test + sort key for the K-nearest pass.  Returns true and the
@@ -295,6 +298,31 @@ struct TopK {
         }
     }
 };
+
+// ---------------------------------------------------------------------------
+// warp aggregation by key: lanes with equal keys form a group (peers); the
+// sum of each group's values ends in the group's lowest lane.  Tree over the
+// group's ranks: each round a lane adds the value of its next remaining peer,
+// then lanes of odd rank leave.  Every lane of the warp must call this.
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void group_sum(unsigned peers, float (&x)[NV]) {
+    const unsigned lane = threadIdx.x & 31u;
+    unsigned rem = peers & ~((2u << lane) - 1u);   // peers above this lane
+    unsigned rank = __popc(peers & ((1u << lane) - 1u));
+    while (__any_sync(0xffffffffu, rem != 0u)) {
+        const int next = __ffs(rem);               // 1-based lane of the next peer, 0 if none
+        const int src = next ? next - 1 : (int)lane;
+#pragma unroll
+        for (int j = 0; j < NV; ++j) {
+            const float t = __shfl_sync(0xffffffffu, x[j], src);
+            if (next) x[j] += t;
+        }
+        const bool done = rank & 1u;
+        rem &= __ballot_sync(0xffffffffu, !done);
+        rank >>= 1;
+    }
+}
 
 __device__ __forceinline__ void set_status(unsigned *status, unsigned bits) {
     if (bits) atomicOr(status, bits);

@@ -92,6 +92,7 @@ struct RastBwdArgs {
 struct BlendArgs {
     int64_t P;  // pixels
     int64_t F, V;
+    int N, S;
     int K;
     const int64_t *pix_to_face;
     const float *zbuf, *bary, *dists;
@@ -110,7 +111,7 @@ cudaError_t launch_scan(const ScanArgs &a, cudaStream_t st);
 cudaError_t launch_fill(const FillArgs &a, cudaStream_t st);
 cudaError_t launch_fine(const FineArgs &a, int bin, cudaStream_t st);
 cudaError_t launch_naive(const NaiveArgs &a, int N, cudaStream_t st);
-cudaError_t launch_rast_bwd(const RastBwdArgs &a, cudaStream_t st);
+cudaError_t launch_rast_bwd(const RastBwdArgs &a, int N, cudaStream_t st);
 cudaError_t launch_blend_fwd(const BlendArgs &a, cudaStream_t st);
 cudaError_t launch_blend_bwd(const BlendArgs &a, cudaStream_t st);
 

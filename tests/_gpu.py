@@ -73,13 +73,20 @@ def pick(fr, pixels, S):
     return [np.asarray(x)[n, r, c] for x in fr]
 
 
-def grad_close(g, ref, rel=1e-4):
-    """per component |g - ref| <= rel * max(|ref|, 1e-2 rms(ref)), and the global
-    relative 2-norm error <= rel.  Returns (worst ratio, global rel err)."""
+def grad_close(g, ref, rel=1e-4, scale=None):
+    """Gradient check.  Per component |g - ref| <= rel * max(|ref|, floor), where
+    floor is the component's sum of |contributions| when ``scale`` is given (an
+    accumulated sum of signed terms is only defined relative to that), else
+    1e-2 * rms(ref); and globally ||g - ref|| / ||ref|| <= rel.
+    Returns (worst per-component ratio, global relative error)."""
     g = np.asarray(g, np.float64)
     ref = np.asarray(ref, np.float64)
-    rms = np.sqrt(np.mean(ref ** 2)) if ref.size else 0.0
-    den = np.maximum(np.abs(ref), 1e-2 * rms) + 1e-30
+    if scale is None:
+        rms = np.sqrt(np.mean(ref ** 2)) if ref.size else 0.0
+        floor = 1e-2 * rms
+    else:
+        floor = np.asarray(scale, np.float64)
+    den = np.maximum(np.abs(ref), floor) + 1e-30
     worst = float(np.max(np.abs(g - ref) / den)) / rel if ref.size else 0.0
     glob = float(np.linalg.norm(g - ref) / (np.linalg.norm(ref) + 1e-30))
     return worst, glob
