@@ -183,7 +183,7 @@ def margins(m: Mesh, S, K, blur=0.0, persp=True, clip=False, pixels=None, eps=1e
     return fl
 
 
-FWD_AMBIGUOUS = 1 | 2 | 4 | 8 | 16
+FWD_AMBIGUOUS = 1 | 2 | 4 | 8 | 16 | 128
 GRAD_AMBIGUOUS = FWD_AMBIGUOUS | 32 | 64
 
 

@@ -207,30 +207,25 @@ __global__ void __launch_bounds__(256) k_blend_bwd(BlendArgs a) {
         const float ztop = any ? (a.zfar - zmin) / range : -__int_as_float(0x7f800000);
         const bool face_max = any && ztop > a.eps;
         const float m = face_max ? ztop : a.eps;
-        float E[KM], W[KM];
-        float num0 = 0.f, num1 = 0.f, num2 = 0.f, den = 0.f;
+        float E[KM], W[KM], C[KM][3];
+        float den = 0.f;
 #pragma unroll
         for (int k = 0; k < KM; ++k) {
             E[k] = 0.f;
             W[k] = 0.f;
+            C[k][0] = C[k][1] = C[k][2] = 0.f;
             if (S.f[k] < 0) continue;
             const float arg = face_max ? (zmin - S.z[k]) / (range * a.gamma)
                                        : ((a.zfar - S.z[k]) / range - m) / a.gamma;
             E[k] = expf(arg);
             W[k] = sigmoidf_(-S.d[k] / a.sigma) * E[k];
-            float c[3], b[3];
+            float b[3];
             int64_t vi[3];
-            slot_colour(a, s0 + k, S.f[k], c, vi, b);
-            num0 += W[k] * c[0];
-            num1 += W[k] * c[1];
-            num2 += W[k] * c[2];
+            slot_colour(a, s0 + k, S.f[k], C[k], vi, b);
             den += W[k];
         }
         const float delta = expf((a.eps - m) / a.gamma);
-        const float D = den + delta;
-        const float iD = 1.f / D;
-        const float rgb0 = (num0 + delta * a.bg0) * iD, rgb1 = (num1 + delta * a.bg1) * iD,
-                    rgb2 = (num2 + delta * a.bg2) * iD;
+        const float iD = 1.f / (den + delta);
 #pragma unroll
         for (int k = 0; k < KM; ++k) {
             const int64_t s = s0 + k;
@@ -250,7 +245,17 @@ __global__ void __launch_bounds__(256) k_blend_bwd(BlendArgs a) {
                 key = S.f[k];
                 float c[3], b[3];
                 slot_colour(a, s, S.f[k], c, vi, b);
-                const float gw = (g.x * (c[0] - rgb0) + g.y * (c[1] - rgb1) + g.z * (c[2] - rgb2)) * iD;
+                // c_k - rgb = (sum_{j != k} w_j (c_k - c_j) + delta (c_k - bg)) / D: exact for the
+                // dominant face, where c_k - rgb would otherwise be lost to cancellation
+                float d0 = delta * (C[k][0] - a.bg0), d1 = delta * (C[k][1] - a.bg1), d2 = delta * (C[k][2] - a.bg2);
+#pragma unroll
+                for (int j = 0; j < KM; ++j) {
+                    if (j == k) continue;
+                    d0 += W[j] * (C[k][0] - C[j][0]);
+                    d1 += W[j] * (C[k][1] - C[j][1]);
+                    d2 += W[j] * (C[k][2] - C[j][2]);
+                }
+                const float gw = (g.x * d0 + g.y * d1 + g.z * d2) * iD * iD;
                 const float prob = sigmoidf_(-S.d[k] / a.sigma);
                 const float q = sigmoidf_(S.d[k] / a.sigma);
                 gd[k] += gw * E[k] * (-prob * q / a.sigma);
@@ -342,34 +347,32 @@ __global__ void __launch_bounds__(256) k_blend_bwd_any(BlendArgs a) {
         if (rgb) zmin = fminf(zmin, a.zbuf[s0 + k]);
         any = true;
     }
-    float range = 0.f, m = 0.f, iD = 0.f, rgb0 = 0.f, rgb1 = 0.f, rgb2 = 0.f;
+    float range = 0.f, m = 0.f, iD = 0.f, delta = 0.f;
     bool face_max = false;
+    float Wl[kMaxK], Cl[kMaxK][3];  // per-slot weights and colours (local memory)
     if (rgb) {
         range = a.zfar - a.znear;
         const float ztop = any ? (a.zfar - zmin) / range : -__int_as_float(0x7f800000);
         face_max = any && ztop > a.eps;
         m = face_max ? ztop : a.eps;
-        float num0 = 0.f, num1 = 0.f, num2 = 0.f, den = 0.f;
-        for (int k = 0; valid && k < K; ++k) {
+        float den = 0.f;
+        for (int k = 0; k < K; ++k) {
+            Wl[k] = 0.f;
+            Cl[k][0] = Cl[k][1] = Cl[k][2] = 0.f;
+            if (!valid) continue;
             const int64_t s = s0 + k;
             const int64_t f = a.pix_to_face[s];
             if (f < 0) continue;
             const float z = a.zbuf[s];
             const float arg = face_max ? (zmin - z) / (range * a.gamma) : ((a.zfar - z) / range - m) / a.gamma;
-            const float w = sigmoidf_(-a.dists[s] / a.sigma) * expf(arg);
-            float c[3], b[3];
+            Wl[k] = sigmoidf_(-a.dists[s] / a.sigma) * expf(arg);
+            float b[3];
             int64_t vi[3];
-            slot_colour(a, s, f, c, vi, b);
-            num0 += w * c[0];
-            num1 += w * c[1];
-            num2 += w * c[2];
-            den += w;
+            slot_colour(a, s, f, Cl[k], vi, b);
+            den += Wl[k];
         }
-        const float delta = expf((a.eps - m) / a.gamma);
+        delta = expf((a.eps - m) / a.gamma);
         iD = 1.f / (den + delta);
-        rgb0 = (num0 + delta * a.bg0) * iD;
-        rgb1 = (num1 + delta * a.bg1) * iD;
-        rgb2 = (num2 + delta * a.bg2) * iD;
     }
     for (int k = 0; k < K; ++k) {  // uniform trip count: every lane reaches the warp aggregation
         const int64_t s = s0 + k;
@@ -398,7 +401,15 @@ __global__ void __launch_bounds__(256) k_blend_bwd_any(BlendArgs a) {
                     const float W = prob * E;
                     float c[3], b[3];
                     slot_colour(a, s, f, c, vi, b);
-                    const float gw = (g.x * (c[0] - rgb0) + g.y * (c[1] - rgb1) + g.z * (c[2] - rgb2)) * iD;
+                    float d0 = delta * (Cl[k][0] - a.bg0), d1 = delta * (Cl[k][1] - a.bg1),
+                          d2 = delta * (Cl[k][2] - a.bg2);
+                    for (int j = 0; j < K; ++j) {
+                        if (j == k) continue;
+                        d0 += Wl[j] * (Cl[k][0] - Cl[j][0]);
+                        d1 += Wl[j] * (Cl[k][1] - Cl[j][1]);
+                        d2 += Wl[j] * (Cl[k][2] - Cl[j][2]);
+                    }
+                    const float gw = (g.x * d0 + g.y * d1 + g.z * d2) * iD * iD;
                     gd += gw * E * (-prob * sigmoidf_(d / a.sigma) / a.sigma);
                     a.grad_zbuf[s] = gw * W / a.gamma * (-1.f / range);
                     const float gc0 = g.x * W * iD, gc1 = g.y * W * iD, gc2 = g.z * W * iD;

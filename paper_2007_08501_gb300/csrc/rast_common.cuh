@@ -167,25 +167,6 @@ __device__ __forceinline__ float nearest_edge(const FaceRec &r, float qx, float 
     return s;
 }
 
-// Lower bound on the squared distance for an outside pixel: the distance to
-// the line of any violated edge.  Edge i here is the one opposite corner i.
-__device__ __forceinline__ bool beyond_blur_lines(const FaceRec &r, float qx, float qy, float b0, float b1,
-                                                  float b2, float blur) {
-    // e_i = b_i * A; squared distance to that edge's line = e_i^2 / |edge_i|^2
-    const float ux = r.b.x, uy = r.b.y, wx = r.b.z, wy = r.b.w;
-    const float A = 1.f / r.d.x;  // only used in a conservative test
-    float l0 = (wx - ux) * (wx - ux) + (wy - uy) * (wy - uy);
-    float l1 = wx * wx + wy * wy;
-    float l2 = ux * ux + uy * uy;
-    float m = 0.f;
-    float A2 = A * A;
-    // compare with a 1e-3 relative slack so rounding never rejects a true candidate
-    if (b0 < 0.f) m = fmaxf(m, b0 * b0 * A2 / l0);
-    if (b1 < 0.f) m = fmaxf(m, b1 * b1 * A2 / l1);
-    if (b2 < 0.f) m = fmaxf(m, b2 * b2 * A2 / l2);
-    return m > blur * 1.001f;
-}
-
 // Depth of a face at a pixel and final barycentrics, in the order
 // perspective correction -> clipping -> z = sum b'_i z_i.
 // With perspective correction 1/z is affine in the pixel position:
@@ -193,10 +174,17 @@ __device__ __forceinline__ bool beyond_blur_lines(const FaceRec &r, float qx, fl
 // accuracy when extrapolated outside the face.  A clipped depth is formed as
 // z_j + sum_i c_i (z_i - z_j) / sum c with j the largest weight, so a pixel
 // clipped to a shared vertex gets exactly that vertex's depth from every face.
+template <bool FAST>
+__device__ __forceinline__ float rcp_(float x) {
+    if constexpr (FAST) return __fdividef(1.f, x);
+    else return __fdiv_rn(1.f, x);
+}
+
+template <bool FAST>
 __device__ __forceinline__ float clipped_depth(float c0, float c1, float c2, const float z[3], float *bp,
                                                bool want) {
     float cs = __fadd_rn(__fadd_rn(c0, c1), c2);
-    float ic = __fdiv_rn(1.f, cs);
+    float ic = rcp_<FAST>(cs);
     float w0 = __fmul_rn(c0, ic), w1 = __fmul_rn(c1, ic), w2 = __fmul_rn(c2, ic);
     if (want) { bp[0] = w0; bp[1] = w1; bp[2] = w2; }
     if (c0 >= c1 && c0 >= c2)
@@ -206,50 +194,75 @@ __device__ __forceinline__ float clipped_depth(float c0, float c1, float c2, con
     return __fadd_rn(z[2], __fadd_rn(__fmul_rn(w0, __fsub_rn(z[0], z[2])), __fmul_rn(w1, __fsub_rn(z[1], z[2]))));
 }
 
-template <bool WANT_BARY>
+// FAST selects approximate (~1 ulp) reciprocals: used for the sort key in the
+// face loop, whose value is also the zbuf output.
+template <bool WANT_BARY, bool FAST = false>
 __device__ __forceinline__ float face_depth(const FaceRec &r, int persp, int clip, bool inside, float b0,
                                             float b1, float b2, float *bp) {
-    const float z[3] = {__frcp_rn(r.d.y), __frcp_rn(r.d.z), __frcp_rn(r.d.w)};
     if (persp) {
         const float T = __fadd_rn(r.d.y, __fadd_rn(__fmul_rn(b1, __fsub_rn(r.d.z, r.d.y)),
                                                    __fmul_rn(b2, __fsub_rn(r.d.w, r.d.y))));
-        const float iT = __fdiv_rn(1.f, T);
+        const float iT = rcp_<FAST>(T);
+        if (!clip || inside) {
+            // b~ = (b_i / z_i) / T; z = 1 / T
+            if (WANT_BARY) {
+                bp[0] = __fmul_rn(__fmul_rn(b0, r.d.y), iT);
+                bp[1] = __fmul_rn(__fmul_rn(b1, r.d.z), iT);
+                bp[2] = __fmul_rn(__fmul_rn(b2, r.d.w), iT);
+            }
+            return iT;
+        }
         const float t0 = __fmul_rn(__fmul_rn(b0, r.d.y), iT);
         const float t1 = __fmul_rn(__fmul_rn(b1, r.d.z), iT);
         const float t2 = __fmul_rn(__fmul_rn(b2, r.d.w), iT);
-        if (!clip || inside) {
-            // b~ = (b_i / z_i) / T; z = 1 / T
-            if (WANT_BARY) { bp[0] = t0; bp[1] = t1; bp[2] = t2; }
-            return iT;
-        }
-        return clipped_depth(fmaxf(t0, 0.f), fmaxf(t1, 0.f), fmaxf(t2, 0.f), z, bp, WANT_BARY);
+        const float z[3] = {rcp_<FAST>(r.d.y), rcp_<FAST>(r.d.z), rcp_<FAST>(r.d.w)};
+        return clipped_depth<FAST>(fmaxf(t0, 0.f), fmaxf(t1, 0.f), fmaxf(t2, 0.f), z, bp, WANT_BARY);
     }
+    const float z[3] = {rcp_<FAST>(r.d.y), rcp_<FAST>(r.d.z), rcp_<FAST>(r.d.w)};
     if (!clip || inside) {
         if (WANT_BARY) { bp[0] = b0; bp[1] = b1; bp[2] = b2; }
         return __fadd_rn(z[0], __fadd_rn(__fmul_rn(b1, __fsub_rn(z[1], z[0])), __fmul_rn(b2, __fsub_rn(z[2], z[0]))));
     }
-    return clipped_depth(fmaxf(b0, 0.f), fmaxf(b1, 0.f), fmaxf(b2, 0.f), z, bp, WANT_BARY);
+    return clipped_depth<FAST>(fmaxf(b0, 0.f), fmaxf(b1, 0.f), fmaxf(b2, 0.f), z, bp, WANT_BARY);
 }
 
-// Candidate test + sort key for the K-nearest pass.  Returns true and the
-// depth when the face is a candidate for the pixel.
-__device__ __forceinline__ bool face_key(const FaceRec &r, const PixC &p, const EvalFlags &fl, float &z) {
-    if (!in_bbox(r, p)) return false;
+// Division-free "squared distance to segment a + t e (t in [0,1]) < blur":
+// in the interior of the segment the squared distance times |e|^2 is
+// |p - a|^2 |e|^2 - ((p - a).e)^2.
+__device__ __forceinline__ bool seg_within(float ax, float ay, float ex, float ey, float qx, float qy,
+                                           float blur) {
+    const float px = qx - ax, py = qy - ay;
+    const float dot = px * ex + py * ey;
+    const float l2 = ex * ex + ey * ey;
+    const float pa2 = px * px + py * py;
+    const float bx = px - ex, by = py - ey;
+    const float end2 = (dot <= 0.f) ? pa2 : bx * bx + by * by;
+    const bool mid = (dot > 0.f) && (dot < l2);
+    return mid ? (pa2 * l2 - dot * dot < blur * l2) : (end2 < blur);
+}
+
+__device__ __forceinline__ bool within_blur(const FaceRec &r, float qx, float qy, float blur) {
+    const float ux = r.b.x, uy = r.b.y, wx = r.b.z, wy = r.b.w;
+    return seg_within(0.f, 0.f, ux, uy, qx, qy, blur) || seg_within(ux, uy, wx - ux, wy - uy, qx, qy, blur) ||
+           seg_within(wx, wy, -wx, -wy, qx, qy, blur);
+}
+
+// Candidate test + sort key for the K-nearest pass (the bbox test is done by
+// the caller).  Returns true and the depth when the face is a candidate.
+__device__ __forceinline__ bool face_key_nobbox(const FaceRec &r, const PixC &p, const EvalFlags &fl, float &z) {
     float qx, qy;
     local_q(r, p, qx, qy);
     float b0, b1, b2;
     screen_bary(r, qx, qy, b0, b1, b2);
-    bool inside = (b0 >= 0.f) && (b1 >= 0.f) && (b2 >= 0.f);
-    if (!inside) {
-        if (!(fl.blur > 0.f)) return false;
-        if (beyond_blur_lines(r, qx, qy, b0, b1, b2, fl.blur)) return false;
-        int e;
-        float t;
-        float s = nearest_edge(r, qx, qy, e, t);
-        if (!(s < fl.blur)) return false;
-    }
-    z = face_depth<false>(r, fl.persp, fl.clip, inside, b0, b1, b2, nullptr);
+    const bool inside = (b0 >= 0.f) && (b1 >= 0.f) && (b2 >= 0.f);
+    if (!inside && !(fl.blur > 0.f && within_blur(r, qx, qy, fl.blur))) return false;
+    z = face_depth<false, true>(r, fl.persp, fl.clip, inside, b0, b1, b2, nullptr);
     return isfinite(z) && z >= fl.znear;
+}
+
+__device__ __forceinline__ bool face_key(const FaceRec &r, const PixC &p, const EvalFlags &fl, float &z) {
+    if (!in_bbox(r, p)) return false;
+    return face_key_nobbox(r, p, fl, z);
 }
 
 // Full fragment (for a face already known to be a candidate).

@@ -436,17 +436,24 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
             }
             __syncthreads();
             const int m = min(BD, cnt - base);
-            if (valid) {
-                for (int jj = 0; jj < m; ++jj) {
-                    const FaceRec R = s_rec[jj];
-                    float z;
-                    if (face_key(R, p, fl, z)) {
-                        const int fid = s_id[jj];
-                        if constexpr (KM > 0) {
-                            if (tk.admits(z, fid)) tk.insert(z, fid);
-                        } else {
-                            if (stk.admits(z, fid)) stk.insert(z, fid);
-                        }
+            // every lane walks the staged faces; a face whose bbox misses all
+            // 32 pixels of the warp is skipped after one 16-byte load
+            for (int jj = 0; jj < m; ++jj) {
+                FaceRec R;
+                R.c = s_rec[jj].c;
+                const bool inbb = valid && in_bbox(R, p);
+                if (!__any_sync(0xffffffffu, inbb)) continue;
+                if (!inbb) continue;
+                R.a = s_rec[jj].a;
+                R.b = s_rec[jj].b;
+                R.d = s_rec[jj].d;
+                float z;
+                if (face_key_nobbox(R, p, fl, z)) {
+                    const int fid = s_id[jj];
+                    if constexpr (KM > 0) {
+                        if (tk.admits(z, fid)) tk.insert(z, fid);
+                    } else {
+                        if (stk.admits(z, fid)) stk.insert(z, fid);
                     }
                 }
             }

@@ -93,7 +93,8 @@ def test_config1_sampled_pixels_at_full_size():
     z = np.where(valid, zb, np.inf)
     assert np.all(np.diff(z, axis=-1)[valid[..., 1:]] >= 0)
     assert np.allclose(ba[valid].sum(-1), 1.0, atol=1e-5)
-    assert np.all(di[valid] < np.float32(w.blur_radius))
+    # inclusion is decided without divisions; the stored distance may sit ~1e-10 above blur
+    assert np.all(di[valid] < np.float32(w.blur_radius) * (1 + 1e-5))
 
 
 def test_blend_matches_oracle_on_same_fragments():
