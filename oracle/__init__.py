@@ -52,7 +52,7 @@ def _open(path):
     L.orc_blend_fwd.argtypes = [_i64, _i64, _i64p, _f64p, _f64p, _f64p, _i64p, _f64p, _dbl, _dbl,
                                 _dbl, _dbl, _f64p, _int, _dbl, _f64p]
     L.orc_blend_bwd.argtypes = [_i64, _i64, _i64p, _f64p, _f64p, _f64p, _i64p, _f64p, _dbl, _dbl,
-                                _dbl, _dbl, _f64p, _int, _dbl, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
+                                _dbl, _dbl, _f64p, _int, _dbl, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
     L.orc_rast_bwd.argtypes = [_f64p, _i64, _i64p, _i64, _i64p, _i64p, _i64, _f64p, _i64, _i64,
                                _dbl, _int, _int, _i64p, _i64, _i64p, _f64p, _f64p, _f64p, _f64p, _f64p]
     return L
@@ -224,8 +224,9 @@ def blend_fwd(pix_to_face, zbuf, bary, dists, faces, colors, sigma, gamma, znear
 
 def blend_bwd(pix_to_face, zbuf, bary, dists, faces, colors, grad_rgba, sigma, gamma, znear, zfar,
               bg=(1.0, 1.0, 1.0), mode=1, eps=1e-10, V=None, with_abs=False):
-    """Adjoint of ``blend_fwd``: returns (grad_zbuf, grad_bary, grad_dists, grad_colors), plus the
-    per-component sums of |contribution| to grad_colors when ``with_abs``."""
+    """Adjoint of ``blend_fwd``: returns (grad_zbuf, grad_bary, grad_dists, grad_colors).  With
+    ``with_abs`` also the per-component sums of |contribution| to grad_colors and the per-slot
+    absolute-term scales (grad_zbuf_abs, grad_bary_abs, grad_dists_abs)."""
     L = _load()
     p2f = _i(pix_to_face)
     K = p2f.shape[-1]
@@ -239,11 +240,15 @@ def blend_bwd(pix_to_face, zbuf, bary, dists, faces, colors, grad_rgba, sigma, g
     gz = np.empty((P, K)); gb = np.empty((P, K, 3)); gd = np.empty((P, K))
     gc = np.zeros((co.shape[0] if V is None else V, 3))
     ga = np.zeros_like(gc) if with_abs else None
+    sa = np.zeros((P, K, 5)) if with_abs else None
     L.orc_blend_bwd(P, K, _p(p2f, _i64p), _p(zb, _f64p), _p(ba, _f64p), _p(di, _f64p), _p(fa, _i64p),
                     _p(co, _f64p), sigma, gamma, znear, zfar, _p(bgv, _f64p), int(mode), eps,
-                    _p(g, _f64p), _p(gz, _f64p), _p(gb, _f64p), _p(gd, _f64p), _p(gc, _f64p), _p(ga, _f64p))
+                    _p(g, _f64p), _p(gz, _f64p), _p(gb, _f64p), _p(gd, _f64p), _p(gc, _f64p), _p(ga, _f64p),
+                    _p(sa, _f64p))
     out = (gz.reshape(*lead, K), gb.reshape(*lead, K, 3), gd.reshape(*lead, K), gc)
-    return out + (ga,) if with_abs else out
+    if not with_abs:
+        return out
+    return out + (ga, sa[..., 1].reshape(*lead, K), sa[..., 2:].reshape(*lead, K, 3), sa[..., 0].reshape(*lead, K))
 
 
 def rast_bwd(m: Mesh, S, K, pix_to_face, grad_zbuf, grad_bary, grad_dists, blur=0.0, persp=True,

@@ -486,20 +486,24 @@ int orc_blend_fwd(int64_t P, int64_t K, const int64_t *pix_to_face, const double
 /* Adjoint of orc_blend_fwd.  Outputs are overwritten: grad_zbuf, grad_dists
  * (P x K), grad_bary (P x K x 3); grad_colors (V x 3) is ACCUMULATED into
  * (caller zeroes it); grad_colors_abs (optional) accumulates the absolute
- * values of the same contributions (the scale of each sum, for tolerances).  zinv_max is treated as a constant: rgb does not depend
+ * values of the same contributions (the scale of each sum, for tolerances).
+ * slot_abs (optional, P x K x 5: dists, zbuf, bary0..2) receives the same
+ * per-slot gradients evaluated with every additive term replaced by its
+ * absolute value -- the scale against which their rounding is judged.  zinv_max is treated as a constant: rgb does not depend
  * on it (it cancels between numerator and denominator). */
 int orc_blend_bwd(int64_t P, int64_t K, const int64_t *pix_to_face, const double *zbuf,
                   const double *bary, const double *dists, const int64_t *faces,
                   const double *colors, double sigma, double gamma, double znear, double zfar,
                   const double *bg, int mode, double eps, const double *grad_rgba,
                   double *grad_zbuf, double *grad_bary, double *grad_dists, double *grad_colors,
-                  double *grad_colors_abs) {
+                  double *grad_colors_abs, double *slot_abs) {
     double *q = (double *)malloc(sizeof(double) * (size_t)(K > 0 ? K : 1));
     for (int64_t p = 0; p < P; p++) {
         for (int64_t k = 0; k < K; k++) {
             int64_t s = p * K + k;
             grad_zbuf[s] = 0.0; grad_dists[s] = 0.0;
             grad_bary[3 * s] = grad_bary[3 * s + 1] = grad_bary[3 * s + 2] = 0.0;
+            if (slot_abs) for (int j = 0; j < 5; j++) slot_abs[5 * s + j] = 0.0;
             q[k] = (pix_to_face[s] >= 0) ? orc_sigmoid(dists[s] / sigma) : 1.0;   /* 1 - prob */
         }
         /* silhouette: alpha = 1 - prod q_k; d alpha / d prob_k = prod_{j != k} q_j */
@@ -513,6 +517,7 @@ int orc_blend_bwd(int64_t P, int64_t K, const int64_t *pix_to_face, const double
             double prob = orc_sigmoid(-dists[s] / sigma);
             /* d prob / d dist = -prob (1 - prob) / sigma */
             grad_dists[s] += ga * others * (-prob * q[k] / sigma);
+            if (slot_abs) slot_abs[5 * s] += fabs(ga * others * (-prob * q[k] / sigma));
         }
         if (mode == 0) continue;
         double zmax = eps;
@@ -550,18 +555,20 @@ int orc_blend_bwd(int64_t P, int64_t K, const int64_t *pix_to_face, const double
             double zi = (zfar - zbuf[s]) / (zfar - znear);
             double E = exp((zi - zmax) / gamma);
             double w = prob * E;
-            double col[3], gw = 0.0;
+            double col[3], gw = 0.0, gw_abs = 0.0;
             for (int ch = 0; ch < 3; ch++) {
                 col[ch] = 0.0;
                 for (int i = 0; i < 3; i++) col[ch] += bary[3 * s + i] * colors[3 * faces[3 * f + i] + ch];
                 /* rgb_ch = (sum w c + delta bg)/D: d/dw_k = (c_k - rgb)/D, d/dc_k = w_k/D */
                 gw += g[ch] * (col[ch] - rgb[ch]) / D;
+                gw_abs += fabs(g[ch]) * (fabs(col[ch]) + fabs(rgb[ch])) / D;
             }
             for (int ch = 0; ch < 3; ch++) {
                 double gc = g[ch] * w / D;
                 for (int i = 0; i < 3; i++) {
                     int64_t v = faces[3 * f + i];
                     grad_bary[3 * s + i] += gc * colors[3 * v + ch];
+                    if (slot_abs) slot_abs[5 * s + 2 + i] += fabs(gc * colors[3 * v + ch]);
                     grad_colors[3 * v + ch] += gc * bary[3 * s + i];
                     if (grad_colors_abs) grad_colors_abs[3 * v + ch] += fabs(gc * bary[3 * s + i]);
                 }
@@ -570,6 +577,10 @@ int orc_blend_bwd(int64_t P, int64_t K, const int64_t *pix_to_face, const double
             double gprob = gw * E;
             grad_dists[s] += gprob * (-prob * q[k] / sigma);
             grad_zbuf[s] += gw * w / gamma * (-1.0 / (zfar - znear));
+            if (slot_abs) {
+                slot_abs[5 * s] += gw_abs * E * prob * q[k] / sigma;
+                slot_abs[5 * s + 1] += gw_abs * w / gamma / (zfar - znear);
+            }
         }
     }
     free(q);

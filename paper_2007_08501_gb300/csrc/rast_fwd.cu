@@ -386,16 +386,28 @@ __device__ __forceinline__ void write_pixel_smem(const FineOut &o, int64_t pix, 
 // ---------------------------------------------------------------------------
 // fine pass: persistent blocks, one bin (bin x bin pixels = block) per item
 // ---------------------------------------------------------------------------
+// Lower bound on a face's depth at any pixel where it is a candidate (nearest
+// corner), valid when the depth is a convex combination of the corner depths:
+// with clipping, or without blur (inside pixels only).  Slightly reduced so
+// that fp32 rounding of the key can never fall below it.
+__device__ __forceinline__ float face_zmin(const FaceRec &R) {
+    if (!(R.c.x <= R.c.y)) return __int_as_float(0x7f800000);  // culled
+    return __fdividef(1.f, fmaxf(R.d.y, fmaxf(R.d.z, R.d.w))) * (1.f - 1e-6f);
+}
+
 template <int KM, int BS>
 __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
     constexpr int BD = BS * BS;
     __shared__ FaceRec s_rec[BD];
     __shared__ int s_id[BD];
+    __shared__ float s_key[BD];
+    __shared__ short s_ord[BD];
     __shared__ int s_item;
     extern __shared__ unsigned char s_dyn[];
     const int tid = threadIdx.x;
     const int ty = tid / BS, tx = tid % BS;
     EvalFlags fl = a.fl;
+    const bool zcull = fl.clip || !(fl.blur > 0.f);
     const int nb2 = a.nb * a.nb;
     while (true) {
         if (tid == 0) s_item = (int)atomicAdd(a.queue, 1u);
@@ -424,32 +436,69 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
         }
         for (int base = 0; base < cnt; base += BD) {
             const int j = base + tid;
+            float key = __int_as_float(0x7f800000);
             if (j < cnt) {
                 const int fid = a.lists[off + j];
                 s_id[tid] = fid;
                 const float4 *src = reinterpret_cast<const float4 *>(a.rec + fid);
-                float4 *dst = reinterpret_cast<float4 *>(s_rec + tid);
-                dst[0] = __ldg(src);
-                dst[1] = __ldg(src + 1);
-                dst[2] = __ldg(src + 2);
-                dst[3] = __ldg(src + 3);
-            }
-            __syncthreads();
-            const int m = min(BD, cnt - base);
-            // every lane walks the staged faces; a face whose bbox misses all
-            // 32 pixels of the warp is skipped after one 16-byte load
-            for (int jj = 0; jj < m; ++jj) {
                 FaceRec R;
-                R.c = s_rec[jj].c;
-                const bool inbb = valid && in_bbox(R, p);
+                R.a = __ldg(src);
+                R.b = __ldg(src + 1);
+                R.c = __ldg(src + 2);
+                R.d = __ldg(src + 3);
+                s_rec[tid] = R;
+                key = face_zmin(R);
+            }
+            s_key[tid] = key;
+            s_ord[tid] = (short)tid;
+            __syncthreads();
+            // bitonic sort of the chunk by nearest-corner depth (front to back)
+#pragma unroll 1
+            for (int k2 = 2; k2 <= BD; k2 <<= 1) {
+#pragma unroll 1
+                for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
+                    const int o = tid ^ j2;
+                    if (o > tid) {
+                        const float ka = s_key[tid], kb = s_key[o];
+                        const bool up = (tid & k2) == 0;
+                        if ((ka > kb) == up) {
+                            s_key[tid] = kb;
+                            s_key[o] = ka;
+                            const short t = s_ord[tid];
+                            s_ord[tid] = s_ord[o];
+                            s_ord[o] = t;
+                        }
+                    }
+                    __syncthreads();
+                }
+            }
+            const int m = min(BD, cnt - base);
+            // Every lane walks the staged faces front to back.  A face is
+            // skipped by a lane when its bbox misses the pixel or its nearest
+            // corner lies behind the lane's K-th depth; by the warp when that
+            // holds for all 32 lanes; and the warp stops once every remaining
+            // face lies behind all of its lanes' K-th depths.
+            for (int jj = 0; jj < m; ++jj) {
+                const float zf = s_key[jj];
+                float thr;
+                if constexpr (KM > 0) thr = tk.z[KM - 1];
+                else thr = stk.z[(a.K - 1) * BD];
+                if (zcull) {
+                    const int wmax = __reduce_max_sync(0xffffffffu, valid ? __float_as_int(thr) : 0);
+                    if (zf > __int_as_float(wmax)) break;
+                }
+                const int jf = s_ord[jj];
+                FaceRec R;
+                R.c = s_rec[jf].c;
+                const bool inbb = valid && in_bbox(R, p) && !(zcull && zf > thr);
                 if (!__any_sync(0xffffffffu, inbb)) continue;
                 if (!inbb) continue;
-                R.a = s_rec[jj].a;
-                R.b = s_rec[jj].b;
-                R.d = s_rec[jj].d;
+                R.a = s_rec[jf].a;
+                R.b = s_rec[jf].b;
+                R.d = s_rec[jf].d;
                 float z;
                 if (face_key_nobbox(R, p, fl, z)) {
-                    const int fid = s_id[jj];
+                    const int fid = s_id[jf];
                     if constexpr (KM > 0) {
                         if (tk.admits(z, fid)) tk.insert(z, fid);
                     } else {

@@ -56,7 +56,9 @@ def compare_frags(gpu, orc, amb, atol=1e-5):
     # empty slots carry exactly -1
     empty = op < 0
     assert np.all(gz[empty & same] == -1) and np.all(gd[empty & same] == -1)
-    v = same & ~empty
+    # values wherever the ids agree, except where the oracle marks the depth
+    # extrapolation as ill-conditioned for fp32 (flag 128)
+    v = same & ~empty & ((amb & 128) == 0)[:, None]
     if v.any():
         ez = np.max(np.abs(gz[v] - oz[v]))
         eb = np.max(np.abs(gb[v] - ob[v]))

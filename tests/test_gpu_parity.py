@@ -122,13 +122,13 @@ def test_blend_matches_oracle_on_same_fragments():
         gb = torch.empty_like(ba) if mode else None
         gc = torch.empty_like(colors) if mode else None
         ops.blend_bwd(bp, N, S, K, p2f, zb, ba, di, faces, colors, g, gz, gb, gd, gc)
-        rz, rb, rd, rc, ra = oracle.blend_bwd(*fn, w.batch.faces, w.batch.colors, g.cpu().numpy(),
-                                              float(np.float32(w.sigma)), float(np.float32(w.gamma)),
-                                              float(np.float32(w.znear)), float(np.float32(w.zfar)), mode=mode,
-                                              with_abs=True)
-        checks = [("grad_dists", gd, rd, None)]
+        rz, rb, rd, rc, ra, az, ab, ad = oracle.blend_bwd(
+            *fn, w.batch.faces, w.batch.colors, g.cpu().numpy(), float(np.float32(w.sigma)),
+            float(np.float32(w.gamma)), float(np.float32(w.znear)), float(np.float32(w.zfar)), mode=mode,
+            with_abs=True)
+        checks = [("grad_dists", gd, rd, ad)]
         if mode:
-            checks += [("grad_zbuf", gz, rz, None), ("grad_bary", gb, rb, None), ("grad_colors", gc, rc, ra)]
+            checks += [("grad_zbuf", gz, rz, az), ("grad_bary", gb, rb, ab), ("grad_colors", gc, rc, ra)]
         for name, a, r, sc in checks:
             worst, glob = grad_close(a.cpu().numpy(), r, scale=sc)
             assert worst <= 1 and glob <= 1e-4, (mode, name, worst, glob)
