@@ -79,6 +79,8 @@ extern "C" {
 #define MESHRAST_ERR_WORKSPACE     (-2)   /* workspace too small or not 256-byte aligned */
 #define MESHRAST_ERR_UNSUPPORTED   (-3)   /* e.g. K > 64, bin_size not in {0, 8, 16} */
 #define MESHRAST_ERR_CUDA          (-4)   /* a kernel launch or memset failed */
+#define MESHRAST_ERR_STATIC_TOO_LARGE (-5) /* rast_mesh_fwd_static: the call needs more workspace
+                                              than MESHRAST_STATIC_WORKSPACE_BYTES */
 
 /* ---- status bits (asynchronous, in the workspace) -------------------- */
 #define MESHRAST_ST_BIN_OVERFLOW    1u    /* a bin held more than max_faces_per_bin faces,
@@ -191,6 +193,40 @@ MESHRAST_API int rast_query_status(const void *workspace, uint32_t *status, void
  * max_faces_per_bin and max_bin_entries. */
 MESHRAST_API int rast_bin_occupancy(const rast_params *p, int64_t V, int64_t F, const void *workspace,
                        int32_t *max_count, int64_t *total_entries, void *stream);
+
+/* ---- forward without a caller-supplied workspace -------------------------
+ * Not part of the paper's method; it exists for callers that cannot allocate
+ * device memory at all -- for example a plugin inside a host application
+ * that owns every device allocation and exposes no allocator, or a
+ * real-time loop that must not allocate once it is running -- and so cannot
+ * provide the workspace rast_mesh_fwd asks for.
+ *
+ * rast_mesh_fwd_static computes exactly what rast_mesh_fwd computes, with
+ * the same arguments minus the workspace.  Its workspace is one array of
+ * MESHRAST_STATIC_WORKSPACE_BYTES (16 MiB) built into the library, which
+ * every GPU that loads the library keeps until the process exits; the call
+ * itself allocates nothing.
+ *   - A call whose rast_workspace_bytes() would exceed that size returns
+ *     MESHRAST_ERR_STATIC_TOO_LARGE and enqueues nothing.  As a guide, the
+ *     benchmark batch of 8 x 5,120 faces at 256x256 with bins of 16 needs
+ *     about 3 MiB with max_faces_per_bin = 256.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before capturing any stream on that device.
+ *   - All calls share the one array, and each call starts by resetting what
+ *     it needs.  Calls that overlap on the GPU (two streams, or several host
+ *     threads) race on it: order them on one stream.
+ *   - The status word it leaves is not readable through this API (there is
+ *     no workspace pointer to pass to rast_query_status); outputs follow the
+ *     same rules as rast_mesh_fwd. */
+#define MESHRAST_STATIC_WORKSPACE_BYTES (16u << 20)
+MESHRAST_API int rast_mesh_fwd_static(const rast_params *p,
+                                      const float *verts, int64_t V,
+                                      const int64_t *faces, int64_t F,
+                                      const int64_t *first_face, const int64_t *num_faces,
+                                      const float *cams,
+                                      int64_t *pix_to_face, float *zbuf, float *bary, float *dists,
+                                      void *stream);
 
 /* Static text for a MESHRAST_ERR_* code. */
 MESHRAST_API const char *rast_strerror(int code);

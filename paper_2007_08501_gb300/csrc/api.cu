@@ -384,6 +384,8 @@ const char *rast_strerror(int code) {
         case MESHRAST_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
         case MESHRAST_ERR_UNSUPPORTED: return "unsupported parameters (K > 64 or bin_size not in {0, 8, 16})";
         case MESHRAST_ERR_CUDA: return "CUDA launch failed";
+        case MESHRAST_ERR_STATIC_TOO_LARGE:
+            return "the call needs more workspace than the library's built-in 16 MiB array (use rast_mesh_fwd)";
         default: return "unknown error";
     }
 }

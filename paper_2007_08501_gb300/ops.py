@@ -20,6 +20,8 @@ MESHRAST_ERR_INVALID_ARG = -1
 MESHRAST_ERR_WORKSPACE = -2
 MESHRAST_ERR_UNSUPPORTED = -3
 MESHRAST_ERR_CUDA = -4
+MESHRAST_ERR_STATIC_TOO_LARGE = -5
+STATIC_WORKSPACE_BYTES = 16 << 20
 
 ST_BIN_OVERFLOW = 1
 ST_BAD_INDEX = 2
@@ -30,7 +32,7 @@ BLEND_SIL = 0
 BLEND_RGB = 1
 
 EXPORTED = ("rast_workspace_bytes", "rast_mesh_fwd", "rast_mesh_bwd", "blend_fwd", "blend_bwd",
-            "rast_query_status", "rast_bin_occupancy", "rast_strerror")
+            "rast_query_status", "rast_bin_occupancy", "rast_strerror", "rast_mesh_fwd_static")
 
 
 class rast_params(ctypes.Structure):
@@ -88,6 +90,8 @@ def load(build_if_missing: bool = False):
     L.rast_bin_occupancy.argtypes = [P, i64, i64, vp, ctypes.POINTER(ctypes.c_int32),
                                      ctypes.POINTER(ctypes.c_int64), vp]
     L.rast_bin_occupancy.restype = ctypes.c_int
+    L.rast_mesh_fwd_static.argtypes = [P, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.rast_mesh_fwd_static.restype = ctypes.c_int
     L.rast_strerror.argtypes = [ctypes.c_int]
     L.rast_strerror.restype = ctypes.c_char_p
     _lib = L
@@ -163,6 +167,23 @@ def rast_mesh_fwd(p, verts, faces, first_face, num_faces, cams, pix_to_face, zbu
         _ptr(bary, torch.float32, "bary"), _ptr(dists, torch.float32, "dists"),
         _ptr(workspace, None, "workspace"), workspace.numel() * workspace.element_size(), _stream(stream))
     _check(rc, "rast_mesh_fwd")
+
+
+def rast_mesh_fwd_static(p, verts, faces, first_face, num_faces, cams, pix_to_face, zbuf, bary, dists,
+                         stream=None, check=True):
+    """rast_mesh_fwd without a workspace argument, for callers that cannot allocate
+    device memory: the library uses its own built-in 16 MiB device array.  Returns
+    the C return code (raises on error when ``check``)."""
+    rc = load().rast_mesh_fwd_static(
+        ctypes.byref(p), _ptr(verts, torch.float32, "verts"), verts.shape[0],
+        _ptr(faces, torch.int64, "faces"), faces.shape[0],
+        _ptr(first_face, torch.int64, "first_face"), _ptr(num_faces, torch.int64, "num_faces"),
+        _ptr(cams, torch.float32, "cams"),
+        _ptr(pix_to_face, torch.int64, "pix_to_face"), _ptr(zbuf, torch.float32, "zbuf"),
+        _ptr(bary, torch.float32, "bary"), _ptr(dists, torch.float32, "dists"), _stream(stream))
+    if check:
+        _check(rc, "rast_mesh_fwd_static")
+    return rc
 
 
 def rast_mesh_bwd(p, verts, faces, first_face, num_faces, cams, pix_to_face, grad_zbuf, grad_bary, grad_dists,

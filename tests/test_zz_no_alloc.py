@@ -1,0 +1,68 @@
+"""rast_mesh_fwd_static: the forward for callers that cannot allocate device
+memory (the library's built-in 16 MiB array stands in for the workspace).
+
+Checked through the C ABI against rast_mesh_fwd on the same inputs, on two
+calls in a row with different batches, so that contents left in the shared
+array by the first call cannot leak into the second.  This file sorts last so
+that a run stopping at the first failure has already run every other test.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2007_08501_gb300 import ops, workloads
+
+pytestmark = pytest.mark.gpu
+
+BLUR = float(np.float32(workloads.BLUR_SIGMA_1E4))
+
+
+def _dev(b):
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return T(b.verts), T(b.faces), T(b.first_face), T(b.num_faces), T(b.cams)
+
+
+def _both(b, S, K, bin_size, max_per_bin, clip=True):
+    v, f, ff, nf, cams = _dev(b)
+    p = ops.make_rast_params(b.N, S, K, BLUR, bin_size, max_per_bin, True, clip)
+    ref = ops.alloc_fragments(b.N, S, K)
+    ws = ops.alloc_workspace(p, b.V, b.F)
+    ops.rast_mesh_fwd(p, v, f, ff, nf, cams, *ref, ws)
+    assert ops.rast_query_status(ws) == 0
+    got = ops.alloc_fragments(b.N, S, K)
+    for t in got:
+        t.fill_(7)          # anything the call fails to write shows up
+    ops.rast_mesh_fwd_static(p, v, f, ff, nf, cams, *got)
+    torch.cuda.synchronize()
+    return ref, got
+
+
+def _same(ref, got):
+    # the same kernels run on the same inputs: identical ids, and values
+    # within the fragment tolerance of the parity tests
+    np.testing.assert_array_equal(ref[0].cpu().numpy(), got[0].cpu().numpy())
+    for a, b in zip(ref[1:], got[1:]):
+        assert np.max(np.abs(a.cpu().numpy() - b.cpu().numpy())) <= 1e-5
+
+
+def test_static_workspace_forward_matches_rast_mesh_fwd_twice():
+    w = workloads.workload(1)
+    ref, got = _both(w.batch, w.image_size, w.K, 16, 256)
+    _same(ref, got)
+    # second call: a different batch, size and bin layout on the same shared array
+    b2 = workloads.sphere_batch([3, 2, 4], 0.05, seed_base=31)
+    ref2, got2 = _both(b2, 100, 3, 8, 512, clip=False)
+    _same(ref2, got2)
+    assert (ref2[0] >= 0).any()
+
+
+def test_static_workspace_rejects_requests_beyond_its_size():
+    b = workloads.sphere_batch([2], 0.05, seed_base=5)
+    v, f, ff, nf, cams = _dev(b)
+    # 1 image at 1024^2 with bins of 8 and 4096 faces per bin needs > 16 MiB of bin lists
+    p = ops.make_rast_params(1, 1024, 1, 0.0, 8, 4096, True, False)
+    assert ops.rast_workspace_bytes(p, b.V, b.F) > ops.STATIC_WORKSPACE_BYTES
+    fr = ops.alloc_fragments(1, 1024, 1)
+    rc = ops.rast_mesh_fwd_static(p, v, f, ff, nf, cams, *fr, check=False)
+    assert rc == ops.MESHRAST_ERR_STATIC_TOO_LARGE
+    assert "16 MiB" in ops.rast_strerror(rc)
