@@ -63,9 +63,16 @@ def compare_frags(gpu, orc, amb, atol=1e-5):
         ez = np.max(np.abs(gz[v] - oz[v]))
         eb = np.max(np.abs(gb[v] - ob[v]))
         ed = np.max(np.abs(gd[v] - od[v]))
-        assert ez <= atol, ("zbuf", ez)
-        assert eb <= atol, ("bary", eb)
-        assert ed <= atol, ("dists", ed)
+
+        def where(err):
+            e = np.where(v, err, -1.0)
+            i = np.unravel_index(np.argmax(e), e.shape)
+            return dict(slot=tuple(int(x) for x in i), face=int(op[i]), gpu_z=float(gz[i]), orc_z=float(oz[i]),
+                        gpu_b=gb[i].tolist(), orc_b=ob[i].tolist(), gpu_d=float(gd[i]), orc_d=float(od[i]),
+                        flags=int(amb[i[0]]))
+        assert ez <= atol, ("zbuf", ez, where(np.abs(gz - oz)))
+        assert eb <= atol, ("bary", eb, where(np.max(np.abs(gb - ob), axis=-1)))
+        assert ed <= atol, ("dists", ed, where(np.abs(gd - od)))
     return int((~ok).sum()), int(bad.size)
 
 
