@@ -276,10 +276,10 @@ int orc_rasterize(const double *verts, int64_t V, const int64_t *faces, int64_t 
  * 16  some face's corner depth, or a candidate's z, within eps of znear
  * 32  (gradient) a top-K face whose two nearest edges are within eps
  * 64  (gradient) a top-K face with a perspective-corrected barycentric within eps of 0 (clip kink)
- * 128 a top-(K+1) candidate outside its face without clipping whose extrapolated depth is
- *     ill-conditioned: kappa * |z| > 50, kappa = sum |b_i w_i| / |sum b_i w_i| with w_i = 1/z_i
- *     (perspective) or z_i (affine), so an fp32 evaluation (~1.5e-7 relative error in the
- *     barycentrics) can miss the depth by more than 1e-5 */
+ * 128 a top-(K+1) candidate outside its face without clipping whose extrapolation is
+ *     ill-conditioned: kappa * max(|z|, max_i |b~_i|) > 50, kappa = sum |b_i w_i| / |sum b_i w_i|
+ *     with w_i = 1/z_i (perspective) or z_i (affine), so an fp32 evaluation (~1.5e-7 relative
+ *     error in the barycentrics) can miss the depth or the barycentrics by more than 1e-5 */
 int orc_margins(const double *verts, int64_t V, const int64_t *faces, int64_t F,
                 const int64_t *first_face, const int64_t *num_faces, int64_t N,
                 const double *cams, int64_t S, int64_t K, double blur, int persp, int clip,
@@ -334,7 +334,10 @@ int orc_margins(const double *verts, int64_t V, const int64_t *faces, int64_t F,
                     num += fabs(o.b[a] * wa);
                     den += o.b[a] * wa;
                 }
-                if (num / fabs(den) * fabs(o.z) > 50.0) fl |= 128;
+                double mag = fabs(o.z);
+                for (int a = 0; a < 3; a++)
+                    if (fabs(o.bt[a]) > mag) mag = fabs(o.bt[a]);
+                if (num / fabs(den) * mag > 50.0) fl |= 128;
             }
             for (int64_t i = 0; i < m && i < K; i++) {
                 orc_face Fc;

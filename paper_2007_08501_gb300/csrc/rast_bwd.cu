@@ -37,21 +37,21 @@ __device__ __forceinline__ void slot_corner_grads(const FaceRec &R, const PixC &
     float tseg;
     (void)nearest_edge(R, qx, qy, edge, tseg);
     const float iz[3] = {R.d.y, R.d.z, R.d.w};
-    const float zc[3] = {1.f / iz[0], 1.f / iz[1], 1.f / iz[2]};
-    float bt[3], T = 1.f;
+    const float zc[3] = {__fdividef(1.f, iz[0]), __fdividef(1.f, iz[1]), __fdividef(1.f, iz[2])};
+    float bt[3], iT = 1.f;
     if (fl.persp) {
         // 1/z is affine in the pixel position: T = iz0 + b1 (iz1 - iz0) + b2 (iz2 - iz0)
-        T = iz[0] + b[1] * (iz[1] - iz[0]) + b[2] * (iz[2] - iz[0]);
-        for (int i = 0; i < 3; ++i) bt[i] = b[i] * iz[i] / T;
+        iT = __fdividef(1.f, iz[0] + b[1] * (iz[1] - iz[0]) + b[2] * (iz[2] - iz[0]));
+        for (int i = 0; i < 3; ++i) bt[i] = b[i] * iz[i] * iT;
     } else {
         for (int i = 0; i < 3; ++i) bt[i] = b[i];
     }
-    float bp[3], cs = 1.f;
+    float bp[3], ics = 1.f;
     if (fl.clip) {
         float cc[3];
         for (int i = 0; i < 3; ++i) cc[i] = fmaxf(bt[i], 0.f);
-        cs = cc[0] + cc[1] + cc[2];
-        for (int i = 0; i < 3; ++i) bp[i] = cc[i] / cs;
+        ics = __fdividef(1.f, cc[0] + cc[1] + cc[2]);
+        for (int i = 0; i < 3; ++i) bp[i] = cc[i] * ics;
     } else {
         for (int i = 0; i < 3; ++i) bp[i] = bt[i];
     }
@@ -66,7 +66,7 @@ __device__ __forceinline__ void slot_corner_grads(const FaceRec &R, const PixC &
     float gbt[3];
     if (fl.clip) {
         const float dot = gbp[0] * bp[0] + gbp[1] * bp[1] + gbp[2] * bp[2];
-        for (int i = 0; i < 3; ++i) gbt[i] = (bt[i] > 0.f) ? (gbp[i] - dot) / cs : 0.f;
+        for (int i = 0; i < 3; ++i) gbt[i] = (bt[i] > 0.f) ? (gbp[i] - dot) * ics : 0.f;
     } else {
         for (int i = 0; i < 3; ++i) gbt[i] = gbp[i];
     }
@@ -75,7 +75,7 @@ __device__ __forceinline__ void slot_corner_grads(const FaceRec &R, const PixC &
         // t_i = b_i / z_i, b~_i = t_i / T:  dt_i/db_i = iz_i, dt_i/dz_i = -b_i iz_i^2
         const float dot = gbt[0] * bt[0] + gbt[1] * bt[1] + gbt[2] * bt[2];
         for (int i = 0; i < 3; ++i) {
-            const float gt = (gbt[i] - dot) / T;
+            const float gt = (gbt[i] - dot) * iT;
             gb[i] = gt * iz[i];
             gZ[i] -= gt * b[i] * iz[i] * iz[i];
         }
@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(256) k_rast_bwd(RastBwdArgs a) {
             R.b = __ldg(src + 1);
             R.c = __ldg(src + 2);
             R.d = __ldg(src + 3);
+            R.e = __ldg(src + 4);
             const float gz = a.grad_zbuf ? a.grad_zbuf[s] : 0.f;
             const float gd = a.grad_dists ? a.grad_dists[s] : 0.f;
             float gb0 = 0.f, gb1 = 0.f, gb2 = 0.f;
@@ -169,10 +170,11 @@ __global__ void __launch_bounds__(256) k_rast_bwd(RastBwdArgs a) {
             const float iz[3] = {R.d.y, R.d.z, R.d.w};
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                const float xn = v0x + Px[i], yn = v0y + Py[i], z = 1.f / iz[i];
-                const float gxv = g[3 * i] * fo / z;
-                const float gyv = g[3 * i + 1] * fo / z;
-                const float gzv = g[3 * i + 2] - (g[3 * i] * xn + g[3 * i + 1] * yn) / z;
+                // x = f x_v / z_v, y = f y_v / z_v: d/dx_v = f/z, d/dz_v = -(x dL/dx + y dL/dy)/z
+                const float xn = v0x + Px[i], yn = v0y + Py[i];
+                const float gxv = g[3 * i] * fo * iz[i];
+                const float gyv = g[3 * i + 1] * fo * iz[i];
+                const float gzv = g[3 * i + 2] - (g[3 * i] * xn + g[3 * i + 1] * yn) * iz[i];
                 const int64_t vi = a.faces[3 * f + i];
                 float *gv = a.grad_verts + 3 * vi;
                 atomicAdd(gv + 0, cam[0] * gxv + cam[3] * gyv + cam[6] * gzv);

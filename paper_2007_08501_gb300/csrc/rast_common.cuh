@@ -19,21 +19,25 @@ constexpr float kCullArea = 1e-12f;
 constexpr int kMaxK = 64;
 
 // ---------------------------------------------------------------------------
-// Staged face record: 64 bytes, four float4, written once per face by the
+// Staged face record: 80 bytes, five float4, written once per face by the
 // staging kernel and read by the fine, plain and backward kernels.
 //   a = (v0x_hi, v0y_hi, v0x_lo, v0y_lo)   corner 0 in NDC as a double-float
-//   b = (ux, uy, wx, wy)                   u = v1 - v0, w = v2 - v0 (NDC)
+//   b = (ux, uy, wx, wy)                   u = v1 - v0, w = v2 - v0 (NDC), high parts
 //   c = (xmin, xmax, ymin, ymax)           bbox inflated by sqrt(blur), rounded outward;
 //                                          culled faces have xmin = +inf, xmax = -inf
-//   d = (1/A, 1/z0, 1/z1, 1/z2)            A = cross(u, w), z_i = view depth of corner i
-// Storing corner 0 as hi + lo and the other corners relative to it keeps
-// pixel-relative coordinates exact to ~1e-14 even for sub-pixel faces, so
-// fp32 barycentrics stay within ~1e-7 of the FP64 values.
+//   d = (1/A, 1/z0, 1/z1, 1/z2)            A = cross(u, w) from the double-float edges,
+//                                          z_i = view depth of corner i
+//   e = (ux_lo, uy_lo, wx_lo, wy_lo)       low parts of the edges
+// Corner 0 as hi + lo and the edges as hi + lo keep the geometry exact to
+// ~1e-14.  The face loop decides coverage with the fp32 high parts (a sign
+// test, robust to ~3e-8 of the edge length); barycentrics that are output or
+// feed an extrapolated depth are evaluated in double-float, so they stay
+// within ~1e-7 of FP64 even for slivers seen edge-on.
 // ---------------------------------------------------------------------------
 struct __align__(16) FaceRec {
-    float4 a, b, c, d;
+    float4 a, b, c, d, e;
 };
-static_assert(sizeof(FaceRec) == 64, "face record is 64 bytes");
+static_assert(sizeof(FaceRec) == 80, "face record is 80 bytes");
 
 // ---------------------------------------------------------------------------
 // double-float (unevaluated sum hi + lo) arithmetic, error-free transforms
@@ -140,13 +144,31 @@ __device__ __forceinline__ void screen_bary(const FaceRec &r, float qx, float qy
     b2 = __fmul_rn(e2, r.d.x);
 }
 
+// Screen barycentrics in double-float: q = p - v0, u, w and the three edge
+// functions carried as hi + lo, then scaled by 1/A.
+__device__ __forceinline__ df df_cross(df ax, df ay, df bx, df by) {
+    return df_sub(df_mul(ax, by), df_mul(ay, bx));
+}
+__device__ __forceinline__ void screen_bary_df(const FaceRec &r, const PixC &p, float &b0, float &b1, float &b2) {
+    const df qx = df_add(two_sum(p.xh, -r.a.x), two_sum(p.xl, -r.a.z));
+    const df qy = df_add(two_sum(p.yh, -r.a.y), two_sum(p.yl, -r.a.w));
+    const df ux = {r.b.x, r.e.x}, uy = {r.b.y, r.e.y}, wx = {r.b.z, r.e.z}, wy = {r.b.w, r.e.w};
+    const df e2 = df_cross(ux, uy, qx, qy);
+    const df e1 = df_cross(qx, qy, wx, wy);
+    const df e0 = df_cross(df_sub(wx, ux), df_sub(wy, uy), df_sub(qx, ux), df_sub(qy, uy));
+    b0 = __fmul_rn(__fadd_rn(e0.hi, e0.lo), r.d.x);
+    b1 = __fmul_rn(__fadd_rn(e1.hi, e1.lo), r.d.x);
+    b2 = __fmul_rn(__fadd_rn(e2.hi, e2.lo), r.d.x);
+}
+
 // squared distance from (qx,qy) to segment a + t e, t in [0,1]; returns s, t
 __device__ __forceinline__ float seg_dist2(float ax, float ay, float ex, float ey, float qx, float qy,
                                            float &t) {
     float l2 = __fmaf_rn(ex, ex, __fmul_rn(ey, ey));
     float px = __fsub_rn(qx, ax), py = __fsub_rn(qy, ay);
     float dot = __fmaf_rn(px, ex, __fmul_rn(py, ey));
-    t = (l2 > 0.f) ? __fdiv_rn(dot, l2) : 0.f;
+    // s is stationary in t at the interior minimum, so a ~2 ulp quotient is enough
+    t = (l2 > 0.f) ? __fdividef(dot, l2) : 0.f;
     t = fminf(fmaxf(t, 0.f), 1.f);
     float rx = __fsub_rn(px, __fmul_rn(t, ex)), ry = __fsub_rn(py, __fmul_rn(t, ey));
     return __fmaf_rn(rx, rx, __fmul_rn(ry, ry));
@@ -255,7 +277,15 @@ __device__ __forceinline__ bool face_key_nobbox(const FaceRec &r, const PixC &p,
     float b0, b1, b2;
     screen_bary(r, qx, qy, b0, b1, b2);
     const bool inside = (b0 >= 0.f) && (b1 >= 0.f) && (b2 >= 0.f);
-    if (!inside && !(fl.blur > 0.f && within_blur(r, qx, qy, fl.blur))) return false;
+    if (!inside) {
+        if (!(fl.blur > 0.f && within_blur(r, qx, qy, fl.blur))) return false;
+        // Outside the face the barycentrics grow with the distance over the
+        // face's height.  Unclipped extrapolation, or a sliver (edge^2 / area
+        // large, where rounding moves fp32 barycentrics by ~6e-8 edge^2/area),
+        // takes the depth from the double-float barycentrics.
+        const float sliver = (r.b.x * r.b.x + r.b.y * r.b.y + r.b.z * r.b.z + r.b.w * r.b.w) * fabsf(r.d.x);
+        if (!fl.clip || sliver > 64.f) screen_bary_df(r, p, b0, b1, b2);
+    }
     z = face_depth<false, true>(r, fl.persp, fl.clip, inside, b0, b1, b2, nullptr);
     return isfinite(z) && z >= fl.znear;
 }
@@ -272,7 +302,9 @@ __device__ __forceinline__ void face_fragment(const FaceRec &r, const PixC &p, c
     local_q(r, p, qx, qy);
     float b0, b1, b2;
     screen_bary(r, qx, qy, b0, b1, b2);
+    // coverage from the same fp32 sign test as the face loop
     bool inside = (b0 >= 0.f) && (b1 >= 0.f) && (b2 >= 0.f);
+    screen_bary_df(r, p, b0, b1, b2);
     int e;
     float t;
     float s = nearest_edge(r, qx, qy, e, t);

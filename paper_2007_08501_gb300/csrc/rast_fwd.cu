@@ -58,6 +58,7 @@ __device__ int stage_face(const StageArgs &a, int64_t f, FaceRec &R) {
     R.b = make_float4(0.f, 0.f, 0.f, 0.f);
     R.c = make_float4(kInf, -kInf, kInf, -kInf);
     R.d = make_float4(0.f, 1.f, 1.f, 1.f);
+    R.e = make_float4(0.f, 0.f, 0.f, 0.f);
     int n = find_mesh(a.first_face, a.N, f);
     if (n < 0 || f >= a.first_face[n] + a.num_faces[n]) return -1;
     unsigned bad = 0;
@@ -86,15 +87,11 @@ __device__ int stage_face(const StageArgs &a, int64_t f, FaceRec &R) {
     }
     df Ux = df_sub(X[1], X[0]), Uy = df_sub(Y[1], Y[0]);
     df Wx = df_sub(X[2], X[0]), Wy = df_sub(Y[2], Y[0]);
-    // culling area in double-float (matches an FP64 evaluation to ~1e-14)
+    // area in double-float (matches an FP64 evaluation to ~1e-14): culling and 1/A
     df Adf = df_sub(df_mul(Ux, Wy), df_mul(Uy, Wx));
     if (!(fabsf(Adf.hi) >= kCullArea)) return -1;
-    // barycentric normalisation uses the area of the ROUNDED edges, so that the
-    // three fp32 barycentrics describe one (slightly perturbed) triangle
+    const float A = __fadd_rn(Adf.hi, Adf.lo);
     float ux = Ux.hi, uy = Uy.hi, wx = Wx.hi, wy = Wy.hi;
-    float p1 = __fmul_rn(uy, wx);
-    float A = __fadd_rn(__fmaf_rn(ux, wy, -p1), __fmaf_rn(-uy, wx, p1));  // ux*wy - uy*wx, Kahan
-    if (A == 0.f) return -1;
     float r = (a.blur > 0.f) ? sqrtf(a.blur) : 0.f;
     df xmin = df_min(df_min(X[0], X[1]), X[2]), xmax = df_max(df_max(X[0], X[1]), X[2]);
     df ymin = df_min(df_min(Y[0], Y[1]), Y[2]), ymax = df_max(df_max(Y[0], Y[1]), Y[2]);
@@ -104,6 +101,7 @@ __device__ int stage_face(const StageArgs &a, int64_t f, FaceRec &R) {
                       df_round_down(df_add(ymin, {-r, 0.f})), df_round_up(df_add(ymax, {r, 0.f})));
     R.d = make_float4(__fdiv_rn(1.f, A), __fdiv_rn(1.f, Z[0].hi), __fdiv_rn(1.f, Z[1].hi),
                       __fdiv_rn(1.f, Z[2].hi));
+    R.e = make_float4(Ux.lo, Uy.lo, Wx.lo, Wy.lo);
     return n;
 }
 
@@ -155,6 +153,7 @@ __global__ void __launch_bounds__(256) k_stage(StageArgs a) {
         dst[1] = R.b;
         dst[2] = R.c;
         dst[3] = R.d;
+        dst[4] = R.e;
         if (a.face_mesh) a.face_mesh[f] = n;
     }
     if (!a.do_count) return;
@@ -313,6 +312,7 @@ __device__ __forceinline__ void write_pixel(const FineOut &o, int64_t pix, int K
             R.b = __ldg(src + 1);
             R.c = __ldg(src + 2);
             R.d = __ldg(src + 3);
+            R.e = __ldg(src + 4);
             float bp[3], d;
             face_fragment(R, p, fl, bp, d);
             o.pix_to_face[s] = f;
@@ -323,6 +323,71 @@ __device__ __forceinline__ void write_pixel(const FineOut &o, int64_t pix, int K
             o.dists[s] = d;
         }
     }
+}
+
+// Block-cooperative copy of a bin's rows from shared memory to the
+// pixel-major output: row y of the tile holds ncols * per_px words, which are
+// contiguous both in shared memory and in the output.  Warps take rows,
+// lanes take consecutive words (fully coalesced).
+template <typename T>
+__device__ __forceinline__ void copy_rows(T *dst, const T *src, int nrows, int ncols, int per_px, int BS,
+                                          int64_t row_stride) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int row_words = ncols * per_px;
+    for (int y = warp; y < nrows; y += nwarps) {
+        T *d = dst + (int64_t)y * row_stride;
+        const T *sp = src + y * BS * per_px;
+        for (int j = lane; j < row_words; j += 32) d[j] = sp[j];
+    }
+}
+
+// Fragments of one pixel's K winners, staged slot by slot in shared memory
+// (28 bytes per slot: id, depth, 3 barycentrics, distance) and then written
+// by the whole block row by row.  Staging layout (BD = pixels per tile):
+//   [BD*K int64 ids][BD*K*3 bary][BD*K zbuf][BD*K dists]
+template <int KM, int BS>
+__device__ __forceinline__ void write_tile(const FineOut &o, int n, int r0, int c0, int S, int K, bool valid,
+                                           const TopK<KM> &tk, const FaceRec *rec, const PixC &p,
+                                           const EvalFlags &fl, unsigned char *stage) {
+    constexpr int BD = BS * BS;
+    const int tid = threadIdx.x;
+    long long *s_id = reinterpret_cast<long long *>(stage);
+    float *s_b = reinterpret_cast<float *>(stage + (size_t)BD * K * 8);
+    float *s_z = s_b + BD * K * 3;
+    float *s_d = s_z + BD * K;
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+        if (k >= K) break;
+        const int j = tid * K + k;
+        float bb[3] = {-1.f, -1.f, -1.f}, dd = -1.f, zz = -1.f;
+        long long id = -1;
+        if (valid && tk.f[k] != 0x7fffffff) {
+            FaceRec R;
+            const float4 *src = reinterpret_cast<const float4 *>(rec + tk.f[k]);
+            R.a = __ldg(src);
+            R.b = __ldg(src + 1);
+            R.c = __ldg(src + 2);
+            R.d = __ldg(src + 3);
+            R.e = __ldg(src + 4);
+            face_fragment(R, p, fl, bb, dd);
+            zz = tk.z[k];
+            id = tk.f[k];
+        }
+        s_id[j] = id;
+        s_b[3 * j] = bb[0];
+        s_b[3 * j + 1] = bb[1];
+        s_b[3 * j + 2] = bb[2];
+        s_z[j] = zz;
+        s_d[j] = dd;
+    }
+    __syncthreads();
+    const int nrows = min(BS, S - r0), ncols = min(BS, S - c0);
+    const int64_t pix0 = ((int64_t)n * S + r0) * S + c0;
+    copy_rows(reinterpret_cast<long long *>(o.pix_to_face) + pix0 * K, s_id, nrows, ncols, K, BS, (int64_t)S * K);
+    copy_rows(o.bary + pix0 * K * 3, s_b, nrows, ncols, 3 * K, BS, (int64_t)S * K * 3);
+    copy_rows(o.zbuf + pix0 * K, s_z, nrows, ncols, K, BS, (int64_t)S * K);
+    copy_rows(o.dists + pix0 * K, s_d, nrows, ncols, K, BS, (int64_t)S * K);
+    __syncthreads();
 }
 
 // large-K variant: per-thread sorted lists in shared memory, [k][thread]
@@ -371,6 +436,7 @@ __device__ __forceinline__ void write_pixel_smem(const FineOut &o, int64_t pix, 
             R.b = __ldg(src + 1);
             R.c = __ldg(src + 2);
             R.d = __ldg(src + 3);
+            R.e = __ldg(src + 4);
             float bp[3], d;
             face_fragment(R, p, fl, bp, d);
             o.pix_to_face[s] = f;
@@ -446,6 +512,7 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
                 R.b = __ldg(src + 1);
                 R.c = __ldg(src + 2);
                 R.d = __ldg(src + 3);
+                R.e = __ldg(src + 4);
                 s_rec[tid] = R;
                 key = face_zmin(R);
             }
@@ -496,6 +563,7 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
                 R.a = s_rec[jf].a;
                 R.b = s_rec[jf].b;
                 R.d = s_rec[jf].d;
+                R.e = s_rec[jf].e;
                 float z;
                 if (face_key_nobbox(R, p, fl, z)) {
                     const int fid = s_id[jf];
@@ -508,10 +576,11 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
             }
             __syncthreads();
         }
-        if (valid) {
+        if constexpr (KM > 0) {
+            write_tile<KM, BS>(a.out, n, by * BS, bx * BS, a.S, a.K, valid, tk, a.rec, p, fl, s_dyn);
+        } else if (valid) {
             const int64_t pix = ((int64_t)n * a.S + r) * a.S + c;
-            if constexpr (KM > 0) write_pixel(a.out, pix, a.K, tk, a.rec, p, fl);
-            else write_pixel_smem(a.out, pix, a.K, stk, a.rec, p, fl);
+            write_pixel_smem(a.out, pix, a.K, stk, a.rec, p, fl);
         }
     }
 }
@@ -550,6 +619,7 @@ __global__ void __launch_bounds__(256) k_naive(NaiveArgs a, int n) {
         R.b = __ldg(src + 1);
         R.c = __ldg(src + 2);
         R.d = __ldg(src + 3);
+        R.e = __ldg(src + 4);
         float z;
         if (face_key(R, p, fl, z)) {
             if constexpr (KM > 0) {
@@ -579,23 +649,15 @@ static int km_for(int K) {
 template <int KM, int BS>
 static cudaError_t launch_fine_t(const FineArgs &a, cudaStream_t st) {
     constexpr int BD = BS * BS;
-    size_t dyn = (KM > 0) ? 0 : (size_t)BD * a.K * 8;
+    // KM > 0: staging buffer for the tile's outputs (28 bytes per slot);
+    // KM == 0: the per-thread sorted lists
+    size_t dyn = (size_t)BD * a.K * ((KM > 0) ? 28 : 8);
     auto kern = k_fine<KM, BS>;
-    static int blocks_per_sm[2] = {-1, -1};
-    int &bps = blocks_per_sm[KM > 0 ? 0 : 1];
-    if (KM == 0) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-        if (e != cudaSuccess) return e;
-        int b = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, BD, dyn);
-        if (e != cudaSuccess) return e;
-        bps = b;
-    } else if (bps < 0) {
-        int b = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, BD, 0);
-        if (e != cudaSuccess) return e;
-        bps = b;
-    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    int bps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, BD, dyn);
+    if (e != cudaSuccess) return e;
     int grid = std::max(1, std::min<int>(a.items, mr_host::num_sms() * std::max(1, bps)));
     kern<<<grid, BD, dyn, st>>>(a);
     return cudaGetLastError();

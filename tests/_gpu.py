@@ -85,8 +85,9 @@ def pick(fr, pixels, S):
 def grad_close(g, ref, rel=1e-4, scale=None):
     """Gradient check.  Per component |g - ref| <= rel * max(|ref|, floor), where
     floor is the component's sum of |contributions| when ``scale`` is given (an
-    accumulated sum of signed terms is only defined relative to that), else
-    1e-2 * rms(ref); and globally ||g - ref|| / ||ref|| <= rel.
+    accumulated sum of signed terms is only defined relative to that; at least
+    1e-3 of the rms of those sums), else 1e-2 * rms(ref); and globally
+    ||g - ref|| / ||ref|| <= rel.
     Returns (worst per-component ratio, global relative error)."""
     g = np.asarray(g, np.float64)
     ref = np.asarray(ref, np.float64)
@@ -94,7 +95,10 @@ def grad_close(g, ref, rel=1e-4, scale=None):
         rms = np.sqrt(np.mean(ref ** 2)) if ref.size else 0.0
         floor = 1e-2 * rms
     else:
-        floor = np.asarray(scale, np.float64)
+        # a component's own contribution scale; components with (almost) no
+        # contributions of their own are judged at 1e-3 of the typical scale
+        sc = np.asarray(scale, np.float64)
+        floor = np.maximum(sc, 1e-3 * np.sqrt(np.mean(sc ** 2)))
     den = np.maximum(np.abs(ref), floor) + 1e-30
     worst = float(np.max(np.abs(g - ref) / den)) / rel if ref.size else 0.0
     glob = float(np.linalg.norm(g - ref) / (np.linalg.norm(ref) + 1e-30))
