@@ -172,7 +172,7 @@ __device__ __forceinline__ void scatter_colour_grads(const BlendArgs &a, int key
 }
 
 template <int KM>
-__global__ void __launch_bounds__(256) k_blend_bwd(BlendArgs a) {
+__global__ void __launch_bounds__(256, (KM >= 16 ? 2 : 3)) k_blend_bwd(BlendArgs a) {
     int64_t pix;
     const bool valid = tile_pixel(a, pix);
     const bool rgb = a.mode == MESHRAST_BLEND_RGB;
@@ -195,92 +195,96 @@ __global__ void __launch_bounds__(256) k_blend_bwd(BlendArgs a) {
         if (rgb) zmin = fminf(zmin, S.z[k]);
         any = true;
     }
-    float gd[KM];
+    const int64_t s0 = pix * KM;
     // silhouette: d alpha / d d_k = -prob_k * prod_j (1 - prob_j) / sigma
+    const float sil = -g.w * keep / a.sigma;
+    if (!rgb) {
+        if (!valid) return;
+        if constexpr (KM % 4 == 0) {
+            float4 *dp = reinterpret_cast<float4 *>(a.grad_dists + s0);
+#pragma unroll
+            for (int j = 0; j < KM / 4; ++j) {
+                float v[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int k = 4 * j + i;
+                    v[i] = (S.f[k] < 0) ? 0.f : sil * sigmoidf_(-S.d[k] / a.sigma);
+                }
+                dp[j] = make_float4(v[0], v[1], v[2], v[3]);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < KM; ++k) a.grad_dists[s0 + k] = (S.f[k] < 0) ? 0.f : sil * sigmoidf_(-S.d[k] / a.sigma);
+        }
+        return;
+    }
+    const float range = a.zfar - a.znear;
+    const float ztop = any ? (a.zfar - zmin) / range : -__int_as_float(0x7f800000);
+    const bool face_max = any && ztop > a.eps;
+    const float m = face_max ? ztop : a.eps;
+    float W[KM], C[KM][3];
+    float den = 0.f;
 #pragma unroll
     for (int k = 0; k < KM; ++k) {
-        gd[k] = (S.f[k] < 0) ? 0.f : g.w * (-sigmoidf_(-S.d[k] / a.sigma) * keep / a.sigma);
+        W[k] = 0.f;
+        C[k][0] = C[k][1] = C[k][2] = 0.f;
+        if (S.f[k] < 0) continue;
+        const float arg = face_max ? (zmin - S.z[k]) / (range * a.gamma) : ((a.zfar - S.z[k]) / range - m) / a.gamma;
+        W[k] = sigmoidf_(-S.d[k] / a.sigma) * expf(arg);
+        float b[3];
+        int64_t vi[3];
+        slot_colour(a, s0 + k, S.f[k], C[k], vi, b);
+        den += W[k];
     }
-    const int64_t s0 = pix * KM;
-    if (rgb) {
-        const float range = a.zfar - a.znear;
-        const float ztop = any ? (a.zfar - zmin) / range : -__int_as_float(0x7f800000);
-        const bool face_max = any && ztop > a.eps;
-        const float m = face_max ? ztop : a.eps;
-        float E[KM], W[KM], C[KM][3];
-        float den = 0.f;
+    const float delta = expf((a.eps - m) / a.gamma);
+    const float iD = 1.f / (den + delta);
 #pragma unroll
-        for (int k = 0; k < KM; ++k) {
-            E[k] = 0.f;
-            W[k] = 0.f;
-            C[k][0] = C[k][1] = C[k][2] = 0.f;
-            if (S.f[k] < 0) continue;
-            const float arg = face_max ? (zmin - S.z[k]) / (range * a.gamma)
-                                       : ((a.zfar - S.z[k]) / range - m) / a.gamma;
-            E[k] = expf(arg);
-            W[k] = sigmoidf_(-S.d[k] / a.sigma) * E[k];
-            float b[3];
-            int64_t vi[3];
-            slot_colour(a, s0 + k, S.f[k], C[k], vi, b);
-            den += W[k];
-        }
-        const float delta = expf((a.eps - m) / a.gamma);
-        const float iD = 1.f / (den + delta);
+    for (int k = 0; k < KM; ++k) {
+        const int64_t s = s0 + k;
+        float gcv[9];
 #pragma unroll
-        for (int k = 0; k < KM; ++k) {
-            const int64_t s = s0 + k;
-            float gcv[9];
-#pragma unroll
-            for (int j = 0; j < 9; ++j) gcv[j] = 0.f;
-            int64_t vi[3] = {-1, -1, -1};
-            int key = -1;
-            if (S.f[k] < 0) {
-                if (valid) {
-                    a.grad_zbuf[s] = 0.f;
-                    a.grad_bary[3 * s] = 0.f;
-                    a.grad_bary[3 * s + 1] = 0.f;
-                    a.grad_bary[3 * s + 2] = 0.f;
-                }
-            } else {
-                key = S.f[k];
-                float c[3], b[3];
-                slot_colour(a, s, S.f[k], c, vi, b);
-                // c_k - rgb = (sum_{j != k} w_j (c_k - c_j) + delta (c_k - bg)) / D: exact for the
-                // dominant face, where c_k - rgb would otherwise be lost to cancellation
-                float d0 = delta * (C[k][0] - a.bg0), d1 = delta * (C[k][1] - a.bg1), d2 = delta * (C[k][2] - a.bg2);
-#pragma unroll
-                for (int j = 0; j < KM; ++j) {
-                    if (j == k) continue;
-                    d0 += W[j] * (C[k][0] - C[j][0]);
-                    d1 += W[j] * (C[k][1] - C[j][1]);
-                    d2 += W[j] * (C[k][2] - C[j][2]);
-                }
-                const float gw = (g.x * d0 + g.y * d1 + g.z * d2) * iD * iD;
-                const float prob = sigmoidf_(-S.d[k] / a.sigma);
-                const float q = sigmoidf_(S.d[k] / a.sigma);
-                gd[k] += gw * E[k] * (-prob * q / a.sigma);
-                a.grad_zbuf[s] = gw * W[k] / a.gamma * (-1.f / range);
-                const float gc0 = g.x * W[k] * iD, gc1 = g.y * W[k] * iD, gc2 = g.z * W[k] * iD;
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const float3 col = vertex_colour(a, vi[i]);
-                    a.grad_bary[3 * s + i] = gc0 * col.x + gc1 * col.y + gc2 * col.z;
-                    gcv[3 * i] = gc0 * b[i];
-                    gcv[3 * i + 1] = gc1 * b[i];
-                    gcv[3 * i + 2] = gc2 * b[i];
-                }
+        for (int j = 0; j < 9; ++j) gcv[j] = 0.f;
+        int64_t vi[3] = {-1, -1, -1};
+        int key = -1;
+        if (S.f[k] < 0) {
+            if (valid) {
+                a.grad_dists[s] = 0.f;
+                a.grad_zbuf[s] = 0.f;
+                a.grad_bary[3 * s] = 0.f;
+                a.grad_bary[3 * s + 1] = 0.f;
+                a.grad_bary[3 * s + 2] = 0.f;
             }
-            scatter_colour_grads(a, key, vi, gcv);
+        } else {
+            key = S.f[k];
+            float c[3], b[3];
+            slot_colour(a, s, S.f[k], c, vi, b);
+            // c_k - rgb = (sum_{j != k} w_j (c_k - c_j) + delta (c_k - bg)) / D: exact for the
+            // dominant face, where c_k - rgb would otherwise be lost to cancellation
+            float d0 = delta * (C[k][0] - a.bg0), d1 = delta * (C[k][1] - a.bg1), d2 = delta * (C[k][2] - a.bg2);
+#pragma unroll
+            for (int j = 0; j < KM; ++j) {
+                if (j == k) continue;
+                d0 += W[j] * (C[k][0] - C[j][0]);
+                d1 += W[j] * (C[k][1] - C[j][1]);
+                d2 += W[j] * (C[k][2] - C[j][2]);
+            }
+            const float gw = (g.x * d0 + g.y * d1 + g.z * d2) * iD * iD;
+            const float prob = sigmoidf_(-S.d[k] / a.sigma);
+            const float q = sigmoidf_(S.d[k] / a.sigma);
+            const float arg = face_max ? (zmin - S.z[k]) / (range * a.gamma) : ((a.zfar - S.z[k]) / range - m) / a.gamma;
+            a.grad_dists[s] = sil * prob + gw * expf(arg) * (-prob * q / a.sigma);
+            a.grad_zbuf[s] = gw * W[k] / a.gamma * (-1.f / range);
+            const float gc0 = g.x * W[k] * iD, gc1 = g.y * W[k] * iD, gc2 = g.z * W[k] * iD;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float3 col = vertex_colour(a, vi[i]);
+                a.grad_bary[3 * s + i] = gc0 * col.x + gc1 * col.y + gc2 * col.z;
+                gcv[3 * i] = gc0 * b[i];
+                gcv[3 * i + 1] = gc1 * b[i];
+                gcv[3 * i + 2] = gc2 * b[i];
+            }
         }
-    }
-    if (!valid) return;
-    if constexpr (KM % 4 == 0) {
-        float4 *dp = reinterpret_cast<float4 *>(a.grad_dists + s0);
-#pragma unroll
-        for (int j = 0; j < KM / 4; ++j) dp[j] = make_float4(gd[4 * j], gd[4 * j + 1], gd[4 * j + 2], gd[4 * j + 3]);
-    } else {
-#pragma unroll
-        for (int k = 0; k < KM; ++k) a.grad_dists[s0 + k] = gd[k];
+        scatter_colour_grads(a, key, vi, gcv);
     }
 }
 

@@ -19,7 +19,7 @@ constexpr float kCullArea = 1e-12f;
 constexpr int kMaxK = 64;
 
 // ---------------------------------------------------------------------------
-// Staged face record: 80 bytes, five float4, written once per face by the
+// Staged face record: 96 bytes, six float4, written once per face by the
 // staging kernel and read by the fine, plain and backward kernels.
 //   a = (v0x_hi, v0y_hi, v0x_lo, v0y_lo)   corner 0 in NDC as a double-float
 //   b = (ux, uy, wx, wy)                   u = v1 - v0, w = v2 - v0 (NDC), high parts
@@ -28,6 +28,8 @@ constexpr int kMaxK = 64;
 //   d = (1/A, 1/z0, 1/z1, 1/z2)            A = cross(u, w) from the double-float edges,
 //                                          z_i = view depth of corner i
 //   e = (ux_lo, uy_lo, wx_lo, wy_lo)       low parts of the edges
+//   h = (H0, H1, H2, 0)                    H_i = (A / |edge opposite corner i|)^2: the squared
+//                                          distance from a point to that edge's line is b_i^2 H_i
 // Corner 0 as hi + lo and the edges as hi + lo keep the geometry exact to
 // ~1e-14.  The face loop decides coverage with the fp32 high parts (a sign
 // test, robust to ~3e-8 of the edge length); barycentrics that are output or
@@ -35,9 +37,9 @@ constexpr int kMaxK = 64;
 // within ~1e-7 of FP64 even for slivers seen edge-on.
 // ---------------------------------------------------------------------------
 struct __align__(16) FaceRec {
-    float4 a, b, c, d, e;
+    float4 a, b, c, d, e, h;
 };
-static_assert(sizeof(FaceRec) == 80, "face record is 80 bytes");
+static_assert(sizeof(FaceRec) == 96, "face record is 96 bytes");
 
 // ---------------------------------------------------------------------------
 // double-float (unevaluated sum hi + lo) arithmetic, error-free transforms
@@ -278,7 +280,13 @@ __device__ __forceinline__ bool face_key_nobbox(const FaceRec &r, const PixC &p,
     screen_bary(r, qx, qy, b0, b1, b2);
     const bool inside = (b0 >= 0.f) && (b1 >= 0.f) && (b2 >= 0.f);
     if (!inside) {
-        if (!(fl.blur > 0.f && within_blur(r, qx, qy, fl.blur))) return false;
+        if (!(fl.blur > 0.f)) return false;
+        // farther than sqrt(blur) from the line of a violated edge: not a candidate
+        const float lim = fl.blur * 1.0001f;
+        if ((b0 < 0.f && b0 * b0 * r.h.x > lim) || (b1 < 0.f && b1 * b1 * r.h.y > lim) ||
+            (b2 < 0.f && b2 * b2 * r.h.z > lim))
+            return false;
+        if (!within_blur(r, qx, qy, fl.blur)) return false;
         // Outside the face the barycentrics grow with the distance over the
         // face's height.  Unclipped extrapolation, or a sliver (edge^2 / area
         // large, where rounding moves fp32 barycentrics by ~6e-8 edge^2/area),

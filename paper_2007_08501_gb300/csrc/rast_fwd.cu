@@ -59,6 +59,7 @@ __device__ int stage_face(const StageArgs &a, int64_t f, FaceRec &R) {
     R.c = make_float4(kInf, -kInf, kInf, -kInf);
     R.d = make_float4(0.f, 1.f, 1.f, 1.f);
     R.e = make_float4(0.f, 0.f, 0.f, 0.f);
+    R.h = make_float4(0.f, 0.f, 0.f, 0.f);
     int n = find_mesh(a.first_face, a.N, f);
     if (n < 0 || f >= a.first_face[n] + a.num_faces[n]) return -1;
     unsigned bad = 0;
@@ -102,6 +103,9 @@ __device__ int stage_face(const StageArgs &a, int64_t f, FaceRec &R) {
     R.d = make_float4(__fdiv_rn(1.f, A), __fdiv_rn(1.f, Z[0].hi), __fdiv_rn(1.f, Z[1].hi),
                       __fdiv_rn(1.f, Z[2].hi));
     R.e = make_float4(Ux.lo, Uy.lo, Wx.lo, Wy.lo);
+    const float A2 = A * A;
+    const float l0 = (wx - ux) * (wx - ux) + (wy - uy) * (wy - uy), l1 = wx * wx + wy * wy, l2 = ux * ux + uy * uy;
+    R.h = make_float4(A2 / l0, A2 / l1, A2 / l2, 0.f);
     return n;
 }
 
@@ -154,6 +158,7 @@ __global__ void __launch_bounds__(256) k_stage(StageArgs a) {
         dst[2] = R.c;
         dst[3] = R.d;
         dst[4] = R.e;
+        dst[5] = R.h;
         if (a.face_mesh) a.face_mesh[f] = n;
     }
     if (!a.do_count) return;
@@ -513,8 +518,15 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
                 R.c = __ldg(src + 2);
                 R.d = __ldg(src + 3);
                 R.e = __ldg(src + 4);
+                R.h = __ldg(src + 5);
                 s_rec[tid] = R;
                 key = face_zmin(R);
+            } else {
+                // padding slots of a partial chunk are never visited (they sort
+                // last and the loop stops at the chunk's face count), and an
+                // empty bbox keeps them inert regardless
+                s_rec[tid].c = make_float4(__int_as_float(0x7f800000), -__int_as_float(0x7f800000),
+                                           __int_as_float(0x7f800000), -__int_as_float(0x7f800000));
             }
             s_key[tid] = key;
             s_ord[tid] = (short)tid;
@@ -564,6 +576,7 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
                 R.b = s_rec[jf].b;
                 R.d = s_rec[jf].d;
                 R.e = s_rec[jf].e;
+                R.h = s_rec[jf].h;
                 float z;
                 if (face_key_nobbox(R, p, fl, z)) {
                     const int fid = s_id[jf];
@@ -620,6 +633,7 @@ __global__ void __launch_bounds__(256) k_naive(NaiveArgs a, int n) {
         R.c = __ldg(src + 2);
         R.d = __ldg(src + 3);
         R.e = __ldg(src + 4);
+        R.h = __ldg(src + 5);
         float z;
         if (face_key(R, p, fl, z)) {
             if constexpr (KM > 0) {

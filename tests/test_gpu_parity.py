@@ -63,15 +63,26 @@ def test_large_k_shared_memory_path():
 
 
 @pytest.mark.parametrize("K", [2, 16, 20])
-def test_binned_equals_plain_bitwise(K):
+def test_binned_equals_plain(K):
+    """The binned fine pass evaluates each face relative to its bin's first
+    pixel, the plain form relative to the face's corner 0: face ids agree
+    bitwise on every pixel outside the oracle's 1e-6 ambiguity band (the two
+    roundings differ only within ~1e-8 of an edge), values to fp32 rounding."""
     b = workloads.sphere_batch([4, 3, 5], 0.05, seed_base=5)
     d = to_dev(b)
     S = 100
+    m = oracle_mesh(b)
+    amb = oracle.margins(m, S, K, BLUR, True, True) & oracle.FWD_AMBIGUOUS
+    ok = (amb == 0).reshape(b.N, S, S)
+    assert ok.mean() > 0.5
     ref = np_frags(gpu_fwd(d, S, K, BLUR, 0, True, True)[0])
     for bs in (8, 16):
         got = np_frags(gpu_fwd(d, S, K, BLUR, bs, True, True)[0])
-        for x, y in zip(ref, got):
-            np.testing.assert_array_equal(x, y)
+        np.testing.assert_array_equal(ref[0][ok], got[0][ok])
+        same = (ref[0] == got[0]) & (ref[0] >= 0)
+        for x, y in zip(ref[1:], got[1:]):
+            sel = same if x.ndim == 4 else same[..., None].repeat(3, -1)
+            assert np.max(np.abs(x[sel] - y[sel])) <= 1e-5
 
 
 def test_config1_sampled_pixels_at_full_size():
@@ -135,6 +146,8 @@ def test_blend_matches_oracle_on_same_fragments():
 
 
 def _rast_bwd_check(batch, S, K, blur, bin_size, persp, clip, seed=0):
+    """GPU rasterizer adjoint against the FP64 adjoint conditioned on the GPU's own
+    face selection, upstream gradients zeroed at gradient-ambiguous pixels."""
     d = to_dev(batch)
     fr, _, p, ws = gpu_fwd(d, S, K, blur, bin_size, persp, clip)
     p2f = fr[0]
@@ -148,21 +161,29 @@ def _rast_bwd_check(batch, S, K, blur, bin_size, persp, clip, seed=0):
     gd = (rng.normal(size=(P, K)) * 1e3).astype(np.float32)
     for g in (gz, gb, gd):
         g[amb != 0] = 0
+    # the forward these gradients are conditioned on matches the oracle
+    orc_p2f = oracle.rasterize(m, S, K, blur, persp, clip)[0]
+    fwd_ok = (oracle.margins(m, S, K, blur, persp, clip) & oracle.FWD_AMBIGUOUS) == 0
+    gp = p2f.cpu().numpy().reshape(P, K)
+    assert np.array_equal(gp[fwd_ok], orc_p2f[fwd_ok])
     gv = torch.empty_like(d["verts"])
     T = lambda a: torch.from_numpy(a).cuda().reshape(*p2f.shape, *a.shape[2:])
     ops.rast_mesh_bwd(p, d["verts"], d["faces"], d["first_face"], d["num_faces"], d["cams"], p2f, T(gz), T(gb),
                       T(gd), gv, ws)
-    ref, ref_abs = oracle.rast_bwd(m, S, K, p2f.cpu().numpy().reshape(P, K), gz, gb, gd, blur, persp, clip,
-                                   with_abs=True)
-    worst, glob = grad_close(gv.cpu().numpy(), ref, scale=ref_abs)
-    assert worst <= 1 and glob <= 1e-4, (worst, glob)
+    ref, ref_abs = oracle.rast_bwd(m, S, K, gp, gz, gb, gd, blur, persp, clip, with_abs=True)
+    g = gv.cpu().numpy()
+    worst, glob = grad_close(g, ref, scale=ref_abs)
+    i = np.unravel_index(np.argmax(np.abs(g - ref)), g.shape)
+    assert worst <= 1 and glob <= 1e-4, (worst, glob, dict(vert=[int(x) for x in i], gpu=float(g[i]),
+                                                           orc=float(ref[i]), abs=float(ref_abs[i])))
 
 
 @pytest.mark.parametrize("persp,clip,blur", [(True, True, BLUR), (True, False, BLUR), (False, True, BLUR),
                                              (True, False, 0.0)])
-def test_rast_bwd_matches_oracle_adjoint(persp, clip, blur):
+@pytest.mark.parametrize("bin_size", [0, 16])
+def test_rast_bwd_matches_oracle_adjoint(persp, clip, blur, bin_size):
     b = workloads.sphere_batch([3, 2], 0.05, seed_base=123)
-    _rast_bwd_check(b, 48, 4, blur, 16, persp, clip)
+    _rast_bwd_check(b, 48, 4, blur, bin_size, persp, clip)
 
 
 def test_rast_bwd_shared_vertices_across_images():
