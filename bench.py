@@ -126,7 +126,7 @@ class ClockSampler:
 class Pipeline:
     """Static device buffers + one CUDA graph per C-ABI call."""
 
-    def __init__(self, w, bin_size, max_faces_per_bin, device):
+    def __init__(self, w, bin_size, max_faces_per_bin, device, max_bin_entries=0):
         import torch
         from paper_2007_08501_gb300 import ops
         self.torch, self.ops = torch, ops
@@ -139,7 +139,8 @@ class Pipeline:
         self.colors = T(b.colors)
         self.gimg = T(workloads_upstream(w))
         self.p = ops.make_rast_params(b.N, w.image_size, w.K, np.float32(w.blur_radius), bin_size,
-                                      max_faces_per_bin, w.perspective_correct, w.clip_barycentric_coords)
+                                      max_faces_per_bin, w.perspective_correct, w.clip_barycentric_coords,
+                                      max_bin_entries)
         self.bp = ops.make_blend_params(w.sigma, w.gamma, w.znear, w.zfar, (1.0, 1.0, 1.0), 1e-10,
                                         ops.BLEND_RGB if w.blend_mode == "rgb" else ops.BLEND_SIL)
         self.rgb = w.blend_mode == "rgb"
@@ -288,7 +289,13 @@ def run_ours(args):
     b = w.batch
     slots = b.N * w.image_size * w.image_size * w.K
 
-    pipe = Pipeline(w, bin_size=16, max_faces_per_bin=2048, device=dev)
+    # launch parameters from the autotuner (outside the timed region)
+    from paper_2007_08501_gb300 import tune
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    tuned = tune.tune(T(b.verts), T(b.faces), T(b.first_face), T(b.num_faces), T(b.cams), w.image_size, w.K,
+                      float(np.float32(w.blur_radius)), w.perspective_correct, w.clip_barycentric_coords)
+    pipe = Pipeline(w, bin_size=tuned["bin_size"], max_faces_per_bin=tuned["max_faces_per_bin"], device=dev,
+                    max_bin_entries=tuned["max_bin_entries"])
     pipe.run_eager()
     torch.cuda.synchronize()
     st = pipe.status()
@@ -392,7 +399,9 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": b.N, "image_size": w.image_size, "K": w.K, "faces": b.F,
                        "verts": b.V, "slots": slots, "blur_radius": float(np.float32(w.blur_radius)),
-                       "bin_size": 16, "max_faces_per_bin": 2048, "graph": "one CUDA graph per C-ABI call",
+                       "bin_size": tuned["bin_size"], "max_faces_per_bin": tuned["max_faces_per_bin"],
+                       "max_bin_entries": tuned["max_bin_entries"], "autotuned": True,
+                       "graph": "one CUDA graph per C-ABI call",
                        "l2": "flushed between steps (256 MiB write), outside the timed events",
                        "bin_occupancy": {"max_faces_in_a_bin": mc, "total_entries": tot},
                        "parallelism": "replicas x%d" % world},

@@ -331,9 +331,10 @@ __device__ __forceinline__ void write_pixel(const FineOut &o, int64_t pix, int K
 }
 
 // Block-cooperative copy of a bin's rows from shared memory to the
-// pixel-major output: row y of the tile holds ncols * per_px words, which are
-// contiguous both in shared memory and in the output.  Warps take rows,
-// lanes take consecutive words (fully coalesced).
+// pixel-major output.  In shared memory pixel t of the tile holds its
+// per_px words at t * (per_px + 1) (one word of padding makes the per-thread
+// writes conflict-free); in the output a tile row of ncols pixels is
+// contiguous.  Warps take rows, lanes take consecutive output words.
 template <typename T>
 __device__ __forceinline__ void copy_rows(T *dst, const T *src, int nrows, int ncols, int per_px, int BS,
                                           int64_t row_stride) {
@@ -341,15 +342,18 @@ __device__ __forceinline__ void copy_rows(T *dst, const T *src, int nrows, int n
     const int row_words = ncols * per_px;
     for (int y = warp; y < nrows; y += nwarps) {
         T *d = dst + (int64_t)y * row_stride;
-        const T *sp = src + y * BS * per_px;
-        for (int j = lane; j < row_words; j += 32) d[j] = sp[j];
+        const T *sp = src + y * BS * (per_px + 1);
+        for (int j = lane; j < row_words; j += 32) {
+            const int px = j / per_px, w = j - px * per_px;
+            d[j] = sp[px * (per_px + 1) + w];
+        }
     }
 }
 
 // Fragments of one pixel's K winners, staged slot by slot in shared memory
-// (28 bytes per slot: id, depth, 3 barycentrics, distance) and then written
-// by the whole block row by row.  Staging layout (BD = pixels per tile):
-//   [BD*K int64 ids][BD*K*3 bary][BD*K zbuf][BD*K dists]
+// (id, depth, 3 barycentrics, distance) and then written by the whole block
+// row by row.  Staging layout (BD = pixels per tile, rows padded by one word):
+//   [BD*(K+1) int64 ids][BD*(3K+1) bary][BD*(K+1) zbuf][BD*(K+1) dists]
 template <int KM, int BS>
 __device__ __forceinline__ void write_tile(const FineOut &o, int n, int r0, int c0, int S, int K, bool valid,
                                            const TopK<KM> &tk, const FaceRec *rec, const PixC &p,
@@ -357,13 +361,12 @@ __device__ __forceinline__ void write_tile(const FineOut &o, int n, int r0, int 
     constexpr int BD = BS * BS;
     const int tid = threadIdx.x;
     long long *s_id = reinterpret_cast<long long *>(stage);
-    float *s_b = reinterpret_cast<float *>(stage + (size_t)BD * K * 8);
-    float *s_z = s_b + BD * K * 3;
-    float *s_d = s_z + BD * K;
+    float *s_b = reinterpret_cast<float *>(stage + (size_t)BD * (K + 1) * 8);
+    float *s_z = s_b + BD * (3 * K + 1);
+    float *s_d = s_z + BD * (K + 1);
 #pragma unroll
     for (int k = 0; k < KM; ++k) {
         if (k >= K) break;
-        const int j = tid * K + k;
         float bb[3] = {-1.f, -1.f, -1.f}, dd = -1.f, zz = -1.f;
         long long id = -1;
         if (valid && tk.f[k] != 0x7fffffff) {
@@ -378,12 +381,12 @@ __device__ __forceinline__ void write_tile(const FineOut &o, int n, int r0, int 
             zz = tk.z[k];
             id = tk.f[k];
         }
-        s_id[j] = id;
-        s_b[3 * j] = bb[0];
-        s_b[3 * j + 1] = bb[1];
-        s_b[3 * j + 2] = bb[2];
-        s_z[j] = zz;
-        s_d[j] = dd;
+        s_id[tid * (K + 1) + k] = id;
+        s_b[tid * (3 * K + 1) + 3 * k] = bb[0];
+        s_b[tid * (3 * K + 1) + 3 * k + 1] = bb[1];
+        s_b[tid * (3 * K + 1) + 3 * k + 2] = bb[2];
+        s_z[tid * (K + 1) + k] = zz;
+        s_d[tid * (K + 1) + k] = dd;
     }
     __syncthreads();
     const int nrows = min(BS, S - r0), ncols = min(BS, S - c0);
@@ -663,9 +666,9 @@ static int km_for(int K) {
 template <int KM, int BS>
 static cudaError_t launch_fine_t(const FineArgs &a, cudaStream_t st) {
     constexpr int BD = BS * BS;
-    // KM > 0: staging buffer for the tile's outputs (28 bytes per slot);
-    // KM == 0: the per-thread sorted lists
-    size_t dyn = (size_t)BD * a.K * ((KM > 0) ? 28 : 8);
+    // KM > 0: staging buffer for the tile's outputs (28 bytes per slot, rows
+    // padded by one word); KM == 0: the per-thread sorted lists
+    size_t dyn = (KM > 0) ? (size_t)BD * (8 * (a.K + 1) + 4 * (3 * a.K + 1) + 8 * (a.K + 1)) : (size_t)BD * a.K * 8;
     auto kern = k_fine<KM, BS>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;

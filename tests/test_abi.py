@@ -69,3 +69,10 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(ops.rast_params) == 48
     assert ops.rast_params.max_bin_entries.offset == 40
     assert ctypes.sizeof(ops.blend_params) == 40
+
+
+def test_autotune_capacities_have_headroom():
+    from paper_2007_08501_gb300 import tune
+    per_bin, entries = tune.capacities(218, 138191)
+    assert per_bin % 64 == 0 and per_bin >= 218 * 1.25 and entries >= 138191 * 1.25
+    assert tune.capacities(0, 0) == (64, 1024)

@@ -257,3 +257,15 @@ def test_sub_pixel_faces_keep_bary_precision():
     n_amb, n_bad = compare_frags(pick(np_frags(fr), px, S), orc, amb, atol=2e-6)
     assert n_bad == 0
     assert (orc[0] >= 0).sum() >= 2
+
+
+def test_autotuner_picks_a_non_overflowing_configuration():
+    from paper_2007_08501_gb300 import tune
+    w = workloads.workload(1)
+    d = to_dev(w.batch)
+    best = tune.tune(d["verts"], d["faces"], d["first_face"], d["num_faces"], d["cams"], w.image_size, w.K,
+                     BLUR, True, True, use_cache=False)
+    assert best["bin_size"] in (8, 16)
+    fr, st, _, _ = gpu_fwd(d, w.image_size, w.K, BLUR, best["bin_size"], True, True, best["max_faces_per_bin"],
+                           best["max_bin_entries"])
+    assert st == 0
