@@ -185,6 +185,9 @@ def margins(m: Mesh, S, K, blur=0.0, persp=True, clip=False, pixels=None, eps=1e
 
 FWD_AMBIGUOUS = 1 | 2 | 4 | 8 | 16 | 128
 GRAD_AMBIGUOUS = FWD_AMBIGUOUS | 32 | 64
+# for gradients conditioned on a given face selection: depth ties (8) and the
+# blur boundary (2) decide which faces are selected, not the adjoint of a slot
+GRAD_COND_AMBIGUOUS = GRAD_AMBIGUOUS & ~(2 | 8)
 
 
 def bins(m: Mesh, S, bin_size, blur=0.0, eps=1e-6):

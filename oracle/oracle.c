@@ -123,6 +123,7 @@ typedef struct {
     int edge;           /* nearest edge: 0 = v0v1, 1 = v1v2, 2 = v2v0 */
     double t;           /* segment parameter on that edge */
     double s_all[3];
+    double t_all[3];
     int candidate;
 } orc_frag;
 
@@ -144,6 +145,7 @@ static void orc_fragment(const orc_face *F, double px, double py, double blur, i
     o->s_all[0] = orc_seg_dist2(v0, v1, px, py, &t01);
     o->s_all[1] = orc_seg_dist2(v1, v2, px, py, &t12);
     o->s_all[2] = orc_seg_dist2(v2, v0, px, py, &t20);
+    o->t_all[0] = t01; o->t_all[1] = t12; o->t_all[2] = t20;
     o->edge = 0; o->s = o->s_all[0]; o->t = t01;
     if (o->s_all[1] < o->s) { o->edge = 1; o->s = o->s_all[1]; o->t = t12; }
     if (o->s_all[2] < o->s) { o->edge = 2; o->s = o->s_all[2]; o->t = t20; }
@@ -274,7 +276,8 @@ int orc_rasterize(const double *verts, int64_t V, const int64_t *faces, int64_t 
  *  4  some face's |A| within eps (relative) of the cull threshold
  *  8  two of the first K+1 sorted candidates have depths within eps
  * 16  some face's corner depth, or a candidate's z, within eps of znear
- * 32  (gradient) a top-K face whose two nearest edges are within eps
+ * 32  (gradient) a top-K face whose two nearest edge segments are within eps in distance
+ *     but reach different points (a shared corner is not a tie)
  * 64  (gradient) a top-K face with a perspective-corrected barycentric within eps of 0 (clip kink)
  * 128 a top-(K+1) candidate outside its face without clipping whose extrapolation is
  *     ill-conditioned: kappa * max(|z|, max_i |b~_i|) > 50, kappa = sum |b_i w_i| / |sum b_i w_i|
@@ -345,8 +348,18 @@ int orc_margins(const double *verts, int64_t V, const int64_t *faces, int64_t F,
                 orc_frag o;
                 orc_fragment(&Fc, px, py, blur, persp, clip, znear, &o);
                 double dd[3] = {sqrt(o.s_all[0]), sqrt(o.s_all[1]), sqrt(o.s_all[2])};
+                double nx[3], ny[3];   /* nearest point on each segment */
+                for (int a = 0; a < 3; a++) {
+                    const double *pa = Fc.P[a], *pb = Fc.P[(a + 1) % 3];
+                    nx[a] = pa[0] + o.t_all[a] * (pb[0] - pa[0]);
+                    ny[a] = pa[1] + o.t_all[a] * (pb[1] - pa[1]);
+                }
+                /* a tie only matters when the tied segments reach different points
+                   (two segments meeting at their shared corner give the same gradient) */
                 for (int a = 0; a < 3; a++)
-                    if (a != o.edge && fabs(dd[a] - dd[o.edge]) < eps) fl |= 32;
+                    if (a != o.edge && fabs(dd[a] - dd[o.edge]) < eps &&
+                        hypot(nx[a] - nx[o.edge], ny[a] - ny[o.edge]) > eps)
+                        fl |= 32;
                 if (clip)
                     for (int a = 0; a < 3; a++)
                         if (fabs(o.bt[a]) < eps) fl |= 64;
@@ -608,7 +621,9 @@ static void orc_edge_grad(const double *a, const double *b, double px, double py
  * segment distance to the three NDC corners, then through the projection
  * Jacobian and R^T to world-space vertex positions.  grad_zbuf, grad_bary,
  * grad_dists may be NULL (zero).  grad_verts (V x 3) is ACCUMULATED into;
- * grad_verts_abs (optional) accumulates |contribution| per component. */
+ * grad_verts_abs (optional) accumulates, per component, the magnitudes of the terms
+ * that the projection Jacobian and R^T combine into each contribution (the scale
+ * against which an fp32 evaluation of the sum is judged). */
 int orc_rast_bwd(const double *verts, int64_t V, const int64_t *faces, int64_t F,
                  const int64_t *first_face, const int64_t *num_faces, int64_t N,
                  const double *cams, int64_t S, int64_t K, double blur, int persp, int clip,
@@ -701,10 +716,15 @@ int orc_rast_bwd(const double *verts, int64_t V, const int64_t *faces, int64_t F
                 double gyv = gP[i][1] * fo / pv[2];
                 double gzv = gP[i][2] - gP[i][0] * fo * pv[0] / (pv[2] * pv[2])
                                       - gP[i][1] * fo * pv[1] / (pv[2] * pv[2]);
+                /* magnitudes of the terms combined by the projection Jacobian and R^T */
+                double axv = fabs(gxv), ayv = fabs(gyv);
+                double azv = fabs(gP[i][2]) + fabs(gP[i][0] * fo * pv[0] / (pv[2] * pv[2])) +
+                             fabs(gP[i][1] * fo * pv[1] / (pv[2] * pv[2]));
                 for (int j = 0; j < 3; j++) {
                     double c = R[j] * gxv + R[3 + j] * gyv + R[6 + j] * gzv;
                     grad_verts[3 * vi + j] += c;
-                    if (grad_verts_abs) grad_verts_abs[3 * vi + j] += fabs(c);
+                    if (grad_verts_abs)
+                        grad_verts_abs[3 * vi + j] += fabs(R[j]) * axv + fabs(R[3 + j]) * ayv + fabs(R[6 + j]) * azv;
                 }
             }
         }
