@@ -495,6 +495,22 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
         fl.znear = __ldg(a.cams + 16 * n + 13);
         const bool valid = (r < a.S) && (c < a.S);
         const PixC p = pixel_centre(r, c, a.S);
+        // rectangle spanned by the centres of this warp's valid pixels (x and y
+        // decrease with the column and row index); empty when no lane is valid
+        const int lane = tid & 31;
+        float wx0 = 1.f, wx1 = -1.f, wy0 = 1.f, wy1 = -1.f;
+        {
+            const unsigned cmin = __reduce_min_sync(0xffffffffu, valid ? (unsigned)c : 0xffffffffu);
+            const unsigned cmax = __reduce_max_sync(0xffffffffu, valid ? (unsigned)c : 0u);
+            const unsigned rmin = __reduce_min_sync(0xffffffffu, valid ? (unsigned)r : 0xffffffffu);
+            const unsigned rmax = __reduce_max_sync(0xffffffffu, valid ? (unsigned)r : 0u);
+            if (cmin <= cmax) {
+                wx1 = pc_hi((int)cmin, a.S);
+                wx0 = pc_hi((int)cmax, a.S);
+                wy1 = pc_hi((int)rmin, a.S);
+                wy0 = pc_hi((int)rmax, a.S);
+            }
+        }
         const int cnt = a.eff[item];
         const int off = a.offsets[item];
         TopK<(KM > 0 ? KM : 1)> tk;
@@ -560,33 +576,50 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
             // corner lies behind the lane's K-th depth; by the warp when that
             // holds for all 32 lanes; and the warp stops once every remaining
             // face lies behind all of its lanes' K-th depths.
-            for (int jj = 0; jj < m; ++jj) {
-                const float zf = s_key[jj];
+            // Faces are culled 32 at a time for the whole warp: lane j tests face
+            // jb + j against the rectangle spanned by the warp's pixel centres
+            // and against the warp's largest K-th depth; one ballot names the
+            // faces the warp walks pixel by pixel.  Chunks are sorted front to
+            // back, so the warp stops once a chunk starts behind every lane's
+            // K-th depth.
+            for (int jb = 0; jb < m; jb += 32) {
                 float thr;
                 if constexpr (KM > 0) thr = tk.z[KM - 1];
                 else thr = stk.z[(a.K - 1) * BD];
-                if (zcull) {
-                    const int wmax = __reduce_max_sync(0xffffffffu, valid ? __float_as_int(thr) : 0);
-                    if (zf > __int_as_float(wmax)) break;
+                const float wthr =
+                    __int_as_float(__reduce_max_sync(0xffffffffu, valid ? __float_as_int(thr) : 0));
+                if (zcull && s_key[jb] > wthr) break;
+                const int jl = jb + lane;
+                bool hit = false;
+                if (jl < m) {
+                    const float4 bb = s_rec[s_ord[jl]].c;
+                    hit = bb.x <= wx1 && bb.y >= wx0 && bb.z <= wy1 && bb.w >= wy0 && !(zcull && s_key[jl] > wthr);
                 }
-                const int jf = s_ord[jj];
-                FaceRec R;
-                R.c = s_rec[jf].c;
-                const bool inbb = valid && in_bbox(R, p) && !(zcull && zf > thr);
-                if (!__any_sync(0xffffffffu, inbb)) continue;
-                if (!inbb) continue;
-                R.a = s_rec[jf].a;
-                R.b = s_rec[jf].b;
-                R.d = s_rec[jf].d;
-                R.e = s_rec[jf].e;
-                R.h = s_rec[jf].h;
-                float z;
-                if (face_key_nobbox(R, p, fl, z)) {
-                    const int fid = s_id[jf];
-                    if constexpr (KM > 0) {
-                        if (tk.admits(z, fid)) tk.insert(z, fid);
-                    } else {
-                        if (stk.admits(z, fid)) stk.insert(z, fid);
+                unsigned mask = __ballot_sync(0xffffffffu, hit);
+                while (mask) {
+                    const int jj = jb + __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    if (!valid) continue;
+                    const int jf = s_ord[jj];
+                    FaceRec R;
+                    R.c = s_rec[jf].c;
+                    if (!in_bbox(R, p)) continue;
+                    if constexpr (KM > 0) thr = tk.z[KM - 1];
+                    else thr = stk.z[(a.K - 1) * BD];
+                    if (zcull && s_key[jj] > thr) continue;
+                    R.a = s_rec[jf].a;
+                    R.b = s_rec[jf].b;
+                    R.d = s_rec[jf].d;
+                    R.e = s_rec[jf].e;
+                    R.h = s_rec[jf].h;
+                    float z;
+                    if (face_key_nobbox(R, p, fl, z)) {
+                        const int fid = s_id[jf];
+                        if constexpr (KM > 0) {
+                            if (tk.admits(z, fid)) tk.insert(z, fid);
+                        } else {
+                            if (stk.admits(z, fid)) stk.insert(z, fid);
+                        }
                     }
                 }
             }
