@@ -244,9 +244,15 @@ __global__ void __launch_bounds__(1024) k_scan(ScanArgs a) {
         if (tid == 1023) carry_s = (int)min((int64_t)carry + warp_sums[31], (int64_t)0x7fffffff);
         __syncthreads();
     }
-    atomicMax(&maxc_s, local_max);
-    atomicAdd(&tot_s, local_tot);
-    if (overflow) set_status(a.status, MESHRAST_ST_BIN_OVERFLOW);
+    // block totals: warp reductions first, then one shared atomic per warp
+    local_max = __reduce_max_sync(0xffffffffu, local_max);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) local_tot += __shfl_xor_sync(0xffffffffu, local_tot, o);
+    if (lane == 0) {
+        atomicMax(&maxc_s, local_max);
+        atomicAdd(&tot_s, local_tot);
+    }
+    if (__any_sync(0xffffffffu, overflow) && lane == 0) set_status(a.status, MESHRAST_ST_BIN_OVERFLOW);
     __syncthreads();
     if (tid == 0) {
         a.offsets[a.NB] = carry_s;
@@ -396,6 +402,59 @@ __device__ __forceinline__ void write_tile(const FineOut &o, int n, int r0, int 
     copy_rows(o.zbuf + pix0 * K, s_z, nrows, ncols, K, BS, (int64_t)S * K);
     copy_rows(o.dists + pix0 * K, s_d, nrows, ncols, K, BS, (int64_t)S * K);
     __syncthreads();
+}
+
+// Fragments of one pixel's K winners written directly by the owning thread,
+// 16-byte vector stores when K is a multiple of 4 (ids: K/2, depths and
+// distances: K/4, barycentrics: 3K/4 stores per pixel).
+constexpr bool kStageOutputs = false;
+
+template <int KM>
+__device__ __forceinline__ void write_pixel_vec(const FineOut &o, int64_t pix, int K, const TopK<KM> &tk,
+                                                const FaceRec *rec, const PixC &p, const EvalFlags &fl) {
+    if (K != KM || (KM % 4) != 0) {
+        write_pixel(o, pix, K, tk, rec, p, fl);
+        return;
+    }
+    const int64_t s0 = pix * KM;
+    longlong2 *ip = reinterpret_cast<longlong2 *>(o.pix_to_face + s0);
+    float4 *zp = reinterpret_cast<float4 *>(o.zbuf + s0);
+    float4 *dp = reinterpret_cast<float4 *>(o.dists + s0);
+    float4 *bp = reinterpret_cast<float4 *>(o.bary + s0 * 3);
+#pragma unroll
+    for (int j = 0; j < KM / 2; ++j) {
+        longlong2 v;
+        v.x = (tk.f[2 * j] == 0x7fffffff) ? -1ll : (long long)tk.f[2 * j];
+        v.y = (tk.f[2 * j + 1] == 0x7fffffff) ? -1ll : (long long)tk.f[2 * j + 1];
+        ip[j] = v;
+    }
+    // four slots at a time: one float4 of depths, of distances, three of barycentrics
+#pragma unroll
+    for (int j = 0; j < KM / 4; ++j) {
+        float bb[4][3], dd[4], zz[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int k = 4 * j + i;
+            bb[i][0] = bb[i][1] = bb[i][2] = -1.f;
+            dd[i] = -1.f;
+            zz[i] = -1.f;
+            if (tk.f[k] == 0x7fffffff) continue;
+            FaceRec R;
+            const float4 *src = reinterpret_cast<const float4 *>(rec + tk.f[k]);
+            R.a = __ldg(src);
+            R.b = __ldg(src + 1);
+            R.c = __ldg(src + 2);
+            R.d = __ldg(src + 3);
+            R.e = __ldg(src + 4);
+            face_fragment(R, p, fl, bb[i], dd[i]);
+            zz[i] = tk.z[k];
+        }
+        zp[j] = make_float4(zz[0], zz[1], zz[2], zz[3]);
+        dp[j] = make_float4(dd[0], dd[1], dd[2], dd[3]);
+        bp[3 * j] = make_float4(bb[0][0], bb[0][1], bb[0][2], bb[1][0]);
+        bp[3 * j + 1] = make_float4(bb[1][1], bb[1][2], bb[2][0], bb[2][1]);
+        bp[3 * j + 2] = make_float4(bb[2][2], bb[3][0], bb[3][1], bb[3][2]);
+    }
 }
 
 // large-K variant: per-thread sorted lists in shared memory, [k][thread]
@@ -625,8 +684,10 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
             }
             __syncthreads();
         }
-        if constexpr (KM > 0) {
+        if constexpr (KM > 0 && kStageOutputs) {
             write_tile<KM, BS>(a.out, n, by * BS, bx * BS, a.S, a.K, valid, tk, a.rec, p, fl, s_dyn);
+        } else if constexpr (KM > 0) {
+            if (valid) write_pixel_vec(a.out, ((int64_t)n * a.S + r) * a.S + c, a.K, tk, a.rec, p, fl);
         } else if (valid) {
             const int64_t pix = ((int64_t)n * a.S + r) * a.S + c;
             write_pixel_smem(a.out, pix, a.K, stk, a.rec, p, fl);
@@ -701,10 +762,14 @@ static cudaError_t launch_fine_t(const FineArgs &a, cudaStream_t st) {
     constexpr int BD = BS * BS;
     // KM > 0: staging buffer for the tile's outputs (28 bytes per slot, rows
     // padded by one word); KM == 0: the per-thread sorted lists
-    size_t dyn = (KM > 0) ? (size_t)BD * (8 * (a.K + 1) + 4 * (3 * a.K + 1) + 8 * (a.K + 1)) : (size_t)BD * a.K * 8;
+    size_t dyn = (KM > 0) ? (kStageOutputs ? (size_t)BD * (8 * (a.K + 1) + 4 * (3 * a.K + 1) + 8 * (a.K + 1)) : 0)
+                          : (size_t)BD * a.K * 8;
     auto kern = k_fine<KM, BS>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
+    if (dyn > 0) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+        if (e != cudaSuccess) return e;
+    }
     int bps = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, BD, dyn);
     if (e != cudaSuccess) return e;
