@@ -39,11 +39,11 @@ METRIC = "fwd+bwd raster+blend ms/batch & Mpix·K/s, % HBM roofline, vs per-mesh
 UNIT = "Mpix*K/s"
 WORKLOAD = "8 icospheres level 4 (5,120 faces each, radial N(0,0.05)), random cameras, 256x256, K=8, " \
            "blur=ln(1/1e-4-1)*1e-4, softmax rgb + silhouette (sigma=gamma=1e-4), fwd+bwd to verts"
-KERNELS_PER_STEP = {"rast_fwd": 4, "blend_fwd": 1, "blend_bwd": 1, "rast_bwd": 2}
-# DRAM bytes per launch of the dominant stage from one ncu capture of this
-# workload (profiles/ summary named in the design doc); None until captured for the
-# current kernel source.
-TRAFFIC_BYTES = {}
+KERNELS_PER_STEP = {"rast_fwd": 4, "blend_fwd": 1, "bwd": 2}
+# DRAM bytes (read + write) per launch of each stage's main kernel, from one
+# ncu capture of this workload with the current kernel source (summary in
+# profiles/); a stage without an entry reports null.
+TRAFFIC_BYTES = {"rast_fwd": {"kernel": "k_fine<8,16>", "bytes": 5991680 + 63094784}}
 
 
 def _args():
@@ -54,6 +54,8 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain per-mesh form")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-separate", action="store_true",
+                    help="skip timing the backward as two separate calls (blend_bwd, rast_mesh_bwd)")
     return ap.parse_args()
 
 
@@ -126,7 +128,7 @@ class ClockSampler:
 class Pipeline:
     """Static device buffers + one CUDA graph per C-ABI call."""
 
-    def __init__(self, w, bin_size, max_faces_per_bin, device, max_bin_entries=0):
+    def __init__(self, w, bin_size, max_faces_per_bin, device, max_bin_entries=0, fused=True):
         import torch
         from paper_2007_08501_gb300 import ops
         self.torch, self.ops = torch, ops
@@ -151,17 +153,27 @@ class Pipeline:
         self.gz, self.gb, self.gd = torch.empty_like(zb), torch.empty_like(ba), torch.empty_like(di)
         self.gc = torch.empty_like(self.colors)
         self.gv = torch.empty_like(self.verts)
+        self.fused = fused
         self.graphs = None
 
     def stages(self):
         ops, p2f, zb, ba, di = (self.ops, *self.frag)
         N, S, K = self.N, self.S, self.K
         rgb = self.rgb
-        return [
+        fwd = [
             ("rast_fwd", lambda: ops.rast_mesh_fwd(self.p, self.verts, self.faces, self.ff, self.nf, self.cams,
                                                    p2f, zb, ba, di, self.ws)),
             ("blend_fwd", lambda: ops.blend_fwd(self.bp, N, S, K, p2f, zb, ba, di, self.faces, self.colors,
                                                 self.img)),
+        ]
+        if self.fused:
+            return fwd + [
+                ("bwd", lambda: ops.blend_rast_bwd(self.p, self.bp, self.verts, self.faces, self.ff, self.nf,
+                                                   self.cams, p2f, zb if rgb else None, ba if rgb else None, di,
+                                                   self.colors if rgb else None, self.gimg, self.gv,
+                                                   self.gc if rgb else None, self.ws)),
+            ]
+        return fwd + [
             ("blend_bwd", lambda: ops.blend_bwd(self.bp, N, S, K, p2f, zb, ba, di, self.faces, self.colors,
                                                 self.gimg, self.gz if rgb else None, self.gb if rgb else None,
                                                 self.gd, self.gc if rgb else None)),
@@ -238,7 +250,8 @@ def algorithmic_bytes(w):
         "blend_fwd": 28 * slots + 16 * pix + rgb_extra,                    # read fragments, write rgba
         "blend_bwd": 28 * slots + 16 * pix + 20 * slots + rgb_extra + 12 * V,
         "rast_bwd": mesh_in + 28 * slots + 12 * V,                         # ids + grad fragments
-    }
+        "bwd": mesh_in + 28 * slots + 16 * pix + rgb_extra + 24 * V,       # fused: fragments + grad image in,
+    }                                                                      # vertex + colour grads out
 
 
 def cpu_baseline(w, target_s=15.0):
@@ -338,9 +351,10 @@ def run_ours(args):
     alg = algorithmic_bytes(w)
     peak, peak_kind = _peaks()
     achieved = alg[dom] / (stages[dom] / 1e3) / 1e9
-    traffic = TRAFFIC_BYTES.get(dom)
+    tr = TRAFFIC_BYTES.get(dom)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom,
+                "frac": round(achieved / peak, 4), "traffic": tr["bytes"] if tr else None,
+                "traffic_kernel": tr["kernel"] if tr else None, "algorithmic_bytes": alg[dom], "kernel": dom,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
                 else "fallback 6.8 TB/s"}
     stage_frac = {k: round(alg[k] / (stages[k] / 1e3) / 1e9 / peak, 4) for k in stages}
@@ -377,6 +391,18 @@ def run_ours(args):
     e2e = {"value": round(world * slots / (e2e_ms / 1e3) / 1e6, 1), "unit": UNIT,
            "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
+    separate = None
+    if not args.no_separate:
+        # the same step with the backward as two C-ABI calls (blend_bwd, rast_mesh_bwd)
+        sp = Pipeline(w, bin_size=tuned["bin_size"], max_faces_per_bin=tuned["max_faces_per_bin"], device=dev,
+                      max_bin_entries=tuned["max_bin_entries"], fused=False)
+        sp.capture()
+        ss = timed_steps(sp, args.steps, 3, flush, use_graph=True)
+        sstages = {k: round(statistics.mean(s[k] for s in ss), 4) for k in ss[0]}
+        separate = {"ms_per_step": round(statistics.mean(sum(s.values()) for s in ss), 4),
+                    "blend_bwd_ms": sstages["blend_bwd"], "rast_bwd_ms": sstages["rast_bwd"]}
+        del sp
+
     plain = None
     if not args.no_plain:
         pp = Pipeline(w, bin_size=0, max_faces_per_bin=1, device=dev)
@@ -385,7 +411,7 @@ def run_ours(args):
         pms = statistics.mean(sum(s.values()) for s in ps)
         pstages = {k: round(statistics.mean(s[k] for s in ps), 4) for k in ps[0]}
         plain = {"ms_per_step": round(pms, 4), "value": round(slots / (pms / 1e3) / 1e6, 1),
-                 "rast_fwd_ms": pstages["rast_fwd"], "launches_per_step": b.N + 1 + 1 + 1 + 2,
+                 "rast_fwd_ms": pstages["rast_fwd"], "launches_per_step": b.N + 1 + 1 + 2,
                  "speedup_of_binned": round(pms / ms, 3)}
 
     cpu = None
@@ -402,6 +428,7 @@ def run_ours(args):
                        "bin_size": tuned["bin_size"], "max_faces_per_bin": tuned["max_faces_per_bin"],
                        "max_bin_entries": tuned["max_bin_entries"], "autotuned": True,
                        "graph": "one CUDA graph per C-ABI call",
+                       "backward": "blend_rast_bwd (blend adjoint fused with the rasterizer adjoint)",
                        "l2": "flushed between steps (256 MiB write), outside the timed events",
                        "bin_occupancy": {"max_faces_in_a_bin": mc, "total_entries": tot},
                        "parallelism": "replicas x%d" % world},
@@ -410,7 +437,7 @@ def run_ours(args):
             "stages_hbm_frac": stage_frac,
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": sum(KERNELS_PER_STEP.values()) * args.steps,
-            "clocks": clk, "plain_form": plain, "status": st,
+            "clocks": clk, "unfused_backward": separate, "plain_form": plain, "status": st,
             "wall_s_timed_region": round(wall, 3),
         }
         print(json.dumps(line), flush=True)

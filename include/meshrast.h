@@ -183,6 +183,33 @@ MESHRAST_API int blend_bwd(const blend_params *bp, int64_t N, int64_t S, int64_t
               float *grad_zbuf, float *grad_bary, float *grad_dists, float *grad_vert_colors,
               void *stream);
 
+/* Fused backward of blend_fwd over the output of rast_mesh_fwd: the blend
+ * adjoint (Algorithms 1 and 2) pulled straight through the rasterizer
+ * adjoint (Section 3.2, backward from the cached Fragment data), without
+ * materialising dL/d(zbuf, bary, dists).
+ * Computes what blend_bwd followed by rast_mesh_bwd computes (the latter
+ * given blend_bwd's grad_zbuf, grad_bary, grad_dists; in
+ * MESHRAST_BLEND_SIL mode only grad_dists), up to float rounding order:
+ *   grad_verts (V,3)            overwritten: dL/dverts
+ *   grad_vert_colors (V,3)      overwritten in MESHRAST_BLEND_RGB mode
+ *                               (may be NULL in MESHRAST_BLEND_SIL mode)
+ * p and the geometry are those of the forward; N, S, K come from p.
+ * pix_to_face, zbuf, bary, dists are the forward's Fragments (zbuf, bary and
+ * vert_colors may be NULL in MESHRAST_BLEND_SIL mode); grad_image (N,S,S,4)
+ * is dL/d(image of blend_fwd).  The fragments and grad_image must be
+ * 16-byte aligned.  Uses the workspace like rast_mesh_bwd (the face records
+ * are rebuilt; the status word is left as it is, new bits are ORed in). */
+MESHRAST_API int blend_rast_bwd(const rast_params *p, const blend_params *bp,
+                  const float *verts, int64_t V,
+                  const int64_t *faces, int64_t F,
+                  const int64_t *first_face, const int64_t *num_faces,
+                  const float *cams,
+                  const int64_t *pix_to_face, const float *zbuf, const float *bary,
+                  const float *dists, const float *vert_colors,
+                  const float *grad_image,
+                  float *grad_verts, float *grad_vert_colors,
+                  void *workspace, size_t workspace_bytes, void *stream);
+
 /* Waits for `stream`, then copies the workspace status word to *status
  * (host memory).  Returns MESHRAST_ERR_CUDA if the stream failed. */
 MESHRAST_API int rast_query_status(const void *workspace, uint32_t *status, void *stream);

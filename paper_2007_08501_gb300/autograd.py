@@ -5,7 +5,9 @@ differentiates to the packed vertices through ``rast_mesh_bwd``, which
 recomputes barycentrics, depth and distance from ``pix_to_face`` instead of
 keeping them for the backward pass.  ``blend`` applies Algorithm 1
 (silhouette) or Algorithms 1 + 2 (softmax rgb + silhouette alpha) and
-differentiates through ``blend_bwd``.
+differentiates through ``blend_bwd``.  ``render_meshes`` does both in one
+Function whose backward is ``blend_rast_bwd``: the blend adjoint goes straight
+into the rasterizer adjoint without materialising fragment gradients.
 """
 from __future__ import annotations
 
@@ -141,3 +143,49 @@ def blend(pix_to_face, zbuf, bary, dists, faces=None, colors=None, settings: Ble
         return _Blend.apply(pix_to_face, zbuf, bary, dists, faces, colors, settings)
     dummy = torch.zeros(0, device=pix_to_face.device)
     return _Blend.apply(pix_to_face, zbuf, bary, dists, dummy, dummy, settings)
+
+
+class _Render(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, verts, colors, faces, first_face, num_faces, cams, rs, bs, ws):
+        N = first_face.shape[0]
+        S, K = rs.image_size, rs.faces_per_pixel
+        p = rs.params(N)
+        buf = ws.get(p, verts.shape[0], faces.shape[0])
+        p2f, zbuf, bary, dists = ops.alloc_fragments(N, S, K, verts.device)
+        ops.rast_mesh_fwd(p, verts, faces, first_face, num_faces, cams, p2f, zbuf, bary, dists, buf)
+        img = torch.empty((N, S, S, 4), dtype=torch.float32, device=verts.device)
+        rgb = bs.rgb
+        ops.blend_fwd(bs.params(), N, S, K, p2f, zbuf if rgb else None, bary if rgb else None, dists,
+                      faces if rgb else None, colors if rgb else None, img)
+        ctx.save_for_backward(verts, colors, faces, first_face, num_faces, cams, p2f, zbuf, bary, dists)
+        ctx.rs, ctx.bs, ctx.ws = rs, bs, ws
+        return img
+
+    @staticmethod
+    def backward(ctx, g_img):
+        verts, colors, faces, first_face, num_faces, cams, p2f, zbuf, bary, dists = ctx.saved_tensors
+        rs, bs = ctx.rs, ctx.bs
+        p = rs.params(first_face.shape[0])
+        buf = ctx.ws.get(p, verts.shape[0], faces.shape[0])
+        gv = torch.empty_like(verts)
+        rgb = bs.rgb
+        gc = torch.empty_like(colors) if rgb else None
+        ops.blend_rast_bwd(p, bs.params(), verts, faces, first_face, num_faces, cams, p2f, zbuf if rgb else None,
+                           bary if rgb else None, dists, colors if rgb else None, g_img.contiguous(), gv, gc, buf)
+        return gv, gc, None, None, None, None, None, None, None
+
+
+def render_meshes(verts, faces, first_face, num_faces, cams, raster: RasterSettings, blend: BlendSettings,
+                  colors=None, ws: Workspace = None):
+    """RGBA image (N, S, S, 4) of a packed mesh batch: rasterize, then blend;
+    differentiable in verts (and colors for the softmax blend) through the
+    fused backward."""
+    if ws is None:
+        ws = Workspace(verts.device)
+    if blend.rgb and colors is None:
+        raise ValueError("rgb blending needs per-vertex colours")
+    if colors is None:
+        colors = torch.zeros(0, 3, device=verts.device)
+    return _Render.apply(verts.contiguous(), colors.contiguous(), faces.contiguous(), first_face.contiguous(),
+                         num_faces.contiguous(), cams.contiguous(), raster, blend, ws)

@@ -348,6 +348,65 @@ int blend_bwd(const blend_params *bp, int64_t N, int64_t S, int64_t K, const int
     return mr::launch_blend_bwd(a, st) == cudaSuccess ? MESHRAST_OK : MESHRAST_ERR_CUDA;
 }
 
+int blend_rast_bwd(const rast_params *p, const blend_params *bp, const float *verts, int64_t V,
+                   const int64_t *faces, int64_t F, const int64_t *first_face, const int64_t *num_faces,
+                   const float *cams, const int64_t *pix_to_face, const float *zbuf, const float *bary,
+                   const float *dists, const float *vert_colors, const float *grad_image, float *grad_verts,
+                   float *grad_vert_colors, void *workspace, size_t workspace_bytes, void *stream) {
+    if (!mr_host::check_params(p, V, F)) return MESHRAST_ERR_INVALID_ARG;
+    if (mr_host::unsupported(p)) return MESHRAST_ERR_UNSUPPORTED;
+    const int64_t N = p->N, S = p->image_size, K = p->faces_per_pixel;
+    int rc = check_blend(bp, N, S, K);
+    if (rc) return rc;
+    const bool rgb = bp->mode == MESHRAST_BLEND_RGB;
+    if (N > 0 && (!first_face || !num_faces || !cams)) return MESHRAST_ERR_INVALID_ARG;
+    if (F > 0 && (!faces || (V > 0 && !verts))) return MESHRAST_ERR_INVALID_ARG;
+    if (V > 0 && !grad_verts) return MESHRAST_ERR_INVALID_ARG;
+    if (rgb && (!faces || !vert_colors || (V > 0 && !grad_vert_colors))) return MESHRAST_ERR_INVALID_ARG;
+    const int64_t slots = N * S * S * K;
+    if (slots > 0) {
+        if (!pix_to_face || !dists || !grad_image) return MESHRAST_ERR_INVALID_ARG;
+        if (rgb && (!zbuf || !bary)) return MESHRAST_ERR_INVALID_ARG;
+        if (!aligned16(grad_image) || !aligned16(pix_to_face) || !aligned16(dists) || (zbuf && !aligned16(zbuf)))
+            return MESHRAST_ERR_INVALID_ARG;
+    }
+    WsLayout L;
+    rc = check_ws(p, V, F, workspace, workspace_bytes, &L);
+    if (rc) return rc;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char *ws = reinterpret_cast<char *>(workspace);
+    if (V > 0 && cudaMemsetAsync(grad_verts, 0, (size_t)V * 3 * sizeof(float), st) != cudaSuccess)
+        return MESHRAST_ERR_CUDA;
+    if (rgb && V > 0 && cudaMemsetAsync(grad_vert_colors, 0, (size_t)V * 3 * sizeof(float), st) != cudaSuccess)
+        return MESHRAST_ERR_CUDA;
+    if (slots == 0) return MESHRAST_OK;
+    rc = stage(p, verts, V, faces, F, first_face, num_faces, cams, ws, L, 0, st);
+    if (rc) return rc;
+    mr::BlendArgs a;
+    fill_blend(a, bp, N, S, K, pix_to_face, zbuf, bary, dists, faces, F, vert_colors, V);
+    a.grad_image = grad_image;
+    a.grad_colors = grad_vert_colors;
+    mr::RastBwdArgs r;
+    std::memset(&r, 0, sizeof(r));
+    r.rec = reinterpret_cast<const mr::FaceRec *>(ws + L.records);
+    r.face_mesh = reinterpret_cast<const int *>(ws + L.face_mesh);
+    r.faces = faces;
+    r.verts = verts;
+    r.cams = cams;
+    r.pix_to_face = pix_to_face;
+    r.grad_verts = grad_verts;
+    r.F = F;
+    r.V = V;
+    r.slots = slots;
+    r.S = (int)S;
+    r.K = (int)K;
+    r.fl.persp = p->perspective_correct;
+    r.fl.clip = p->clip_barycentric_coords;
+    r.fl.blur = p->blur_radius;
+    r.fl.znear = 0.f;
+    return mr::launch_blend_rast_bwd(a, r, st) == cudaSuccess ? MESHRAST_OK : MESHRAST_ERR_CUDA;
+}
+
 int rast_query_status(const void *workspace, uint32_t *status, void *stream) {
     if (!workspace || !status) return MESHRAST_ERR_INVALID_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -4,7 +4,7 @@
 // two-pass approach that first assigns faces to image tiles (bins) and then
 // finds, per pixel, the K nearest faces along z with a priority queue, and the
 // Fragment data of those faces.  Launch sequence of one binned forward:
-//   k_stage     one thread per face: double-float projection, 64-byte face
+//   k_stage     one thread per face: double-float projection, 96-byte face
 //               record, warp-aggregated bin counts
 //   k_scan      one block: clamp counts to capacity, exclusive scan -> offsets
 //   k_fill      one thread per face: warp-aggregated atomic append into lists

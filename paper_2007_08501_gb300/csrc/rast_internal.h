@@ -114,5 +114,6 @@ cudaError_t launch_naive(const NaiveArgs &a, int N, cudaStream_t st);
 cudaError_t launch_rast_bwd(const RastBwdArgs &a, int N, cudaStream_t st);
 cudaError_t launch_blend_fwd(const BlendArgs &a, cudaStream_t st);
 cudaError_t launch_blend_bwd(const BlendArgs &a, cudaStream_t st);
+cudaError_t launch_blend_rast_bwd(const BlendArgs &a, const RastBwdArgs &r, cudaStream_t st);
 
 }  // namespace mr

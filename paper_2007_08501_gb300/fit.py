@@ -1,8 +1,9 @@
 """Analysis by synthesis: fit a mesh to target silhouettes, one CUDA graph per step.
 
 Each step renders soft silhouettes of one mesh from several cameras through the
-differentiable rasterizer (``autograd.rasterize_meshes``) and the silhouette
-blend (Algorithm 1), compares them with target silhouettes using the negative
+differentiable rasterizer and the silhouette blend (Algorithm 1),
+``autograd.render_meshes``, whose backward is the fused blend + rasterizer
+adjoint, compares them with target silhouettes using the negative
 IoU of Appendix B,
 
     L_s = 1 - sum(S_p * S_g) / sum(S_p + S_g - S_p * S_g),
@@ -56,9 +57,8 @@ class SilhouetteFitter:
     def _step(self):
         self.opt.zero_grad(set_to_none=False)
         verts = self.base + self.offsets
-        p2f, zb, ba, di = ag.rasterize_meshes(verts, self.faces, self.first_face, self.num_faces, self.cams,
-                                              self.settings, self.ws)
-        img = ag.blend(p2f, zb, ba, di, settings=self.blend)
+        img = ag.render_meshes(verts, self.faces, self.first_face, self.num_faces, self.cams, self.settings,
+                               self.blend, ws=self.ws)
         loss = iou_loss(img[..., 3], self.target)
         loss.backward()
         self.opt.step()

@@ -32,7 +32,8 @@ BLEND_SIL = 0
 BLEND_RGB = 1
 
 EXPORTED = ("rast_workspace_bytes", "rast_mesh_fwd", "rast_mesh_bwd", "blend_fwd", "blend_bwd",
-            "rast_query_status", "rast_bin_occupancy", "rast_strerror", "rast_mesh_fwd_static")
+            "rast_query_status", "rast_bin_occupancy", "rast_strerror", "rast_mesh_fwd_static",
+            "blend_rast_bwd")
 
 
 class rast_params(ctypes.Structure):
@@ -85,6 +86,8 @@ def load(build_if_missing: bool = False):
     L.blend_fwd.restype = ctypes.c_int
     L.blend_bwd.argtypes = [B, i64, i64, i64, vp, vp, vp, vp, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp]
     L.blend_bwd.restype = ctypes.c_int
+    L.blend_rast_bwd.argtypes = [P, B, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.blend_rast_bwd.restype = ctypes.c_int
     L.rast_query_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), vp]
     L.rast_query_status.restype = ctypes.c_int
     L.rast_bin_occupancy.argtypes = [P, i64, i64, vp, ctypes.POINTER(ctypes.c_int32),
@@ -222,6 +225,21 @@ def blend_bwd(bp, N, S, K, pix_to_face, zbuf, bary, dists, faces, vert_colors, g
                           _ptr(grad_bary, torch.float32, "grad_bary"), _ptr(grad_dists, torch.float32, "grad_dists"),
                           _ptr(grad_vert_colors, torch.float32, "grad_vert_colors"), _stream(stream))
     _check(rc, "blend_bwd")
+
+
+def blend_rast_bwd(p, bp, verts, faces, first_face, num_faces, cams, pix_to_face, zbuf, bary, dists, vert_colors,
+                   grad_image, grad_verts, grad_vert_colors, workspace, stream=None):
+    """blend_bwd followed by rast_mesh_bwd in one pass (fragment gradients stay in registers)."""
+    rc = load().blend_rast_bwd(
+        ctypes.byref(p), ctypes.byref(bp), _ptr(verts, torch.float32, "verts"), verts.shape[0],
+        _ptr(faces, torch.int64, "faces"), faces.shape[0],
+        _ptr(first_face, torch.int64, "first_face"), _ptr(num_faces, torch.int64, "num_faces"),
+        _ptr(cams, torch.float32, "cams"), _ptr(pix_to_face, torch.int64, "pix_to_face"),
+        _ptr(zbuf, torch.float32, "zbuf"), _ptr(bary, torch.float32, "bary"), _ptr(dists, torch.float32, "dists"),
+        _ptr(vert_colors, torch.float32, "vert_colors"), _ptr(grad_image, torch.float32, "grad_image"),
+        _ptr(grad_verts, torch.float32, "grad_verts"), _ptr(grad_vert_colors, torch.float32, "grad_vert_colors"),
+        _ptr(workspace, None, "workspace"), workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "blend_rast_bwd")
 
 
 def rast_query_status(workspace, stream=None) -> int:
