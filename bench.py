@@ -37,8 +37,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd raster+blend ms/batch & Mpix·K/s, % HBM roofline, vs per-mesh plain form"
 UNIT = "Mpix*K/s"
-WORKLOAD = "8 icospheres level 4 (5,120 faces each, radial N(0,0.05)), random cameras, 256x256, K=8, " \
-           "blur=ln(1/1e-4-1)*1e-4, softmax rgb + silhouette (sigma=gamma=1e-4), fwd+bwd to verts"
+WORKLOADS = {
+    "1": (1, "", "8 icospheres level 4 (5,120 faces each, radial N(0,0.05)), random cameras, 256x256, K=8, "
+                 "blur=ln(1/1e-4-1)*1e-4, softmax rgb + silhouette (sigma=gamma=1e-4), fwd+bwd to verts"),
+    "2": (2, "", "32 icospheres of levels 3..7 (heterogeneous packed batch, radial N(0,0.03)), random cameras, "
+                 "512x512, K=4, blur=ln(1/1e-4-1)*1e-4, soft silhouette, fwd+bwd to verts"),
+    "3hard": (3, "hard", "1 icosphere level 8 (1,310,720 faces, radial N(0,0.02)), 1024x1024, K=1, blur 0, "
+                         "silhouette, fwd+bwd to verts"),
+    "3soft": (3, "soft", "1 icosphere level 8 (1,310,720 faces, radial N(0,0.02)), 1024x1024, K=8, "
+                         "blur=ln(1/1e-4-1)*1e-4, soft silhouette, fwd+bwd to verts"),
+    "4": (4, "", "1 icosphere level 6 (81,920 faces) seen by 20 cameras (shared vertices), 512x512, K=50, "
+                 "blur=ln(1/1e-4-1)*1e-4, soft silhouette, fwd+bwd to verts"),
+}
 KERNELS_PER_STEP = {"rast_fwd": 4, "blend_fwd": 1, "bwd": 2}
 # DRAM bytes (read + write) per launch of each stage's main kernel, from one
 # ncu capture of this workload with the current kernel source (summary in
@@ -52,8 +62,13 @@ def _args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="1", choices=sorted(WORKLOADS),
+                    help="1 (default, the headline line) or one of the larger parity workloads")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain per-mesh form")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-fit", action="store_true", help="workload 4: skip timing the fitting loop")
+    ap.add_argument("--max-images", type=int, default=0,
+                    help="keep only the first N images of the workload (small cases for profiling)")
     ap.add_argument("--no-separate", action="store_true",
                     help="skip timing the backward as two separate calls (blend_bwd, rast_mesh_bwd)")
     return ap.parse_args()
@@ -244,7 +259,7 @@ def algorithmic_bytes(w):
     slots, pix, V, F = N * S * S * K, N * S * S, b.V, b.F
     cams = 64 * N
     mesh_in = 12 * V + 24 * F + cams + 16 * N
-    rgb_extra = 24 * F + 12 * V          # faces + colours gathered by the rgb blend
+    rgb_extra = 24 * F + 12 * V if w.blend_mode == "rgb" else 0   # faces + colours gathered by the rgb blend
     return {
         "rast_fwd": mesh_in + 28 * slots,                                  # write fragments
         "blend_fwd": 28 * slots + 16 * pix + rgb_extra,                    # read fragments, write rgba
@@ -284,6 +299,49 @@ def cpu_baseline(w, target_s=15.0):
                       "(rasterize all faces per pixel + blend fwd/bwd + adjoint), %.1f s" % (n, per_image, t)}
 
 
+def time_fit_loop(w, tuned, dev, flush, iters=100):
+    """Workload 4's analysis-by-synthesis loop: ``iters`` graph replays of one
+    fitting step (render 20 soft silhouettes, negative IoU, fused backward,
+    Adam) against the silhouettes of a differently seeded sphere."""
+    import torch
+    from paper_2007_08501_gb300 import autograd as ag
+    from paper_2007_08501_gb300 import workloads
+    from paper_2007_08501_gb300.fit import SilhouetteFitter
+    b = w.batch
+    views = b.N
+    F0 = int(b.num_faces[0])
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    verts, faces0, cams = T(b.verts), T(b.faces[:F0]), T(b.cams)
+    # the mesh moves while it is fitted: four times the capacities tuned on the start mesh
+    rs = ag.RasterSettings(w.image_size, w.K, float(np.float32(w.blur_radius)), bin_size=tuned["bin_size"],
+                           max_faces_per_bin=4 * tuned["max_faces_per_bin"],
+                           max_bin_entries=4 * tuned["max_bin_entries"],
+                           clip_barycentric_coords=w.clip_barycentric_coords)
+    bs = ag.BlendSettings(sigma=w.sigma, gamma=w.gamma, znear=w.znear, zfar=w.zfar, rgb=False)
+    tv, tf = workloads.target_sphere()
+    tverts = T(tv.astype(np.float32))
+    tfaces = T(tf.astype(np.int64)).repeat(views, 1)
+    ff = torch.arange(views, device=dev, dtype=torch.int64) * tf.shape[0]
+    nf = torch.full((views,), tf.shape[0], device=dev, dtype=torch.int64)
+    trs = ag.RasterSettings(w.image_size, w.K, float(np.float32(w.blur_radius)), bin_size=tuned["bin_size"],
+                            max_faces_per_bin=4096, clip_barycentric_coords=w.clip_barycentric_coords)
+    with torch.no_grad():
+        target = ag.blend(*ag.rasterize_meshes(tverts, tfaces, ff, nf, cams, trs), settings=bs)[..., 3].clone()
+    fitter = SilhouetteFitter(verts, faces0, cams, target, rs, bs, lr=2e-3).capture(warmup=3)
+    l0 = float(fitter.replay(1))
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    fitter.replay(iters)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"iterations": iters, "ms_per_iteration": round(ms / iters, 4), "loss_first": round(l0, 6),
+            "loss_last": round(float(fitter.loss), 6), "status": fitter.ws.status(),
+            "step": "render 20 soft silhouettes + negative IoU + fused backward + Adam, one CUDA graph"}
+
+
 def run_ours(args):
     import torch
     from paper_2007_08501_gb300 import ops, workloads
@@ -298,7 +356,11 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     ops.load()
-    w = workloads.workload(1)
+    widx, wvar, wdesc = WORKLOADS[args.workload]
+    w = workloads.workload(widx, wvar)
+    if args.max_images:
+        w.batch = workloads.first_images(w.batch, args.max_images)
+        wdesc += " (first %d images)" % w.batch.N
     b = w.batch
     slots = b.N * w.image_size * w.image_size * w.K
 
@@ -315,6 +377,7 @@ def run_ours(args):
     if st != 0:
         raise RuntimeError("device status %d after the first step" % st)
     mc, tot = ops.rast_bin_occupancy(pipe.p, b.V, b.F, pipe.ws)
+    fine_tests = int(tot) * tuned["bin_size"] ** 2
     pipe.capture()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -404,15 +467,19 @@ def run_ours(args):
         del sp
 
     plain = None
-    if not args.no_plain:
+    if not args.no_plain and args.workload == "1":
         pp = Pipeline(w, bin_size=0, max_faces_per_bin=1, device=dev)
-        pp.capture()
-        ps = timed_steps(pp, max(3, args.steps // 2), 2, flush, use_graph=True)
+        pp.run_eager()
+        ps = timed_steps(pp, max(3, args.steps // 2), 2, flush, use_graph=False)
         pms = statistics.mean(sum(s.values()) for s in ps)
         pstages = {k: round(statistics.mean(s[k] for s in ps), 4) for k in ps[0]}
         plain = {"ms_per_step": round(pms, 4), "value": round(slots / (pms / 1e3) / 1e6, 1),
                  "rast_fwd_ms": pstages["rast_fwd"], "launches_per_step": b.N + 1 + 1 + 2,
                  "speedup_of_binned": round(pms / ms, 3)}
+
+    fit_loop = None
+    if args.workload == "4" and not args.no_fit:
+        fit_loop = time_fit_loop(w, tuned, dev, flush)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -423,7 +490,7 @@ def run_ours(args):
             "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": b.N, "image_size": w.image_size, "K": w.K, "faces": b.F,
+            "config": {"workload": wdesc, "N": b.N, "image_size": w.image_size, "K": w.K, "faces": b.F,
                        "verts": b.V, "slots": slots, "blur_radius": float(np.float32(w.blur_radius)),
                        "bin_size": tuned["bin_size"], "max_faces_per_bin": tuned["max_faces_per_bin"],
                        "max_bin_entries": tuned["max_bin_entries"], "autotuned": True,
@@ -437,7 +504,12 @@ def run_ours(args):
             "stages_hbm_frac": stage_frac,
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": sum(KERNELS_PER_STEP.values()) * args.steps,
-            "clocks": clk, "unfused_backward": separate, "plain_form": plain, "status": st,
+            "ms_per_step_median": round(statistics.median(step_ms), 4),
+            "fine_pass": {"face_pixel_tests": fine_tests,
+                          "tests_per_s": round(fine_tests / (stages["rast_fwd"] / 1e3), 1),
+                          "note": "sum over bins of (pixels in bin x faces in bin)"},
+            "clocks": clk, "unfused_backward": separate, "plain_form": plain, "fit_loop": fit_loop,
+            "status": st,
             "wall_s_timed_region": round(wall, 3),
         }
         print(json.dumps(line), flush=True)
@@ -454,19 +526,22 @@ def run_reference(args):
     import oracle
     from paper_2007_08501_gb300 import workloads
     oracle.build()
-    w = workloads.workload(1)
+    widx, wvar, wdesc = WORKLOADS[args.workload]
+    w = workloads.workload(widx, wvar)
     m = oracle.Mesh.from_batch(w.batch)
     blur = float(np.float32(w.blur_radius))
     S, K = w.image_size, w.K
     g_full = workloads.upstream_grad(w.batch.N, S, w.grad_seed)
-    per_image = 256
+    per_image = max(8, 2048 // w.batch.N) if args.workload == "1" else max(4, 256 // w.batch.N)
 
     def step(seed):
         px = workloads.sample_pixels(w.batch.N, S, per_image, seed)
         fr = oracle.rasterize(m, S, K, blur, True, w.clip_barycentric_coords, pixels=px)
         g = g_full[px[:, 0], px[:, 1], px[:, 2]]
-        oracle.blend_fwd(*fr, w.batch.faces, w.batch.colors, w.sigma, w.gamma, w.znear, w.zfar)
-        gz, gb, gd, _ = oracle.blend_bwd(*fr, w.batch.faces, w.batch.colors, g, w.sigma, w.gamma, w.znear, w.zfar)
+        mode = 1 if w.blend_mode == "rgb" else 0
+        oracle.blend_fwd(*fr, w.batch.faces, w.batch.colors, w.sigma, w.gamma, w.znear, w.zfar, mode=mode)
+        gz, gb, gd, _ = oracle.blend_bwd(*fr, w.batch.faces, w.batch.colors, g, w.sigma, w.gamma, w.znear, w.zfar,
+                                         mode=mode)
         oracle.rast_bwd(m, S, K, fr[0], gz, gb, gd, blur, True, w.clip_barycentric_coords, pixels=px)
         return px.shape[0]
 
@@ -484,7 +559,7 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get(
             "WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic", "config": {"workload": WORKLOAD},
+        "dtype": "f64", "data": "synthetic", "config": {"workload": wdesc},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
 

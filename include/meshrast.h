@@ -236,7 +236,7 @@ MESHRAST_API int rast_bin_occupancy(const rast_params *p, int64_t V, int64_t F, 
  *   - A call whose rast_workspace_bytes() would exceed that size returns
  *     MESHRAST_ERR_STATIC_TOO_LARGE and enqueues nothing.  As a guide, a
  *     batch of 8 x 5,120 faces at 256x256 with bins of 16 and
- *     max_faces_per_bin = 256 needs about 6 MiB.
+ *     max_faces_per_bin = 256 needs about 8 MiB.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
  *     before capturing any stream on that device.

@@ -44,7 +44,7 @@ bool ws_layout(const rast_params *p, int64_t V, int64_t F, mr::WsLayout *L) {
         L->cursor = off;
         off = align256(off + (size_t)NB * 4);
         L->lists = off;
-        off = align256(off + (size_t)cap * 4);
+        off = align256(off + (size_t)cap * 8);
     }
     L->bytes = off;
     return true;
@@ -196,12 +196,12 @@ int rast_mesh_fwd(const rast_params *p, const float *verts, int64_t V, const int
     fa.cursor = reinterpret_cast<int *>(ws + L.cursor);
     fa.eff = reinterpret_cast<const int *>(ws + L.eff);
     fa.offsets = reinterpret_cast<const int *>(ws + L.offsets);
-    fa.lists = reinterpret_cast<int *>(ws + L.lists);
+    fa.lists = reinterpret_cast<unsigned long long *>(ws + L.lists);
     if (mr::launch_fill(fa, st) != cudaSuccess) return MESHRAST_ERR_CUDA;
     mr::FineArgs ka;
     ka.rec = reinterpret_cast<const mr::FaceRec *>(ws + L.records);
     ka.cams = cams;
-    ka.lists = reinterpret_cast<const int *>(ws + L.lists);
+    ka.lists = reinterpret_cast<unsigned long long *>(ws + L.lists);
     ka.eff = reinterpret_cast<const int *>(ws + L.eff);
     ka.offsets = reinterpret_cast<const int *>(ws + L.offsets);
     ka.queue = reinterpret_cast<unsigned *>(ws + L.queue);
@@ -211,6 +211,7 @@ int rast_mesh_fwd(const rast_params *p, const float *verts, int64_t V, const int
     ka.K = (int)K;
     ka.fl = fl;
     ka.out = out;
+    ka.sort_cap = mr::fine_sort_cap(p->max_faces_per_bin, (int)K);
     return mr::launch_fine(ka, p->bin_size, st) == cudaSuccess ? MESHRAST_OK : MESHRAST_ERR_CUDA;
 }
 

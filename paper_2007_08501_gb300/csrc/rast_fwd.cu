@@ -264,6 +264,22 @@ __global__ void __launch_bounds__(1024) k_scan(ScanArgs a) {
 // ---------------------------------------------------------------------------
 // fill: warp-aggregated atomic append into the per-bin lists
 // ---------------------------------------------------------------------------
+// Lower bound on a face's depth at any pixel where it is a candidate (nearest
+// corner), valid when the depth is a convex combination of the corner depths:
+// with clipping, or without blur (inside pixels only).  Slightly reduced so
+// that fp32 rounding of the key can never fall below it.
+__device__ __forceinline__ float face_zmin(const FaceRec &R) {
+    if (!(R.c.x <= R.c.y)) return __int_as_float(0x7f800000);  // culled
+    return __fdividef(1.f, fmaxf(R.d.y, fmaxf(R.d.z, R.d.w))) * (1.f - 1e-6f);
+}
+
+// Bin-list entry: nearest-corner depth (a positive float, so its bits order
+// like the value) in the high word, face id in the low word; sorting entries
+// as integers orders a bin's faces front to back, ties by id.
+__device__ __forceinline__ unsigned long long bin_entry(float zmin, int f) {
+    return ((unsigned long long)__float_as_uint(zmin) << 32) | (unsigned)f;
+}
+
 __global__ void __launch_bounds__(256) k_fill(FillArgs a) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int n = -1;
@@ -273,10 +289,12 @@ __global__ void __launch_bounds__(256) k_fill(FillArgs a) {
         if (n >= 0) {
             const float4 *src = reinterpret_cast<const float4 *>(a.rec + f);
             R.c = src[2];
+            R.d = src[3];
         }
     }
     int bx0 = 1, bx1 = 0, by0 = 1, by1 = 0;
     if (n >= 0) bin_rect(R, a.S, a.bin, bx0, bx1, by0, by1);
+    const unsigned long long entry = n >= 0 ? bin_entry(face_zmin(R), (int)f) : 0ull;
     const int nbx = max(0, bx1 - bx0 + 1), nby = max(0, by1 - by0 + 1);
     const int cnt = nbx * nby;
     const int wmax = __reduce_max_sync(0xffffffffu, cnt);
@@ -292,7 +310,7 @@ __global__ void __launch_bounds__(256) k_fill(FillArgs a) {
         base = __shfl_sync(0xffffffffu, base, leader);
         if (key >= 0) {
             int slot = base + __popc(grp & lt);
-            if (slot < a.eff[key]) a.lists[a.offsets[key] + slot] = (int)f;
+            if (slot < a.eff[key]) a.lists[a.offsets[key] + slot] = entry;
         }
     }
 }
@@ -336,78 +354,9 @@ __device__ __forceinline__ void write_pixel(const FineOut &o, int64_t pix, int K
     }
 }
 
-// Block-cooperative copy of a bin's rows from shared memory to the
-// pixel-major output.  In shared memory pixel t of the tile holds its
-// per_px words at t * (per_px + 1) (one word of padding makes the per-thread
-// writes conflict-free); in the output a tile row of ncols pixels is
-// contiguous.  Warps take rows, lanes take consecutive output words.
-template <typename T>
-__device__ __forceinline__ void copy_rows(T *dst, const T *src, int nrows, int ncols, int per_px, int BS,
-                                          int64_t row_stride) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int row_words = ncols * per_px;
-    for (int y = warp; y < nrows; y += nwarps) {
-        T *d = dst + (int64_t)y * row_stride;
-        const T *sp = src + y * BS * (per_px + 1);
-        for (int j = lane; j < row_words; j += 32) {
-            const int px = j / per_px, w = j - px * per_px;
-            d[j] = sp[px * (per_px + 1) + w];
-        }
-    }
-}
-
-// Fragments of one pixel's K winners, staged slot by slot in shared memory
-// (id, depth, 3 barycentrics, distance) and then written by the whole block
-// row by row.  Staging layout (BD = pixels per tile, rows padded by one word):
-//   [BD*(K+1) int64 ids][BD*(3K+1) bary][BD*(K+1) zbuf][BD*(K+1) dists]
-template <int KM, int BS>
-__device__ __forceinline__ void write_tile(const FineOut &o, int n, int r0, int c0, int S, int K, bool valid,
-                                           const TopK<KM> &tk, const FaceRec *rec, const PixC &p,
-                                           const EvalFlags &fl, unsigned char *stage) {
-    constexpr int BD = BS * BS;
-    const int tid = threadIdx.x;
-    long long *s_id = reinterpret_cast<long long *>(stage);
-    float *s_b = reinterpret_cast<float *>(stage + (size_t)BD * (K + 1) * 8);
-    float *s_z = s_b + BD * (3 * K + 1);
-    float *s_d = s_z + BD * (K + 1);
-#pragma unroll
-    for (int k = 0; k < KM; ++k) {
-        if (k >= K) break;
-        float bb[3] = {-1.f, -1.f, -1.f}, dd = -1.f, zz = -1.f;
-        long long id = -1;
-        if (valid && tk.f[k] != 0x7fffffff) {
-            FaceRec R;
-            const float4 *src = reinterpret_cast<const float4 *>(rec + tk.f[k]);
-            R.a = __ldg(src);
-            R.b = __ldg(src + 1);
-            R.c = __ldg(src + 2);
-            R.d = __ldg(src + 3);
-            R.e = __ldg(src + 4);
-            face_fragment(R, p, fl, bb, dd);
-            zz = tk.z[k];
-            id = tk.f[k];
-        }
-        s_id[tid * (K + 1) + k] = id;
-        s_b[tid * (3 * K + 1) + 3 * k] = bb[0];
-        s_b[tid * (3 * K + 1) + 3 * k + 1] = bb[1];
-        s_b[tid * (3 * K + 1) + 3 * k + 2] = bb[2];
-        s_z[tid * (K + 1) + k] = zz;
-        s_d[tid * (K + 1) + k] = dd;
-    }
-    __syncthreads();
-    const int nrows = min(BS, S - r0), ncols = min(BS, S - c0);
-    const int64_t pix0 = ((int64_t)n * S + r0) * S + c0;
-    copy_rows(reinterpret_cast<long long *>(o.pix_to_face) + pix0 * K, s_id, nrows, ncols, K, BS, (int64_t)S * K);
-    copy_rows(o.bary + pix0 * K * 3, s_b, nrows, ncols, 3 * K, BS, (int64_t)S * K * 3);
-    copy_rows(o.zbuf + pix0 * K, s_z, nrows, ncols, K, BS, (int64_t)S * K);
-    copy_rows(o.dists + pix0 * K, s_d, nrows, ncols, K, BS, (int64_t)S * K);
-    __syncthreads();
-}
-
 // Fragments of one pixel's K winners written directly by the owning thread,
 // 16-byte vector stores when K is a multiple of 4 (ids: K/2, depths and
 // distances: K/4, barycentrics: 3K/4 stores per pixel).
-constexpr bool kStageOutputs = false;
 
 template <int KM>
 __device__ __forceinline__ void write_pixel_vec(const FineOut &o, int64_t pix, int K, const TopK<KM> &tk,
@@ -462,14 +411,19 @@ struct SmemTopK {
     float *z;
     int *f;
     int stride, K;
-    __device__ __forceinline__ void init() {
-        for (int k = 0; k < K; ++k) { z[k * stride] = __int_as_float(0x7f800000); f[k * stride] = 0x7fffffff; }
+    int n;  // entries held (< K while the list is not full)
+    __device__ __forceinline__ void init() { n = 0; }
+    // K-th smallest depth so far (infinite until K candidates were kept)
+    __device__ __forceinline__ float thr() const {
+        return n < K ? __int_as_float(0x7f800000) : z[(K - 1) * stride];
     }
     __device__ __forceinline__ bool admits(float zz, int ff) const {
-        return key_less(zz, ff, z[(K - 1) * stride], f[(K - 1) * stride]);
+        return n < K || key_less(zz, ff, z[(K - 1) * stride], f[(K - 1) * stride]);
     }
+    // insertion from the end of the held entries: candidates arrive nearly in
+    // depth order, so most insertions are appends
     __device__ __forceinline__ void insert(float zz, int ff) {
-        int k = K - 1;
+        int k = n < K ? n : K - 1;
         while (k > 0) {
             float zp = z[(k - 1) * stride];
             int fp = f[(k - 1) * stride];
@@ -480,6 +434,7 @@ struct SmemTopK {
         }
         z[k * stride] = zz;
         f[k * stride] = ff;
+        if (n < K) ++n;
     }
 };
 
@@ -488,7 +443,7 @@ __device__ __forceinline__ void write_pixel_smem(const FineOut &o, int64_t pix, 
     const int64_t s0 = pix * (int64_t)K;
     for (int k = 0; k < K; ++k) {
         const int64_t s = s0 + k;
-        const int f = tk.f[k * tk.stride];
+        const int f = k < tk.n ? tk.f[k * tk.stride] : 0x7fffffff;
         if (f == 0x7fffffff) {
             o.pix_to_face[s] = -1;
             o.zbuf[s] = -1.f;
@@ -519,24 +474,15 @@ __device__ __forceinline__ void write_pixel_smem(const FineOut &o, int64_t pix, 
 // ---------------------------------------------------------------------------
 // fine pass: persistent blocks, one bin (bin x bin pixels = block) per item
 // ---------------------------------------------------------------------------
-// Lower bound on a face's depth at any pixel where it is a candidate (nearest
-// corner), valid when the depth is a convex combination of the corner depths:
-// with clipping, or without blur (inside pixels only).  Slightly reduced so
-// that fp32 rounding of the key can never fall below it.
-__device__ __forceinline__ float face_zmin(const FaceRec &R) {
-    if (!(R.c.x <= R.c.y)) return __int_as_float(0x7f800000);  // culled
-    return __fdividef(1.f, fmaxf(R.d.y, fmaxf(R.d.z, R.d.w))) * (1.f - 1e-6f);
-}
-
 template <int KM, int BS>
 __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
     constexpr int BD = BS * BS;
     __shared__ FaceRec s_rec[BD];
     __shared__ int s_id[BD];
     __shared__ float s_key[BD];
-    __shared__ short s_ord[BD];
     __shared__ int s_item;
-    extern __shared__ unsigned char s_dyn[];
+    // dynamic: sort_cap bin entries; K > 16: afterwards the per-thread lists
+    extern __shared__ unsigned long long s_sort[];
     const int tid = threadIdx.x;
     const int ty = tid / BS, tx = tid % BS;
     EvalFlags fl = a.fl;
@@ -574,119 +520,140 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
         const int off = a.offsets[item];
         TopK<(KM > 0 ? KM : 1)> tk;
         SmemTopK stk;
-        if constexpr (KM > 0) {
-            tk.init();
-        } else {
-            stk.z = reinterpret_cast<float *>(s_dyn) + tid;
-            stk.f = reinterpret_cast<int *>(s_dyn) + BD * a.K + tid;
-            stk.stride = BD;
-            stk.K = a.K;
-            stk.init();
-        }
-        for (int base = 0; base < cnt; base += BD) {
-            const int j = base + tid;
-            float key = __int_as_float(0x7f800000);
-            if (j < cnt) {
-                const int fid = a.lists[off + j];
-                s_id[tid] = fid;
-                const float4 *src = reinterpret_cast<const float4 *>(a.rec + fid);
-                FaceRec R;
-                R.a = __ldg(src);
-                R.b = __ldg(src + 1);
-                R.c = __ldg(src + 2);
-                R.d = __ldg(src + 3);
-                R.e = __ldg(src + 4);
-                R.h = __ldg(src + 5);
-                s_rec[tid] = R;
-                key = face_zmin(R);
-            } else {
-                // padding slots of a partial chunk are never visited (they sort
-                // last and the loop stops at the chunk's face count), and an
-                // empty bbox keeps them inert regardless
-                s_rec[tid].c = make_float4(__int_as_float(0x7f800000), -__int_as_float(0x7f800000),
-                                           __int_as_float(0x7f800000), -__int_as_float(0x7f800000));
-            }
-            s_key[tid] = key;
-            s_ord[tid] = (short)tid;
+        // The bin's list is sorted front to back in segments of up to sort_cap
+        // entries (one segment unless the bin holds more faces than that).
+        // K <= 16: each segment is sorted in shared memory right before it is
+        // walked.  K > 16: every segment is sorted first and written back to
+        // the (block-owned) list, so that the same shared memory then holds
+        // the per-pixel lists.
+        auto sort_segment = [&](int seg, int m) {
+            int n2 = 32;
+            while (n2 < m) n2 <<= 1;
+            for (int i = tid; i < n2; i += BD) s_sort[i] = i < m ? a.lists[off + seg + i] : ~0ull;
             __syncthreads();
-            // bitonic sort of the chunk by nearest-corner depth (front to back)
+            // bitonic sort (padding entries sort last)
 #pragma unroll 1
-            for (int k2 = 2; k2 <= BD; k2 <<= 1) {
+            for (int k2 = 2; k2 <= n2; k2 <<= 1) {
 #pragma unroll 1
                 for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
-                    const int o = tid ^ j2;
-                    if (o > tid) {
-                        const float ka = s_key[tid], kb = s_key[o];
-                        const bool up = (tid & k2) == 0;
-                        if ((ka > kb) == up) {
-                            s_key[tid] = kb;
-                            s_key[o] = ka;
-                            const short t = s_ord[tid];
-                            s_ord[tid] = s_ord[o];
-                            s_ord[o] = t;
+                    for (int i = tid; i < (n2 >> 1); i += BD) {
+                        const int lo = ((i & ~(j2 - 1)) << 1) | (i & (j2 - 1));
+                        const int hi = lo + j2;
+                        const unsigned long long x = s_sort[lo], y = s_sort[hi];
+                        if ((x > y) == ((lo & k2) == 0)) {
+                            s_sort[lo] = y;
+                            s_sort[hi] = x;
                         }
                     }
                     __syncthreads();
                 }
             }
-            const int m = min(BD, cnt - base);
-            // Every lane walks the staged faces front to back.  A face is
-            // skipped by a lane when its bbox misses the pixel or its nearest
-            // corner lies behind the lane's K-th depth; by the warp when that
-            // holds for all 32 lanes; and the warp stops once every remaining
-            // face lies behind all of its lanes' K-th depths.
-            // Faces are culled 32 at a time for the whole warp: lane j tests face
-            // jb + j against the rectangle spanned by the warp's pixel centres
-            // and against the warp's largest K-th depth; one ballot names the
-            // faces the warp walks pixel by pixel.  Chunks are sorted front to
-            // back, so the warp stops once a chunk starts behind every lane's
-            // K-th depth.
-            for (int jb = 0; jb < m; jb += 32) {
-                float thr;
-                if constexpr (KM > 0) thr = tk.z[KM - 1];
-                else thr = stk.z[(a.K - 1) * BD];
-                const float wthr =
-                    __int_as_float(__reduce_max_sync(0xffffffffu, valid ? __float_as_int(thr) : 0));
-                if (zcull && s_key[jb] > wthr) break;
-                const int jl = jb + lane;
-                bool hit = false;
-                if (jl < m) {
-                    const float4 bb = s_rec[s_ord[jl]].c;
-                    hit = bb.x <= wx1 && bb.y >= wx0 && bb.z <= wy1 && bb.w >= wy0 && !(zcull && s_key[jl] > wthr);
-                }
-                unsigned mask = __ballot_sync(0xffffffffu, hit);
-                while (mask) {
-                    const int jj = jb + __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    if (!valid) continue;
-                    const int jf = s_ord[jj];
+        };
+        if constexpr (KM > 0) {
+            tk.init();
+        } else {
+            for (int seg = 0; seg < cnt; seg += a.sort_cap) {
+                const int m = min(a.sort_cap, cnt - seg);
+                sort_segment(seg, m);
+                for (int i = tid; i < m; i += BD) a.lists[off + seg + i] = s_sort[i];
+                __syncthreads();
+            }
+            stk.z = reinterpret_cast<float *>(s_sort) + tid;
+            stk.f = reinterpret_cast<int *>(s_sort) + BD * a.K + tid;
+            stk.stride = BD;
+            stk.K = a.K;
+            stk.init();
+        }
+        for (int seg = 0; seg < cnt; seg += a.sort_cap) {
+            const int m = min(a.sort_cap, cnt - seg);
+            if constexpr (KM > 0) sort_segment(seg, m);
+            const unsigned long long *ent = (KM > 0) ? s_sort : a.lists + off + seg;
+            // Chunks of BD faces, front to back: every lane walks the staged
+            // faces in order.  Faces are culled 32 at a time for the whole
+            // warp: lane j tests face jb + j against the rectangle spanned by
+            // the warp's pixel centres and against the warp's largest K-th
+            // depth; one ballot names the faces the warp walks pixel by pixel.
+            // A face is skipped by a lane when its bbox misses the pixel or its
+            // nearest corner lies behind the lane's K-th depth.  Once a warp's
+            // largest K-th depth lies in front of the next face, the rest of
+            // the segment is behind all its lanes, and the block stops when
+            // that holds for every warp.
+            for (int base = 0; base < m; base += BD) {
+                const int mc = min(BD, m - base);
+                if (tid < mc) {
+                    const unsigned long long v = ent[base + tid];
+                    const int fid = (int)(unsigned)(v & 0xffffffffull);
+                    s_id[tid] = fid;
+                    s_key[tid] = __uint_as_float((unsigned)(v >> 32));
+                    const float4 *src = reinterpret_cast<const float4 *>(a.rec + fid);
                     FaceRec R;
-                    R.c = s_rec[jf].c;
-                    if (!in_bbox(R, p)) continue;
+                    R.a = __ldg(src);
+                    R.b = __ldg(src + 1);
+                    R.c = __ldg(src + 2);
+                    R.d = __ldg(src + 3);
+                    R.e = __ldg(src + 4);
+                    R.h = __ldg(src + 5);
+                    s_rec[tid] = R;
+                }
+                __syncthreads();
+                bool warp_done = false;
+                for (int jb = 0; jb < mc; jb += 32) {
+                    float thr;
                     if constexpr (KM > 0) thr = tk.z[KM - 1];
-                    else thr = stk.z[(a.K - 1) * BD];
-                    if (zcull && s_key[jj] > thr) continue;
-                    R.a = s_rec[jf].a;
-                    R.b = s_rec[jf].b;
-                    R.d = s_rec[jf].d;
-                    R.e = s_rec[jf].e;
-                    R.h = s_rec[jf].h;
-                    float z;
-                    if (face_key_nobbox(R, p, fl, z)) {
-                        const int fid = s_id[jf];
-                        if constexpr (KM > 0) {
-                            if (tk.admits(z, fid)) tk.insert(z, fid);
-                        } else {
-                            if (stk.admits(z, fid)) stk.insert(z, fid);
+                    else thr = stk.thr();
+                    const float wthr =
+                        __int_as_float(__reduce_max_sync(0xffffffffu, valid ? __float_as_int(thr) : 0));
+                    if (zcull && s_key[jb] > wthr) {
+                        warp_done = true;
+                        break;
+                    }
+                    const int jl = jb + lane;
+                    bool hit = false;
+                    if (jl < mc) {
+                        const float4 bb = s_rec[jl].c;
+                        hit = bb.x <= wx1 && bb.y >= wx0 && bb.z <= wy1 && bb.w >= wy0 &&
+                              !(zcull && s_key[jl] > wthr);
+                    }
+                    unsigned mask = __ballot_sync(0xffffffffu, hit);
+                    while (mask) {
+                        const int jj = jb + __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        if (!valid) continue;
+                        FaceRec R;
+                        R.c = s_rec[jj].c;
+                        if (!in_bbox(R, p)) continue;
+                        if constexpr (KM > 0) thr = tk.z[KM - 1];
+                        else thr = stk.thr();
+                        if (zcull && s_key[jj] > thr) continue;
+                        R.a = s_rec[jj].a;
+                        R.b = s_rec[jj].b;
+                        R.d = s_rec[jj].d;
+                        R.e = s_rec[jj].e;
+                        R.h = s_rec[jj].h;
+                        float z;
+                        if (face_key_nobbox(R, p, fl, z)) {
+                            const int fid = s_id[jj];
+                            if constexpr (KM > 0) {
+                                if (tk.admits(z, fid)) tk.insert(z, fid);
+                            } else {
+                                if (stk.admits(z, fid)) stk.insert(z, fid);
+                            }
                         }
                     }
                 }
+                if (!warp_done && zcull && base + BD < m) {
+                    float thr;
+                    if constexpr (KM > 0) thr = tk.z[KM - 1];
+                    else thr = stk.thr();
+                    const float wthr =
+                        __int_as_float(__reduce_max_sync(0xffffffffu, valid ? __float_as_int(thr) : 0));
+                    warp_done = __uint_as_float((unsigned)(ent[base + BD] >> 32)) > wthr;
+                }
+                if (__syncthreads_and(warp_done)) break;
             }
             __syncthreads();
         }
-        if constexpr (KM > 0 && kStageOutputs) {
-            write_tile<KM, BS>(a.out, n, by * BS, bx * BS, a.S, a.K, valid, tk, a.rec, p, fl, s_dyn);
-        } else if constexpr (KM > 0) {
+        if constexpr (KM > 0) {
             if (valid) write_pixel_vec(a.out, ((int64_t)n * a.S + r) * a.S + c, a.K, tk, a.rec, p, fl);
         } else if (valid) {
             const int64_t pix = ((int64_t)n * a.S + r) * a.S + c;
@@ -760,13 +727,11 @@ static int km_for(int K) {
 template <int KM, int BS>
 static cudaError_t launch_fine_t(const FineArgs &a, cudaStream_t st) {
     constexpr int BD = BS * BS;
-    // KM > 0: staging buffer for the tile's outputs (28 bytes per slot, rows
-    // padded by one word); KM == 0: the per-thread sorted lists
-    size_t dyn = (KM > 0) ? (kStageOutputs ? (size_t)BD * (8 * (a.K + 1) + 4 * (3 * a.K + 1) + 8 * (a.K + 1)) : 0)
-                          : (size_t)BD * a.K * 8;
+    // the sort buffer; KM == 0: the same memory then holds the per-thread lists
+    const size_t dyn = std::max((size_t)a.sort_cap * 8, (KM > 0) ? (size_t)0 : (size_t)BD * a.K * 8);
     auto kern = k_fine<KM, BS>;
     cudaError_t e = cudaSuccess;
-    if (dyn > 0) {
+    if (dyn > 0) {  // static + dynamic above 48 KB needs the opt-in
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
         if (e != cudaSuccess) return e;
     }

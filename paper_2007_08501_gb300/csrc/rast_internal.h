@@ -46,7 +46,7 @@ struct FillArgs {
     int S, bin, nb;
     int *cursor;
     const int *eff, *offsets;
-    int *lists;
+    unsigned long long *lists;  // (nearest-corner depth bits << 32) | face id
 };
 
 struct FineOut {
@@ -57,9 +57,11 @@ struct FineOut {
 struct FineArgs {
     const FaceRec *rec;
     const float *cams;
-    const int *lists, *eff, *offsets;
+    unsigned long long *lists;  // K > 16: each block sorts its bins' lists in place
+    const int *eff, *offsets;
     unsigned *queue;
     int items, nb, S, K;
+    int sort_cap;  // bin entries sorted at a time (power of two)
     EvalFlags fl;
     FineOut out;
 };

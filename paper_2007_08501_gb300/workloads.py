@@ -196,6 +196,14 @@ def pack(meshes, cams, colors=None) -> MeshBatch:
                      colors.astype(np.float32))
 
 
+def first_images(b: MeshBatch, n: int) -> MeshBatch:
+    """The first ``n`` images of a packed batch (all vertices kept)."""
+    n = max(1, min(int(n), b.N))
+    F = int(b.first_face[n - 1] + b.num_faces[n - 1])
+    return MeshBatch(b.verts, b.faces[:F].copy(), b.first_face[:n].copy(), b.num_faces[:n].copy(),
+                     b.cams[:n].copy(), b.colors, list(b.levels[:n]))
+
+
 def sphere_batch(levels, sigma, seed_base, cam_seed=None, color_seed=None, cams=None):
     """One displaced icosphere per image; mesh i draws from seed ``seed_base + i``."""
     meshes, cam_rows = [], []

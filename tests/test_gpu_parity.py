@@ -20,9 +20,9 @@ pytestmark = pytest.mark.gpu
 BLUR = float(np.float32(BLUR_SIGMA_1E4))
 
 
-def _full_check(batch, S, K, blur, bin_size, persp=True, clip=False, max_amb_frac=0.10):
+def _full_check(batch, S, K, blur, bin_size, persp=True, clip=False, max_amb_frac=0.10, max_faces_per_bin=4096):
     d = to_dev(batch)
-    fr, status, _, _ = gpu_fwd(d, S, K, blur, bin_size, persp, clip)
+    fr, status, _, _ = gpu_fwd(d, S, K, blur, bin_size, persp, clip, max_faces_per_bin=max_faces_per_bin)
     assert status == 0
     m = oracle_mesh(batch)
     orc = oracle.rasterize(m, S, K, blur, persp, clip)
@@ -60,6 +60,18 @@ def test_large_k_shared_memory_path():
     b = workloads.sphere_batch([3, 3], 0.05, seed_base=91)
     for bs in (0, 8):
         _full_check(b, 48, 50, BLUR, bs, True, True)
+
+
+@pytest.mark.parametrize("level,S,K,bin_size,clip", [
+    (6, 32, 4, 16, True),     # ~20k faces per bin: sorted in segments of 8192
+    (6, 32, 4, 16, False),    # unclipped blur: no depth cull, every segment walked
+    (5, 32, 50, 8, True),     # K > 16: segments of 2048 sorted before the walk
+    (5, 32, 20, 16, False),
+])
+def test_bins_larger_than_the_sort_buffer(level, S, K, bin_size, clip):
+    b = workloads.sphere_batch([level], 0.05, seed_base=17)
+    # dense meshes at 32x32: many pixels sit within 1e-6 of some edge or depth tie
+    _full_check(b, S, K, BLUR, bin_size, True, clip, max_amb_frac=0.6, max_faces_per_bin=65536)
 
 
 @pytest.mark.parametrize("K", [2, 16, 20])
