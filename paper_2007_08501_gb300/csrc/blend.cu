@@ -215,11 +215,24 @@ __global__ void __launch_bounds__(256) k_blend_fwd_any(BlendArgs a) {
     const int64_t s0 = pix * K;
     float keep = 1.f, zmin = __int_as_float(0x7f800000);
     bool any = false;
-    for (int k = 0; k < K; ++k) {
-        if (a.pix_to_face[s0 + k] < 0) continue;
-        keep *= sigmoidf_(a.dists[s0 + k] / a.sigma);
-        if (rgb) zmin = fminf(zmin, a.zbuf[s0 + k]);
+    auto take = [&](long long f, float d, int k) {
+        if (f < 0) return;
+        keep *= sigmoidf_(d / a.sigma);
+        if (rgb) zmin = fminf(zmin, __ldg(a.zbuf + s0 + k));
         any = true;
+    };
+    if ((K & 1) == 0) {
+        // even K: slot pairs are 16-byte (ids) and 8-byte (distances) aligned
+        const longlong2 *fp = reinterpret_cast<const longlong2 *>(a.pix_to_face + s0);
+        const float2 *dp = reinterpret_cast<const float2 *>(a.dists + s0);
+        for (int j = 0; j < K / 2; ++j) {
+            const longlong2 f2 = __ldg(fp + j);
+            const float2 d2 = __ldg(dp + j);
+            take(f2.x, d2.x, 2 * j);
+            take(f2.y, d2.y, 2 * j + 1);
+        }
+    } else {
+        for (int k = 0; k < K; ++k) take(__ldg(a.pix_to_face + s0 + k), __ldg(a.dists + s0 + k), k);
     }
     float4 out = make_float4(0.f, 0.f, 0.f, 1.f - keep);
     if (rgb) {

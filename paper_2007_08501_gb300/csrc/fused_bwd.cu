@@ -258,11 +258,24 @@ __global__ void __launch_bounds__(256) k_blend_rast_bwd_any(BlendArgs a, RastBwd
     const float4 g = valid ? reinterpret_cast<const float4 *>(a.grad_image)[pix] : make_float4(0.f, 0.f, 0.f, 0.f);
     float keep = 1.f, zmin = __int_as_float(0x7f800000);
     bool any = false;
-    for (int k = 0; valid && k < K; ++k) {
-        if (a.pix_to_face[s0 + k] < 0) continue;
-        keep *= sigmoidf_(a.dists[s0 + k] / a.sigma);
-        if (RGB) zmin = fminf(zmin, a.zbuf[s0 + k]);
+    auto take = [&](long long f, float d, int k) {
+        if (f < 0) return;
+        keep *= sigmoidf_(d / a.sigma);
+        if (RGB) zmin = fminf(zmin, __ldg(a.zbuf + s0 + k));
         any = true;
+    };
+    if (valid && (K & 1) == 0) {
+        // even K: slot pairs are 16-byte (ids) and 8-byte (distances) aligned
+        const longlong2 *fp = reinterpret_cast<const longlong2 *>(a.pix_to_face + s0);
+        const float2 *dp = reinterpret_cast<const float2 *>(a.dists + s0);
+        for (int j = 0; j < K / 2; ++j) {
+            const longlong2 f2 = __ldg(fp + j);
+            const float2 d2 = __ldg(dp + j);
+            take(f2.x, d2.x, 2 * j);
+            take(f2.y, d2.y, 2 * j + 1);
+        }
+    } else if (valid) {
+        for (int k = 0; k < K; ++k) take(__ldg(a.pix_to_face + s0 + k), __ldg(a.dists + s0 + k), k);
     }
     const float sil = -g.w * keep / a.sigma;
     float range = 0.f, m = 0.f, iD = 0.f, delta = 0.f;
@@ -292,16 +305,23 @@ __global__ void __launch_bounds__(256) k_blend_rast_bwd_any(BlendArgs a, RastBwd
         delta = expf((a.eps - m) / a.gamma);
         iD = 1.f / (den + delta);
     }
+    // the next slot's id and distance are loaded one iteration ahead
+    int f_next = valid ? clamp_id(__ldg(a.pix_to_face + s0)) : -1;
+    float d_next = valid ? __ldg(a.dists + s0) : 0.f;
     for (int k = 0; k < K; ++k) {  // uniform trip count: every lane reaches the warp grouping
         const int64_t s = s0 + k;
-        const int f = valid ? clamp_id(a.pix_to_face[s]) : -1;
+        const int f = f_next;
+        const float d = d_next;
+        if (valid && k + 1 < K) {
+            f_next = clamp_id(__ldg(a.pix_to_face + s + 1));
+            d_next = __ldg(a.dists + s + 1);
+        }
         float gd = 0.f, gz = 0.f, gb[3] = {0.f, 0.f, 0.f};
         float acc[NA];
 #pragma unroll
         for (int j = 0; j < NA; ++j) acc[j] = 0.f;
         int64_t vi[3] = {-1, -1, -1};
         if (f >= 0) {
-            const float d = a.dists[s];
             const float prob = sigmoidf_(-d / a.sigma);
             gd = sil * prob;
             if constexpr (RGB) {

@@ -19,11 +19,12 @@ constexpr float kCullArea = 1e-12f;
 constexpr int kMaxK = 64;
 
 // Bin entries the fine pass sorts at a time: the bin capacity rounded up to a
-// power of two, at most 8192 (64 KB of shared memory), at most 2048 when the
-// per-pixel lists live in shared memory too (K > 16).
+// power of two, at least 256 (one per thread of the largest block), at most
+// 8192 (64 KB of shared memory), at most 2048 when the per-pixel lists live in
+// shared memory too (K > 16).
 inline int fine_sort_cap(int max_faces_per_bin, int K) {
     const int lim = K > 16 ? 2048 : 8192;
-    int c = 32;
+    int c = 256;
     while (c < max_faces_per_bin && c < lim) c <<= 1;
     return c;
 }

@@ -529,9 +529,34 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
         auto sort_segment = [&](int seg, int m) {
             int n2 = 32;
             while (n2 < m) n2 <<= 1;
+            if (n2 <= BD) {
+                // one entry per thread: partners closer than 32 trade through
+                // shuffles, farther ones through shared memory
+                unsigned long long v = tid < m ? a.lists[off + seg + tid] : ~0ull;
+#pragma unroll 1
+                for (int k2 = 2; k2 <= n2; k2 <<= 1) {
+#pragma unroll 1
+                    for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
+                        unsigned long long o;
+                        if (j2 >= 32) {
+                            s_sort[tid] = v;
+                            __syncthreads();
+                            o = s_sort[tid ^ j2];
+                            __syncthreads();
+                        } else {
+                            o = __shfl_xor_sync(0xffffffffu, v, j2);
+                        }
+                        const bool keep_min = ((tid & j2) == 0) == ((tid & k2) == 0);
+                        v = keep_min ? (o < v ? o : v) : (o > v ? o : v);
+                    }
+                }
+                s_sort[tid] = v;
+                __syncthreads();
+                return;
+            }
             for (int i = tid; i < n2; i += BD) s_sort[i] = i < m ? a.lists[off + seg + i] : ~0ull;
             __syncthreads();
-            // bitonic sort (padding entries sort last)
+            // bitonic sort in shared memory (padding entries sort last)
 #pragma unroll 1
             for (int k2 = 2; k2 <= n2; k2 <<= 1) {
 #pragma unroll 1
@@ -558,9 +583,9 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
                 for (int i = tid; i < m; i += BD) a.lists[off + seg + i] = s_sort[i];
                 __syncthreads();
             }
-            stk.z = reinterpret_cast<float *>(s_sort) + tid;
-            stk.f = reinterpret_cast<int *>(s_sort) + BD * a.K + tid;
-            stk.stride = BD;
+            stk.z = reinterpret_cast<float *>(s_sort) + tid * a.K;
+            stk.f = reinterpret_cast<int *>(s_sort) + BD * a.K + tid * a.K;
+            stk.stride = 1;
             stk.K = a.K;
             stk.init();
         }
@@ -655,9 +680,50 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
         }
         if constexpr (KM > 0) {
             if (valid) write_pixel_vec(a.out, ((int64_t)n * a.S + r) * a.S + c, a.K, tk, a.rec, p, fl);
-        } else if (valid) {
-            const int64_t pix = ((int64_t)n * a.S + r) * a.S + c;
-            write_pixel_smem(a.out, pix, a.K, stk, a.rec, p, fl);
+        } else {
+            // K > 16: the block writes its tile slot by slot: consecutive
+            // threads take consecutive output slots of a tile row (coalesced),
+            // each recomputing its slot's barycentrics and distance
+            s_id[tid] = valid ? stk.n : 0;
+            __syncthreads();
+            const int K = a.K;
+            const int rows = min(BS, a.S - by * BS), cols = min(BS, a.S - bx * BS);
+            const int per_row = cols * K;
+            const float *lz = reinterpret_cast<const float *>(s_sort);
+            const int *lf = reinterpret_cast<const int *>(s_sort) + BD * K;
+            for (int i = tid; i < rows * per_row; i += BD) {
+                const int ry = i / per_row, rem = i - ry * per_row;
+                const int cx = rem / K, k = rem - cx * K;
+                const int t = ry * BS + cx;
+                const int rr = by * BS + ry, cc = bx * BS + cx;
+                const int64_t sl = (((int64_t)n * a.S + rr) * a.S + cc) * K + k;
+                if (k < s_id[t]) {
+                    const int f = lf[t * K + k];
+                    FaceRec R;
+                    const float4 *src = reinterpret_cast<const float4 *>(a.rec + f);
+                    R.a = __ldg(src);
+                    R.b = __ldg(src + 1);
+                    R.c = __ldg(src + 2);
+                    R.d = __ldg(src + 3);
+                    R.e = __ldg(src + 4);
+                    float bp[3], d;
+                    face_fragment(R, pixel_centre(rr, cc, a.S), fl, bp, d);
+                    a.out.pix_to_face[sl] = f;
+                    a.out.zbuf[sl] = lz[t * K + k];
+                    a.out.bary[3 * sl] = bp[0];
+                    a.out.bary[3 * sl + 1] = bp[1];
+                    a.out.bary[3 * sl + 2] = bp[2];
+                    a.out.dists[sl] = d;
+                } else {
+                    a.out.pix_to_face[sl] = -1;
+                    a.out.zbuf[sl] = -1.f;
+                    a.out.bary[3 * sl] = -1.f;
+                    a.out.bary[3 * sl + 1] = -1.f;
+                    a.out.bary[3 * sl + 2] = -1.f;
+                    a.out.dists[sl] = -1.f;
+                }
+            }
+            __syncthreads();
         }
     }
 }
