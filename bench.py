@@ -49,11 +49,11 @@ WORKLOADS = {
     "4": (4, "", "1 icosphere level 6 (81,920 faces) seen by 20 cameras (shared vertices), 512x512, K=50, "
                  "blur=ln(1/1e-4-1)*1e-4, soft silhouette, fwd+bwd to verts"),
 }
-KERNELS_PER_STEP = {"rast_fwd": 4, "blend_fwd": 1, "bwd": 2}
+KERNELS_PER_STEP = {"fwd": 4, "bwd": 2}
 # DRAM bytes (read + write) per launch of each stage's main kernel, from one
 # ncu capture of this workload with the current kernel source (summary in
 # profiles/); a stage without an entry reports null.
-TRAFFIC_BYTES = {"rast_fwd": {"kernel": "k_fine<8,16>", "bytes": 5991680 + 63094784}}
+TRAFFIC_BYTES = {}
 
 
 def _args():
@@ -70,7 +70,7 @@ def _args():
     ap.add_argument("--max-images", type=int, default=0,
                     help="keep only the first N images of the workload (small cases for profiling)")
     ap.add_argument("--no-separate", action="store_true",
-                    help="skip timing the backward as two separate calls (blend_bwd, rast_mesh_bwd)")
+                    help="skip timing the step as four separate calls (no fused forward or backward)")
     return ap.parse_args()
 
 
@@ -175,20 +175,21 @@ class Pipeline:
         ops, p2f, zb, ba, di = (self.ops, *self.frag)
         N, S, K = self.N, self.S, self.K
         rgb = self.rgb
-        fwd = [
-            ("rast_fwd", lambda: ops.rast_mesh_fwd(self.p, self.verts, self.faces, self.ff, self.nf, self.cams,
-                                                   p2f, zb, ba, di, self.ws)),
-            ("blend_fwd", lambda: ops.blend_fwd(self.bp, N, S, K, p2f, zb, ba, di, self.faces, self.colors,
-                                                self.img)),
-        ]
         if self.fused:
-            return fwd + [
+            return [
+                ("fwd", lambda: ops.rast_blend_fwd(self.p, self.bp, self.verts, self.faces, self.ff, self.nf,
+                                                   self.cams, self.colors if rgb else None, p2f, zb, ba, di,
+                                                   self.img, self.ws)),
                 ("bwd", lambda: ops.blend_rast_bwd(self.p, self.bp, self.verts, self.faces, self.ff, self.nf,
                                                    self.cams, p2f, zb if rgb else None, ba if rgb else None, di,
                                                    self.colors if rgb else None, self.gimg, self.gv,
                                                    self.gc if rgb else None, self.ws)),
             ]
-        return fwd + [
+        return [
+            ("rast_fwd", lambda: ops.rast_mesh_fwd(self.p, self.verts, self.faces, self.ff, self.nf, self.cams,
+                                                   p2f, zb, ba, di, self.ws)),
+            ("blend_fwd", lambda: ops.blend_fwd(self.bp, N, S, K, p2f, zb, ba, di, self.faces, self.colors,
+                                                self.img)),
             ("blend_bwd", lambda: ops.blend_bwd(self.bp, N, S, K, p2f, zb, ba, di, self.faces, self.colors,
                                                 self.gimg, self.gz if rgb else None, self.gb if rgb else None,
                                                 self.gd, self.gc if rgb else None)),
@@ -262,6 +263,7 @@ def algorithmic_bytes(w):
     rgb_extra = 24 * F + 12 * V if w.blend_mode == "rgb" else 0   # faces + colours gathered by the rgb blend
     return {
         "rast_fwd": mesh_in + 28 * slots,                                  # write fragments
+        "fwd": mesh_in + 28 * slots + 16 * pix + rgb_extra,                # fused: fragments + rgba out
         "blend_fwd": 28 * slots + 16 * pix + rgb_extra,                    # read fragments, write rgba
         "blend_bwd": 28 * slots + 16 * pix + 20 * slots + rgb_extra + 12 * V,
         "rast_bwd": mesh_in + 28 * slots + 12 * V,                         # ids + grad fragments
@@ -456,14 +458,14 @@ def run_ours(args):
 
     separate = None
     if not args.no_separate:
-        # the same step with the backward as two C-ABI calls (blend_bwd, rast_mesh_bwd)
+        # the same step as four C-ABI calls (rast_mesh_fwd, blend_fwd, blend_bwd, rast_mesh_bwd)
         sp = Pipeline(w, bin_size=tuned["bin_size"], max_faces_per_bin=tuned["max_faces_per_bin"], device=dev,
                       max_bin_entries=tuned["max_bin_entries"], fused=False)
         sp.capture()
         ss = timed_steps(sp, args.steps, 3, flush, use_graph=True)
         sstages = {k: round(statistics.mean(s[k] for s in ss), 4) for k in ss[0]}
         separate = {"ms_per_step": round(statistics.mean(sum(s.values()) for s in ss), 4),
-                    "blend_bwd_ms": sstages["blend_bwd"], "rast_bwd_ms": sstages["rast_bwd"]}
+                    **{k + "_ms": v for k, v in sstages.items()}}
         del sp
 
     plain = None
@@ -474,7 +476,7 @@ def run_ours(args):
         pms = statistics.mean(sum(s.values()) for s in ps)
         pstages = {k: round(statistics.mean(s[k] for s in ps), 4) for k in ps[0]}
         plain = {"ms_per_step": round(pms, 4), "value": round(slots / (pms / 1e3) / 1e6, 1),
-                 "rast_fwd_ms": pstages["rast_fwd"], "launches_per_step": b.N + 1 + 1 + 2,
+                 "fwd_ms": pstages["fwd"], "launches_per_step": b.N + 1 + 1 + 2,
                  "speedup_of_binned": round(pms / ms, 3)}
 
     fit_loop = None
@@ -495,7 +497,8 @@ def run_ours(args):
                        "bin_size": tuned["bin_size"], "max_faces_per_bin": tuned["max_faces_per_bin"],
                        "max_bin_entries": tuned["max_bin_entries"], "autotuned": True,
                        "graph": "one CUDA graph per C-ABI call",
-                       "backward": "blend_rast_bwd (blend adjoint fused with the rasterizer adjoint)",
+                       "calls": "rast_blend_fwd (fine pass blends as it writes) + blend_rast_bwd (blend adjoint "
+                                "fused with the rasterizer adjoint)",
                        "l2": "flushed between steps (256 MiB write), outside the timed events",
                        "bin_occupancy": {"max_faces_in_a_bin": mc, "total_entries": tot},
                        "parallelism": "replicas x%d" % world},
@@ -506,9 +509,9 @@ def run_ours(args):
             "gpu_launches": sum(KERNELS_PER_STEP.values()) * args.steps,
             "ms_per_step_median": round(statistics.median(step_ms), 4),
             "fine_pass": {"face_pixel_tests": fine_tests,
-                          "tests_per_s": round(fine_tests / (stages["rast_fwd"] / 1e3), 1),
+                          "tests_per_s": round(fine_tests / (stages["fwd"] / 1e3), 1),
                           "note": "sum over bins of (pixels in bin x faces in bin)"},
-            "clocks": clk, "unfused_backward": separate, "plain_form": plain, "fit_loop": fit_loop,
+            "clocks": clk, "unfused": separate, "plain_form": plain, "fit_loop": fit_loop,
             "status": st,
             "wall_s_timed_region": round(wall, 3),
         }

@@ -170,6 +170,26 @@ MESHRAST_API int blend_fwd(const blend_params *bp, int64_t N, int64_t S, int64_t
               const int64_t *faces, int64_t F, const float *vert_colors, int64_t V,
               float *image, void *stream);
 
+/* Forward rasterization and blend in one call: what rast_mesh_fwd followed by
+ * blend_fwd on its fragments computes (Section 3.2 "Rasterizer" and
+ * "Shaders", Algorithms 1-2), same arithmetic in the same order.  In
+ * MESHRAST_BLEND_SIL mode with bin_size 8 or 16 and K <= 16 the fine pass
+ * blends each pixel's fragments while it writes them (no second pass over
+ * the fragments); otherwise the blend runs as a separate kernel inside this
+ * call.
+ * Outputs (all overwritten): the Fragments as in rast_mesh_fwd, and image
+ * (N,S,S,4) as in blend_fwd; N, S, K come from p.  vert_colors may be NULL in
+ * MESHRAST_BLEND_SIL mode.  image, pix_to_face, dists (and zbuf) must be
+ * 16-byte aligned.  Status word as in rast_mesh_fwd. */
+MESHRAST_API int rast_blend_fwd(const rast_params *p, const blend_params *bp,
+                  const float *verts, int64_t V,
+                  const int64_t *faces, int64_t F,
+                  const int64_t *first_face, const int64_t *num_faces,
+                  const float *cams, const float *vert_colors,
+                  int64_t *pix_to_face, float *zbuf, float *bary, float *dists,
+                  float *image,
+                  void *workspace, size_t workspace_bytes, void *stream);
+
 /* Blend backward: adjoint of blend_fwd for upstream grad_image (N,S,S,4).
  * grad_dists (N,S,S,K) is overwritten.  In MESHRAST_BLEND_RGB mode
  * grad_zbuf (N,S,S,K), grad_bary (N,S,S,K,3) and grad_vert_colors (V,3) are

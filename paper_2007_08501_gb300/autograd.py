@@ -6,8 +6,10 @@ recomputes barycentrics, depth and distance from ``pix_to_face`` instead of
 keeping them for the backward pass.  ``blend`` applies Algorithm 1
 (silhouette) or Algorithms 1 + 2 (softmax rgb + silhouette alpha) and
 differentiates through ``blend_bwd``.  ``render_meshes`` does both in one
-Function whose backward is ``blend_rast_bwd``: the blend adjoint goes straight
-into the rasterizer adjoint without materialising fragment gradients.
+Function: its forward is ``rast_blend_fwd`` (the fine pass blends as it
+writes the fragments) and its backward ``blend_rast_bwd`` (the blend adjoint
+goes straight into the rasterizer adjoint without materialising fragment
+gradients).
 """
 from __future__ import annotations
 
@@ -153,11 +155,9 @@ class _Render(torch.autograd.Function):
         p = rs.params(N)
         buf = ws.get(p, verts.shape[0], faces.shape[0])
         p2f, zbuf, bary, dists = ops.alloc_fragments(N, S, K, verts.device)
-        ops.rast_mesh_fwd(p, verts, faces, first_face, num_faces, cams, p2f, zbuf, bary, dists, buf)
         img = torch.empty((N, S, S, 4), dtype=torch.float32, device=verts.device)
-        rgb = bs.rgb
-        ops.blend_fwd(bs.params(), N, S, K, p2f, zbuf if rgb else None, bary if rgb else None, dists,
-                      faces if rgb else None, colors if rgb else None, img)
+        ops.rast_blend_fwd(p, bs.params(), verts, faces, first_face, num_faces, cams, colors if bs.rgb else None,
+                           p2f, zbuf, bary, dists, img, buf)
         ctx.save_for_backward(verts, colors, faces, first_face, num_faces, cams, p2f, zbuf, bary, dists)
         ctx.rs, ctx.bs, ctx.ws = rs, bs, ws
         return img

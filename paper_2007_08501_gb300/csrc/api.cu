@@ -127,9 +127,13 @@ static int check_ws(const rast_params *p, int64_t V, int64_t F, void *ws, size_t
     return MESHRAST_OK;
 }
 
-int rast_mesh_fwd(const rast_params *p, const float *verts, int64_t V, const int64_t *faces, int64_t F,
-                  const int64_t *first_face, const int64_t *num_faces, const float *cams, int64_t *pix_to_face,
-                  float *zbuf, float *bary, float *dists, void *workspace, size_t workspace_bytes, void *stream) {
+// Forward rasterization; with `blend` set, the fine pass also applies the blend
+// (register path, K <= 16) and *blended tells whether it did.
+static int forward(const rast_params *p, const float *verts, int64_t V, const int64_t *faces, int64_t F,
+                   const int64_t *first_face, const int64_t *num_faces, const float *cams, int64_t *pix_to_face,
+                   float *zbuf, float *bary, float *dists, void *workspace, size_t workspace_bytes, void *stream,
+                   const mr::FineBlend *blend, bool *blended) {
+    if (blended) *blended = false;
     if (!mr_host::check_params(p, V, F)) return MESHRAST_ERR_INVALID_ARG;
     if (mr_host::unsupported(p)) return MESHRAST_ERR_UNSUPPORTED;
     if (p->N > 0 && (!first_face || !num_faces || !cams)) return MESHRAST_ERR_INVALID_ARG;
@@ -212,7 +216,19 @@ int rast_mesh_fwd(const rast_params *p, const float *verts, int64_t V, const int
     ka.fl = fl;
     ka.out = out;
     ka.sort_cap = mr::fine_sort_cap(p->max_faces_per_bin, (int)K);
+    std::memset(&ka.blend, 0, sizeof(ka.blend));
+    if (blend && mr::fine_blends((int)K, blend->rgb != 0)) {
+        ka.blend = *blend;
+        if (blended) *blended = true;
+    }
     return mr::launch_fine(ka, p->bin_size, st) == cudaSuccess ? MESHRAST_OK : MESHRAST_ERR_CUDA;
+}
+
+int rast_mesh_fwd(const rast_params *p, const float *verts, int64_t V, const int64_t *faces, int64_t F,
+                  const int64_t *first_face, const int64_t *num_faces, const float *cams, int64_t *pix_to_face,
+                  float *zbuf, float *bary, float *dists, void *workspace, size_t workspace_bytes, void *stream) {
+    return forward(p, verts, V, faces, F, first_face, num_faces, cams, pix_to_face, zbuf, bary, dists, workspace,
+                   workspace_bytes, stream, nullptr, nullptr);
 }
 
 int rast_mesh_bwd(const rast_params *p, const float *verts, int64_t V, const int64_t *faces, int64_t F,
@@ -312,6 +328,52 @@ int blend_fwd(const blend_params *bp, int64_t N, int64_t S, int64_t K, const int
         return MESHRAST_ERR_INVALID_ARG;
     if (!aligned16(image) || !aligned16(pix_to_face) || !aligned16(dists) || (zbuf && !aligned16(zbuf)))
         return MESHRAST_ERR_INVALID_ARG;
+    mr::BlendArgs a;
+    fill_blend(a, bp, N, S, K, pix_to_face, zbuf, bary, dists, faces, F, vert_colors, V);
+    a.image = image;
+    return mr::launch_blend_fwd(a, reinterpret_cast<cudaStream_t>(stream)) == cudaSuccess ? MESHRAST_OK
+                                                                                          : MESHRAST_ERR_CUDA;
+}
+
+int rast_blend_fwd(const rast_params *p, const blend_params *bp, const float *verts, int64_t V,
+                   const int64_t *faces, int64_t F, const int64_t *first_face, const int64_t *num_faces,
+                   const float *cams, const float *vert_colors, int64_t *pix_to_face, float *zbuf, float *bary,
+                   float *dists, float *image, void *workspace, size_t workspace_bytes, void *stream) {
+    if (!mr_host::check_params(p, V, F)) return MESHRAST_ERR_INVALID_ARG;
+    if (mr_host::unsupported(p)) return MESHRAST_ERR_UNSUPPORTED;
+    const int64_t N = p->N, S = p->image_size, K = p->faces_per_pixel;
+    int rc = check_blend(bp, N, S, K);
+    if (rc) return rc;
+    const bool rgb = bp->mode == MESHRAST_BLEND_RGB;
+    const int64_t P = N * S * S;
+    if (P > 0) {
+        if (!image || !aligned16(image)) return MESHRAST_ERR_INVALID_ARG;
+        if (!pix_to_face || !dists || !aligned16(pix_to_face) || !aligned16(dists) || (zbuf && !aligned16(zbuf)))
+            return MESHRAST_ERR_INVALID_ARG;
+        if (rgb && (!faces || !vert_colors)) return MESHRAST_ERR_INVALID_ARG;
+    }
+    mr::FineBlend fbl;
+    std::memset(&fbl, 0, sizeof(fbl));
+    fbl.on = 1;
+    fbl.rgb = rgb ? 1 : 0;
+    fbl.sigma = bp->sigma;
+    fbl.gamma = bp->gamma;
+    fbl.znear = bp->znear;
+    fbl.zfar = bp->zfar;
+    fbl.eps = bp->eps;
+    fbl.bg0 = bp->bg[0];
+    fbl.bg1 = bp->bg[1];
+    fbl.bg2 = bp->bg[2];
+    fbl.faces = faces;
+    fbl.colors = vert_colors;
+    fbl.F = F;
+    fbl.V = V;
+    fbl.image = image;
+    bool blended = false;
+    rc = forward(p, verts, V, faces, F, first_face, num_faces, cams, pix_to_face, zbuf, bary, dists, workspace,
+                 workspace_bytes, stream, &fbl, &blended);
+    if (rc || blended || P == 0) return rc;
+    // the plain form and K > 16: the blend kernel on the written fragments
     mr::BlendArgs a;
     fill_blend(a, bp, N, S, K, pix_to_face, zbuf, bary, dists, faces, F, vert_colors, V);
     a.image = image;

@@ -85,6 +85,56 @@ __device__ __forceinline__ float3 vertex_colour(const BlendArgs &a, int64_t v) {
     return make_float3(__ldg(col), __ldg(col + 1), __ldg(col + 2));
 }
 
+// Algorithms 1-2 accumulated slot by slot while the fine pass writes a pixel's
+// fragments (slots in output order, sorted by depth, so the first valid slot
+// holds the smallest depth).  The arithmetic and its order are those of
+// k_blend_fwd.
+struct FwdBlend {
+    float keep, zmin, range, m, num0, num1, num2, den;
+    bool face_max;
+    __device__ __forceinline__ void begin(const FineBlend &b, bool any, float zfirst) {
+        keep = 1.f;
+        num0 = num1 = num2 = den = 0.f;
+        zmin = any ? zfirst : __int_as_float(0x7f800000);
+        range = b.zfar - b.znear;
+        const float ztop = any ? (b.zfar - zmin) / range : -__int_as_float(0x7f800000);
+        face_max = any && ztop > b.eps;
+        m = face_max ? ztop : b.eps;
+    }
+    __device__ __forceinline__ void slot(const FineBlend &b, int f, float z, float d, const float bb[3]) {
+        keep *= sigmoidf_(d / b.sigma);
+        if (!b.rgb) return;
+        const float arg = face_max ? (zmin - z) / (range * b.gamma) : ((b.zfar - z) / range - m) / b.gamma;
+        const float w = sigmoidf_(-d / b.sigma) * expf(arg);
+        float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if ((int64_t)f >= b.F) continue;
+            const int64_t v = __ldg(b.faces + 3 * (int64_t)f + i);
+            if (v < 0 || v >= b.V) continue;
+            const float *col = b.colors + 3 * v;
+            c0 += bb[i] * __ldg(col);
+            c1 += bb[i] * __ldg(col + 1);
+            c2 += bb[i] * __ldg(col + 2);
+        }
+        num0 += w * c0;
+        num1 += w * c1;
+        num2 += w * c2;
+        den += w;
+    }
+    __device__ __forceinline__ void end(const FineBlend &b, int64_t pix) const {
+        float4 out = make_float4(0.f, 0.f, 0.f, 1.f - keep);
+        if (b.rgb) {
+            const float delta = expf((b.eps - m) / b.gamma);
+            const float D = den + delta;
+            out.x = (num0 + delta * b.bg0) / D;
+            out.y = (num1 + delta * b.bg1) / D;
+            out.z = (num2 + delta * b.bg2) / D;
+        }
+        reinterpret_cast<float4 *>(b.image)[pix] = out;
+    }
+};
+
 // pixel of a thread in the 16 x 16 tiled launch used by the backward kernels
 __device__ __forceinline__ bool tile_pixel(const BlendArgs &a, int64_t &pix) {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;

@@ -37,6 +37,7 @@ __device__ __forceinline__ void load_adjoint_rec(const FaceRec *rec, int f, Face
     R.a = __ldg(src);
     R.b = __ldg(src + 1);
     R.d = __ldg(src + 3);
+    R.e = __ldg(src + 4);
 }
 
 // one lane per face: colour atomics (softmax blend) and vertex atomics

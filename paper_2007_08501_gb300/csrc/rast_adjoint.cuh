@@ -16,7 +16,7 @@ __device__ __forceinline__ void edge_grad(float ax, float ay, float bx, float by
 }
 
 // NDC-space corner gradients of one slot: g[3*i + {0,1,2}] = dL/d(x_i, y_i, z_i)
-// of corner i (NDC x, NDC y, view depth).  Returns false for an empty slot.
+// of corner i (NDC x, NDC y, view depth).  Uses the record's a, b, d and e.
 __device__ __forceinline__ void slot_corner_grads(const FaceRec &R, const PixC &p, const EvalFlags &fl, float gz,
                                                   float gd, float gbp0, float gbp1, float gbp2, float (&g)[9]) {
     // ---- forward recompute (corner-0-relative coordinates) ----
@@ -24,7 +24,16 @@ __device__ __forceinline__ void slot_corner_grads(const FaceRec &R, const PixC &
     local_q(R, p, qx, qy);
     float b[3];
     screen_bary(R, qx, qy, b[0], b[1], b[2]);
+    // Coverage from the fp32 sign test of the forward.  The forward output the
+    // double-float barycentrics; fp32 ones are off by ~6e-8 edge^2/area, which
+    // near zero (a clip kink) or on a sliver can flip the sign of a clamped
+    // component, so those cases take the double-float values.
     const bool inside = (b[0] >= 0.f) && (b[1] >= 0.f) && (b[2] >= 0.f);
+    {
+        const float sliver = (R.b.x * R.b.x + R.b.y * R.b.y + R.b.z * R.b.z + R.b.w * R.b.w) * fabsf(R.d.x);
+        const float bmin = fminf(fabsf(b[0]), fminf(fabsf(b[1]), fabsf(b[2])));
+        if (sliver > 64.f || bmin < 1e-5f * fmaxf(1.f, sliver)) screen_bary_df(R, p, b[0], b[1], b[2]);
+    }
     int edge;
     float tseg;
     (void)nearest_edge(R, qx, qy, edge, tseg);

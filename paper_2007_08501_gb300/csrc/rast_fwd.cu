@@ -20,6 +20,7 @@
 
 #include "rast_common.cuh"
 #include "rast_internal.h"
+#include "blend_common.cuh"
 
 namespace mr {
 
@@ -318,10 +319,13 @@ __global__ void __launch_bounds__(256) k_fill(FillArgs a) {
 // ---------------------------------------------------------------------------
 // output of one pixel's K fragments
 // ---------------------------------------------------------------------------
-template <int KM>
+template <int KM, bool BL>
 __device__ __forceinline__ void write_pixel(const FineOut &o, int64_t pix, int K, const TopK<KM> &tk,
-                                            const FaceRec *rec, const PixC &p, const EvalFlags &fl) {
+                                            const FaceRec *rec, const PixC &p, const EvalFlags &fl,
+                                            const FineBlend &bl) {
     const int64_t s0 = pix * (int64_t)K;
+    FwdBlend fb;
+    if constexpr (BL) fb.begin(bl, tk.f[0] != 0x7fffffff, tk.z[0]);
 #pragma unroll
     for (int k = 0; k < KM; ++k) {
         if (k >= K) break;
@@ -350,21 +354,26 @@ __device__ __forceinline__ void write_pixel(const FineOut &o, int64_t pix, int K
             o.bary[3 * s + 1] = bp[1];
             o.bary[3 * s + 2] = bp[2];
             o.dists[s] = d;
+            if constexpr (BL) fb.slot(bl, f, tk.z[k], d, bp);
         }
     }
+    if constexpr (BL) fb.end(bl, pix);
 }
 
 // Fragments of one pixel's K winners written directly by the owning thread,
 // 16-byte vector stores when K is a multiple of 4 (ids: K/2, depths and
 // distances: K/4, barycentrics: 3K/4 stores per pixel).
 
-template <int KM>
+template <int KM, bool BL>
 __device__ __forceinline__ void write_pixel_vec(const FineOut &o, int64_t pix, int K, const TopK<KM> &tk,
-                                                const FaceRec *rec, const PixC &p, const EvalFlags &fl) {
+                                                const FaceRec *rec, const PixC &p, const EvalFlags &fl,
+                                                const FineBlend &bl) {
     if (K != KM || (KM % 4) != 0) {
-        write_pixel(o, pix, K, tk, rec, p, fl);
+        write_pixel<KM, BL>(o, pix, K, tk, rec, p, fl, bl);
         return;
     }
+    FwdBlend fb;
+    if constexpr (BL) fb.begin(bl, tk.f[0] != 0x7fffffff, tk.z[0]);
     const int64_t s0 = pix * KM;
     longlong2 *ip = reinterpret_cast<longlong2 *>(o.pix_to_face + s0);
     float4 *zp = reinterpret_cast<float4 *>(o.zbuf + s0);
@@ -397,6 +406,7 @@ __device__ __forceinline__ void write_pixel_vec(const FineOut &o, int64_t pix, i
             R.e = __ldg(src + 4);
             face_fragment(R, p, fl, bb[i], dd[i]);
             zz[i] = tk.z[k];
+            if constexpr (BL) fb.slot(bl, tk.f[k], zz[i], dd[i], bb[i]);
         }
         zp[j] = make_float4(zz[0], zz[1], zz[2], zz[3]);
         dp[j] = make_float4(dd[0], dd[1], dd[2], dd[3]);
@@ -404,6 +414,7 @@ __device__ __forceinline__ void write_pixel_vec(const FineOut &o, int64_t pix, i
         bp[3 * j + 1] = make_float4(bb[1][1], bb[1][2], bb[2][0], bb[2][1]);
         bp[3 * j + 2] = make_float4(bb[2][2], bb[3][0], bb[3][1], bb[3][2]);
     }
+    if constexpr (BL) fb.end(bl, pix);
 }
 
 // large-K variant: per-thread sorted lists in shared memory, [k][thread]
@@ -474,7 +485,7 @@ __device__ __forceinline__ void write_pixel_smem(const FineOut &o, int64_t pix, 
 // ---------------------------------------------------------------------------
 // fine pass: persistent blocks, one bin (bin x bin pixels = block) per item
 // ---------------------------------------------------------------------------
-template <int KM, int BS>
+template <int KM, int BS, bool BL>
 __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
     constexpr int BD = BS * BS;
     __shared__ FaceRec s_rec[BD];
@@ -679,7 +690,7 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
             __syncthreads();
         }
         if constexpr (KM > 0) {
-            if (valid) write_pixel_vec(a.out, ((int64_t)n * a.S + r) * a.S + c, a.K, tk, a.rec, p, fl);
+            if (valid) write_pixel_vec<KM, BL>(a.out, ((int64_t)n * a.S + r) * a.S + c, a.K, tk, a.rec, p, fl, a.blend);
         } else {
             // K > 16: the block writes its tile slot by slot: consecutive
             // threads take consecutive output slots of a tile row (coalesced),
@@ -774,7 +785,7 @@ __global__ void __launch_bounds__(256) k_naive(NaiveArgs a, int n) {
         }
     }
     const int64_t pix = (int64_t)n * a.S * a.S + pidx;
-    if constexpr (KM > 0) write_pixel(a.out, pix, a.K, tk, a.rec, p, fl);
+    if constexpr (KM > 0) write_pixel<KM, false>(a.out, pix, a.K, tk, a.rec, p, fl, FineBlend{});
     else write_pixel_smem(a.out, pix, a.K, stk, a.rec, p, fl);
 }
 
@@ -790,12 +801,12 @@ static int km_for(int K) {
     return 0;  // shared-memory lists
 }
 
-template <int KM, int BS>
+template <int KM, int BS, bool BL>
 static cudaError_t launch_fine_t(const FineArgs &a, cudaStream_t st) {
     constexpr int BD = BS * BS;
     // the sort buffer; KM == 0: the same memory then holds the per-thread lists
     const size_t dyn = std::max((size_t)a.sort_cap * 8, (KM > 0) ? (size_t)0 : (size_t)BD * a.K * 8);
-    auto kern = k_fine<KM, BS>;
+    auto kern = k_fine<KM, BS, BL>;
     cudaError_t e = cudaSuccess;
     if (dyn > 0) {  // static + dynamic above 48 KB needs the opt-in
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
@@ -809,15 +820,27 @@ static cudaError_t launch_fine_t(const FineArgs &a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// The silhouette blend runs inside the fine pass for K <= 16; the softmax
+// blend does not (its colour gathers cost the fine pass more than the separate
+// blend kernel's pass over the fragments).
+bool fine_blends(int K, bool rgb) { return km_for(K) > 0 && !rgb; }
+
 cudaError_t launch_fine(const FineArgs &a, int bin, cudaStream_t st) {
     const int km = km_for(a.K);
-#define MR_FINE(KM_)                                              \
-    if (km == KM_) {                                              \
-        if (bin == 8) return launch_fine_t<KM_, 8>(a, st);        \
-        if (bin == 16) return launch_fine_t<KM_, 16>(a, st);      \
+    const bool bl = a.blend.on != 0;
+#define MR_FINE(KM_)                                                          \
+    if (km == KM_) {                                                          \
+        if (bin == 8) return bl ? launch_fine_t<KM_, 8, true>(a, st)          \
+                                : launch_fine_t<KM_, 8, false>(a, st);        \
+        if (bin == 16) return bl ? launch_fine_t<KM_, 16, true>(a, st)        \
+                                 : launch_fine_t<KM_, 16, false>(a, st);      \
     }
-    MR_FINE(1) MR_FINE(2) MR_FINE(4) MR_FINE(8) MR_FINE(16) MR_FINE(0)
+    MR_FINE(1) MR_FINE(2) MR_FINE(4) MR_FINE(8) MR_FINE(16)
 #undef MR_FINE
+    if (km == 0) {
+        if (bin == 8) return launch_fine_t<0, 8, false>(a, st);
+        if (bin == 16) return launch_fine_t<0, 16, false>(a, st);
+    }
     return cudaErrorInvalidValue;
 }
 

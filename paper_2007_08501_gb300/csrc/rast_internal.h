@@ -54,6 +54,18 @@ struct FineOut {
     float *zbuf, *bary, *dists;
 };
 
+// Blend (Algorithm 1; the fields of Algorithm 2 are kept for FwdBlend) applied
+// by the fine pass to each pixel's fragments as it writes them (register path,
+// K <= 16): same arithmetic as blend_fwd.
+struct FineBlend {
+    int on, rgb;
+    float sigma, gamma, znear, zfar, eps, bg0, bg1, bg2;
+    const int64_t *faces;
+    const float *colors;
+    int64_t F, V;
+    float *image;
+};
+
 struct FineArgs {
     const FaceRec *rec;
     const float *cams;
@@ -64,6 +76,7 @@ struct FineArgs {
     int sort_cap;  // bin entries sorted at a time (power of two)
     EvalFlags fl;
     FineOut out;
+    FineBlend blend;
 };
 
 struct NaiveArgs {
@@ -112,6 +125,7 @@ cudaError_t launch_stage(const StageArgs &a, cudaStream_t st);
 cudaError_t launch_scan(const ScanArgs &a, cudaStream_t st);
 cudaError_t launch_fill(const FillArgs &a, cudaStream_t st);
 cudaError_t launch_fine(const FineArgs &a, int bin, cudaStream_t st);
+bool fine_blends(int K, bool rgb);  // whether launch_fine applies FineArgs::blend
 cudaError_t launch_naive(const NaiveArgs &a, int N, cudaStream_t st);
 cudaError_t launch_rast_bwd(const RastBwdArgs &a, int N, cudaStream_t st);
 cudaError_t launch_blend_fwd(const BlendArgs &a, cudaStream_t st);

@@ -33,7 +33,7 @@ BLEND_RGB = 1
 
 EXPORTED = ("rast_workspace_bytes", "rast_mesh_fwd", "rast_mesh_bwd", "blend_fwd", "blend_bwd",
             "rast_query_status", "rast_bin_occupancy", "rast_strerror", "rast_mesh_fwd_static",
-            "blend_rast_bwd")
+            "blend_rast_bwd", "rast_blend_fwd")
 
 
 class rast_params(ctypes.Structure):
@@ -86,6 +86,8 @@ def load(build_if_missing: bool = False):
     L.blend_fwd.restype = ctypes.c_int
     L.blend_bwd.argtypes = [B, i64, i64, i64, vp, vp, vp, vp, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp]
     L.blend_bwd.restype = ctypes.c_int
+    L.rast_blend_fwd.argtypes = [P, B, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.rast_blend_fwd.restype = ctypes.c_int
     L.blend_rast_bwd.argtypes = [P, B, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
     L.blend_rast_bwd.restype = ctypes.c_int
     L.rast_query_status.argtypes = [vp, ctypes.POINTER(ctypes.c_uint32), vp]
@@ -225,6 +227,20 @@ def blend_bwd(bp, N, S, K, pix_to_face, zbuf, bary, dists, faces, vert_colors, g
                           _ptr(grad_bary, torch.float32, "grad_bary"), _ptr(grad_dists, torch.float32, "grad_dists"),
                           _ptr(grad_vert_colors, torch.float32, "grad_vert_colors"), _stream(stream))
     _check(rc, "blend_bwd")
+
+
+def rast_blend_fwd(p, bp, verts, faces, first_face, num_faces, cams, vert_colors, pix_to_face, zbuf, bary, dists,
+                   image, workspace, stream=None):
+    """rast_mesh_fwd and blend_fwd in one call (the fine pass blends as it writes)."""
+    rc = load().rast_blend_fwd(
+        ctypes.byref(p), ctypes.byref(bp), _ptr(verts, torch.float32, "verts"), verts.shape[0],
+        _ptr(faces, torch.int64, "faces"), faces.shape[0],
+        _ptr(first_face, torch.int64, "first_face"), _ptr(num_faces, torch.int64, "num_faces"),
+        _ptr(cams, torch.float32, "cams"), _ptr(vert_colors, torch.float32, "vert_colors"),
+        _ptr(pix_to_face, torch.int64, "pix_to_face"), _ptr(zbuf, torch.float32, "zbuf"),
+        _ptr(bary, torch.float32, "bary"), _ptr(dists, torch.float32, "dists"), _ptr(image, torch.float32, "image"),
+        _ptr(workspace, None, "workspace"), workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "rast_blend_fwd")
 
 
 def blend_rast_bwd(p, bp, verts, faces, first_face, num_faces, cams, pix_to_face, zbuf, bary, dists, vert_colors,

@@ -178,3 +178,42 @@ def test_render_meshes_autograd_equals_separate_functions(rgb):
     assert np.linalg.norm(out[0][1] - ref) <= 1e-5 * np.linalg.norm(ref)
     if rgb:
         assert np.linalg.norm(out[0][2] - out[1][2]) <= 1e-5 * np.linalg.norm(out[1][2])
+
+
+@pytest.mark.parametrize("mode,K,bin_size,clip", [
+    (ops.BLEND_RGB, 8, 16, True),     # fine pass blends (vector write path)
+    (ops.BLEND_RGB, 8, 8, True),
+    (ops.BLEND_SIL, 4, 16, True),
+    (ops.BLEND_SIL, 1, 8, False),
+    (ops.BLEND_RGB, 5, 16, True),     # fine pass blends (scalar write path, K < 8)
+    (ops.BLEND_RGB, 16, 16, False),
+    (ops.BLEND_RGB, 20, 8, True),     # K > 16: separate blend kernel inside the call
+    (ops.BLEND_SIL, 4, 0, True),      # plain form: separate blend kernel
+])
+def test_fused_forward_equals_rasterize_then_blend(mode, K, bin_size, clip):
+    b = workloads.sphere_batch([3, 2, 4], 0.05, seed_base=71)
+    d = to_dev(b)
+    N, S = b.N, 70                                   # ragged: 70 = 4 * 16 + 6
+    blur = BLUR if clip or mode == ops.BLEND_RGB else 0.0
+    p = ops.make_rast_params(N, S, K, np.float32(blur), bin_size, 4096, True, clip)
+    ws = ops.alloc_workspace(p, b.V, b.F)
+    colors = torch.from_numpy(b.colors).cuda()
+    bp = ops.make_blend_params(SIGMA, GAMMA, ZNEAR, ZFAR, (1.0, 1.0, 1.0), 1e-10, mode)
+    ref = ops.alloc_fragments(N, S, K)
+    ops.rast_mesh_fwd(p, d["verts"], d["faces"], d["first_face"], d["num_faces"], d["cams"], *ref, ws)
+    ref_img = torch.empty((N, S, S, 4), device="cuda")
+    ops.blend_fwd(bp, N, S, K, *ref[:4], d["faces"], colors, ref_img)
+    got = ops.alloc_fragments(N, S, K)
+    img = torch.full((N, S, S, 4), 7.0, device="cuda")
+    ops.rast_blend_fwd(p, bp, d["verts"], d["faces"], d["first_face"], d["num_faces"], d["cams"],
+                       colors if mode else None, *got, img, ws)
+    assert ops.rast_query_status(ws) == 0
+    for x, y in zip(ref, got):
+        assert torch.equal(x, y)
+    assert np.max(np.abs(img.cpu().numpy() - ref_img.cpu().numpy())) <= 1e-6
+    # and the image matches the oracle blend of these fragments
+    fn = [x.cpu().numpy() for x in got]
+    P = N * S * S
+    orc = oracle.blend_fwd(fn[0].reshape(P, K), fn[1].reshape(P, K), fn[2].reshape(P, K, 3), fn[3].reshape(P, K),
+                           b.faces, b.colors, _f32(SIGMA), _f32(GAMMA), _f32(ZNEAR), _f32(ZFAR), mode=mode)
+    assert np.max(np.abs(img.cpu().numpy().reshape(P, 4) - orc)) <= 1e-5

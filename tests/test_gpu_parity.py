@@ -194,6 +194,14 @@ def test_rast_bwd_matches_oracle_adjoint(persp, clip, blur, bin_size):
     _rast_bwd_check(b, 48, 4, blur, bin_size, persp, clip)
 
 
+def test_rast_bwd_at_clip_kinks_of_outside_pixels():
+    # pixels outside a face near its corner, where the clipped barycentrics are
+    # (0, 0, 1): the adjoint must see the forward's double-float barycentrics
+    # (fp32 ones can put a clamped component on the wrong side of zero)
+    b = workloads.sphere_batch([3, 3], 0.05, seed_base=2024)
+    _rast_bwd_check(b, 64, 4, BLUR, 16, True, True)
+
+
 def test_rast_bwd_shared_vertices_across_images():
     # two images of ONE mesh: both images' faces index the same vertices
     v, f = workloads.displaced_sphere(2, 0.05, np.random.default_rng(3))
