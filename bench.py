@@ -50,10 +50,14 @@ WORKLOADS = {
                  "blur=ln(1/1e-4-1)*1e-4, soft silhouette, fwd+bwd to verts"),
 }
 KERNELS_PER_STEP = {"fwd": 4, "bwd": 2}
-# DRAM bytes (read + write) per launch of each stage's main kernel, from one
-# ncu capture of this workload with the current kernel source (summary in
-# profiles/); a stage without an entry reports null.
-TRAFFIC_BYTES = {}
+# DRAM bytes (read + write) per launch of a stage's main kernel, keyed by
+# (workload, stage, bin size), from one ncu capture with the current kernel
+# source (summaries in profiles/); a combination without an entry reports null.
+TRAFFIC_BYTES = {
+    ("1", "fwd", 8): {"kernel": "k_fine<8,8,0>", "bytes": 10693376 + 66129664},
+    ("1", "bwd", 8): {"kernel": "k_blend_rast_bwd<8,1>", "bytes": 104484352 + 3294464},
+    ("1", "bwd", 16): {"kernel": "k_blend_rast_bwd<8,1>", "bytes": 104484352 + 3294464},
+}
 
 
 def _args():
@@ -67,6 +71,8 @@ def _args():
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain per-mesh form")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fit", action="store_true", help="workload 4: skip timing the fitting loop")
+    ap.add_argument("--bin-size", type=int, default=0, choices=[0, 8, 16],
+                    help="fix the bin size (0: the autotuner picks 8 or 16)")
     ap.add_argument("--max-images", type=int, default=0,
                     help="keep only the first N images of the workload (small cases for profiling)")
     ap.add_argument("--no-separate", action="store_true",
@@ -370,7 +376,8 @@ def run_ours(args):
     from paper_2007_08501_gb300 import tune
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     tuned = tune.tune(T(b.verts), T(b.faces), T(b.first_face), T(b.num_faces), T(b.cams), w.image_size, w.K,
-                      float(np.float32(w.blur_radius)), w.perspective_correct, w.clip_barycentric_coords)
+                      float(np.float32(w.blur_radius)), w.perspective_correct, w.clip_barycentric_coords,
+                      bin_sizes=(args.bin_size,) if args.bin_size else (8, 16))
     pipe = Pipeline(w, bin_size=tuned["bin_size"], max_faces_per_bin=tuned["max_faces_per_bin"], device=dev,
                     max_bin_entries=tuned["max_bin_entries"])
     pipe.run_eager()
@@ -416,7 +423,7 @@ def run_ours(args):
     alg = algorithmic_bytes(w)
     peak, peak_kind = _peaks()
     achieved = alg[dom] / (stages[dom] / 1e3) / 1e9
-    tr = TRAFFIC_BYTES.get(dom)
+    tr = TRAFFIC_BYTES.get((args.workload, dom, tuned["bin_size"]))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": tr["bytes"] if tr else None,
                 "traffic_kernel": tr["kernel"] if tr else None, "algorithmic_bytes": alg[dom], "kernel": dom,

@@ -8,7 +8,7 @@ size the tuner runs one forward with generous capacities, reads the real
 occupancy back (``rast_bin_occupancy``), sizes the capacities with headroom,
 times a few forwards with CUDA events and keeps the fastest.  Results are
 cached per (N, image size, K, blur > 0, clipping, perspective, log2 of the
-face count) in ``tuned.json`` next to this file.
+face count, candidate bin sizes) in ``tuned.json`` next to this file.
 
 Tuning synchronises and allocates; run it before capturing a CUDA graph.
 """
@@ -28,9 +28,9 @@ _CACHE_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned.js
 _lock = threading.Lock()
 
 
-def _key(N, S, K, blur, persp, clip, F):
-    return "N%d_S%d_K%d_b%d_c%d_p%d_F%d" % (N, S, K, int(blur > 0), int(bool(clip)), int(bool(persp)),
-                                            int(math.log2(max(F, 1))))
+def _key(N, S, K, blur, persp, clip, F, bin_sizes):
+    return "N%d_S%d_K%d_b%d_c%d_p%d_F%d_bins%s" % (N, S, K, int(blur > 0), int(bool(clip)), int(bool(persp)),
+                                                   int(math.log2(max(F, 1))), "-".join(str(b) for b in bin_sizes))
 
 
 def _load_cache():
@@ -59,7 +59,7 @@ def tune(verts, faces, first_face, num_faces, cams, image_size, K, blur_radius=0
          clip_barycentric_coords=False, bin_sizes=(8, 16), reps=5, use_cache=True):
     """Returns dict(bin_size, max_faces_per_bin, max_bin_entries, ms, candidates)."""
     N, V, F = first_face.shape[0], verts.shape[0], faces.shape[0]
-    key = _key(N, image_size, K, blur_radius, perspective_correct, clip_barycentric_coords, F)
+    key = _key(N, image_size, K, blur_radius, perspective_correct, clip_barycentric_coords, F, bin_sizes)
     with _lock:
         cache = _load_cache() if use_cache else {}
         if key in cache:
