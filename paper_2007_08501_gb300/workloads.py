@@ -301,6 +301,75 @@ def target_sphere(seed=4321, level=6, sigma=0.05):
 
 
 # --------------------------------------------------------------------------
+# point clouds: points sampled uniformly from displaced sphere surfaces
+# --------------------------------------------------------------------------
+@dataclass
+class PointBatch:
+    points: np.ndarray       # (P,3) f32
+    first_point: np.ndarray  # (N,) i64
+    num_points: np.ndarray   # (N,) i64
+    cams: np.ndarray         # (N,16) f32
+    features: np.ndarray     # (P,D) f32
+
+    @property
+    def N(self):
+        return int(self.first_point.shape[0])
+
+    @property
+    def P(self):
+        return int(self.points.shape[0])
+
+
+def sample_surface(verts, faces, n, rng):
+    """``n`` points uniform over the surface: faces by area, then uniform barycentrics."""
+    a, b, c = verts[faces[:, 0]], verts[faces[:, 1]], verts[faces[:, 2]]
+    area = 0.5 * np.linalg.norm(np.cross(b - a, c - a), axis=1)
+    fi = rng.choice(faces.shape[0], size=n, p=area / area.sum())
+    u, v = rng.random(n), rng.random(n)
+    flip = u + v > 1.0
+    u[flip], v[flip] = 1.0 - u[flip], 1.0 - v[flip]
+    return a[fi] + u[:, None] * (b[fi] - a[fi]) + v[:, None] * (c[fi] - a[fi])
+
+
+def point_batch(counts, seed_base, level=4, sigma=0.05, D=1, cams=None):
+    """One cloud per image with ``counts[i]`` points; cloud i draws from seed ``seed_base + i``.
+    Features are 1 (silhouette) for D == 1, else U[0,1]."""
+    pts, cam_rows, feats = [], [], []
+    for i, n in enumerate(counts):
+        rng = np.random.default_rng(seed_base + i)
+        v, f = displaced_sphere(level, sigma, rng)
+        pts.append(sample_surface(v, f, int(n), rng))
+        cam_rows.append(random_camera(rng) if cams is None else cams[i])
+        feats.append(np.ones((int(n), 1)) if D == 1 else rng.uniform(0.0, 1.0, size=(int(n), D)))
+    counts = np.asarray(counts, np.int64)
+    first = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64)
+    return PointBatch(np.concatenate(pts, 0).astype(np.float32), first, counts,
+                      np.stack(cam_rows, 0).astype(np.float32), np.concatenate(feats, 0).astype(np.float32))
+
+
+POINT_RADIUS = 0.01   # NDC units: 1.28 pixels at 256 x 256
+
+
+@dataclass
+class PointWorkload:
+    name: str
+    batch: PointBatch
+    image_size: int
+    K: int
+    radius: float
+    mode: int                # 0: Alpha compositing, 1: Norm
+    grad_seed: int = 0
+
+
+def point_workload(mode: int = 0) -> PointWorkload:
+    """The point renderer benchmark: 8 clouds x 200,000 points sampled from displaced
+    level-4 spheres, 256 x 256, K = 50, silhouettes (D = 1)."""
+    b = point_batch([200_000] * 8, 5000, level=4, sigma=0.05)
+    return PointWorkload("8 clouds x 200,000 points, 256x256, K=50, silhouette, %s compositing"
+                         % ("Alpha" if mode == 0 else "Norm"), b, 256, 50, POINT_RADIUS, mode, grad_seed=5500)
+
+
+# --------------------------------------------------------------------------
 # pixel sampling for oracle checks on large images
 # --------------------------------------------------------------------------
 def sample_pixels(N, S, per_image, seed):
