@@ -202,11 +202,11 @@ int orp_composite_fwd(int64_t npix, int64_t K, const int64_t *idx, const double 
 
 /* Adjoint of orp_composite_fwd for upstream grad_out (npix, D): grad_dists
  * (npix, K) (0 on empty slots) and grad_features (P, D) (accumulated, the
- * caller zeroes it).  grad_features_abs (may be NULL) accumulates the
- * magnitudes of the terms. */
+ * caller zeroes it).  grad_features_abs and grad_dists_abs (either may be
+ * NULL) receive the magnitudes of the terms that form each component. */
 int orp_composite_bwd(int64_t npix, int64_t K, const int64_t *idx, const double *dists, const double *features,
                       int64_t D, double radius, int mode, const double *grad_out, double *grad_dists,
-                      double *grad_features, double *grad_features_abs) {
+                      double *grad_features, double *grad_features_abs, double *grad_dists_abs) {
     const double r2 = radius * radius;
     double *a = (double *)malloc(sizeof(double) * (size_t)K);
     double *T = (double *)malloc(sizeof(double) * (size_t)K);
@@ -219,6 +219,7 @@ int orp_composite_bwd(int64_t npix, int64_t K, const int64_t *idx, const double 
         for (int64_t k = 0; k < K; k++) {
             const int64_t i = idx[p * K + k];
             grad_dists[p * K + k] = 0.0;
+            if (grad_dists_abs) grad_dists_abs[p * K + k] = 0.0;
             if (i < 0) { a[k] = 0.0; T[k] = Tc; continue; }
             a[k] = orp_alpha(dists[p * K + k], radius);
             T[k] = Tc;
@@ -233,14 +234,16 @@ int orp_composite_bwd(int64_t npix, int64_t K, const int64_t *idx, const double 
             for (int64_t k = 0; k < K; k++) {
                 const int64_t i = idx[p * K + k];
                 if (i < 0) continue;
-                double ga = 0.0;
+                double ga = 0.0, gabs = 0.0;
                 for (int64_t c = 0; c < D; c++) {
                     const double t = a[k] / asum * g[c];
                     grad_features[i * D + c] += t;
                     if (grad_features_abs) grad_features_abs[i * D + c] += fabs(t);
                     ga += g[c] * (features[i * D + c] - out[c]) / asum;
+                    gabs += fabs(g[c]) * (fabs(features[i * D + c]) + fabs(out[c])) / asum;
                 }
                 grad_dists[p * K + k] = -ga / r2;
+                if (grad_dists_abs) grad_dists_abs[p * K + k] = gabs / r2;
             }
         } else {
             /* f = P_k + T_k (a_k f_k + (1 - a_k) S_k), S_k the composite of the slots after
@@ -249,16 +252,18 @@ int orp_composite_bwd(int64_t npix, int64_t K, const int64_t *idx, const double 
             for (int64_t k = K - 1; k >= 0; k--) {
                 const int64_t i = idx[p * K + k];
                 if (i < 0) continue;
-                double ga = 0.0;
+                double ga = 0.0, gabs = 0.0;
                 for (int64_t c = 0; c < D; c++) {
                     const double fc = features[i * D + c];
                     const double t = a[k] * T[k] * g[c];
                     grad_features[i * D + c] += t;
                     if (grad_features_abs) grad_features_abs[i * D + c] += fabs(t);
                     ga += g[c] * T[k] * (fc - S[c]);
+                    gabs += fabs(g[c]) * T[k] * (fabs(fc) + fabs(S[c]));
                     S[c] = a[k] * fc + (1.0 - a[k]) * S[c];
                 }
                 grad_dists[p * K + k] = -ga / r2;
+                if (grad_dists_abs) grad_dists_abs[p * K + k] = gabs / r2;
             }
         }
     }

@@ -55,7 +55,7 @@ def _load():
                                   _u8p]
         L.orp_composite_fwd.argtypes = [_i64, _i64, _i64p, _f64p, _f64p, _i64, _dbl, _int, _f64p]
         L.orp_composite_bwd.argtypes = [_i64, _i64, _i64p, _f64p, _f64p, _i64, _dbl, _int, _f64p, _f64p, _f64p,
-                                        _f64p]
+                                        _f64p, _f64p]
         L.orp_rast_bwd.argtypes = [_f64p, _i64, _i64p, _i64p, _i64, _f64p, _i64, _i64, _i64p, _f64p, _f64p,
                                    _i64p, _i64, _f64p, _f64p]
         _lib = L
@@ -145,7 +145,8 @@ def composite_fwd(idx, dists, features, radius, mode=ALPHA):
 
 
 def composite_bwd(idx, dists, features, radius, grad_out, mode=ALPHA, with_abs=False):
-    """(grad_dists (npix, K), grad_features (P, D)[, grad_features_abs])."""
+    """(grad_dists (npix, K), grad_features (P, D)[, grad_features_abs, grad_dists_abs]): the
+    *_abs arrays hold the magnitudes of the terms that form each component."""
     L = _load()
     idx = _i(idx)
     K = idx.shape[-1]
@@ -155,9 +156,11 @@ def composite_bwd(idx, dists, features, radius, grad_out, mode=ALPHA, with_abs=F
     gdi = np.zeros((npix, K))
     gf = np.zeros_like(feats)
     ga = np.zeros_like(feats) if with_abs else None
+    gda = np.zeros((npix, K)) if with_abs else None
     L.orp_composite_bwd(npix, K, _p(idx, _i64p), _p(_d(dists), _f64p), _p(feats, _f64p), D, float(radius), mode,
-                        _p(_d(grad_out).reshape(npix, D), _f64p), _p(gdi, _f64p), _p(gf, _f64p), _p(ga, _f64p))
-    return (gdi, gf, ga) if with_abs else (gdi, gf)
+                        _p(_d(grad_out).reshape(npix, D), _f64p), _p(gdi, _f64p), _p(gf, _f64p), _p(ga, _f64p),
+                        _p(gda, _f64p))
+    return (gdi, gf, ga, gda) if with_abs else (gdi, gf)
 
 
 def rast_bwd(c: Clouds, S, K, idx, grad_zbuf, grad_dists, pixels=None, with_abs=False):

@@ -21,37 +21,13 @@
 #include "rast_common.cuh"
 #include "rast_internal.h"
 #include "blend_common.cuh"
+#include "bin_common.cuh"
 
 namespace mr {
 
 // ---------------------------------------------------------------------------
 // staging
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int find_mesh(const int64_t *first_face, int N, int64_t f) {
-    int lo = 0, hi = N - 1, ans = -1;
-    while (lo <= hi) {
-        int mid = (lo + hi) >> 1;
-        if (first_face[mid] <= f) { ans = mid; lo = mid + 1; } else { hi = mid - 1; }
-    }
-    return ans;
-}
-
-// world -> view -> NDC of one corner, in double-float arithmetic
-__device__ __forceinline__ void project_corner(const float *cam, float px, float py, float pz, df &X, df &Y,
-                                               df &Z) {
-    df d0 = two_sum(px, -cam[9]), d1 = two_sum(py, -cam[10]), d2 = two_sum(pz, -cam[11]);
-    df x = df_add(df_add(df_mul_f(d0, cam[0]), df_mul_f(d1, cam[1])), df_mul_f(d2, cam[2]));
-    df y = df_add(df_add(df_mul_f(d0, cam[3]), df_mul_f(d1, cam[4])), df_mul_f(d2, cam[5]));
-    df z = df_add(df_add(df_mul_f(d0, cam[6]), df_mul_f(d1, cam[7])), df_mul_f(d2, cam[8]));
-    float f = cam[12];
-    X = df_div(df_mul_f(x, f), z);
-    Y = df_div(df_mul_f(y, f), z);
-    Z = z;
-}
-
-__device__ __forceinline__ df df_min(df a, df b) { return (a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo)) ? a : b; }
-__device__ __forceinline__ df df_max(df a, df b) { return (a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo)) ? a : b; }
-
 // Build the record of face f; returns the mesh index or -1 when culled.
 __device__ int stage_face(const StageArgs &a, int64_t f, FaceRec &R) {
     const float kInf = __int_as_float(0x7f800000);
@@ -108,43 +84,6 @@ __device__ int stage_face(const StageArgs &a, int64_t f, FaceRec &R) {
     const float l0 = (wx - ux) * (wx - ux) + (wy - uy) * (wy - uy), l1 = wx * wx + wy * wy, l2 = ux * ux + uy * uy;
     R.h = make_float4(A2 / l0, A2 / l1, A2 / l2, 0.f);
     return n;
-}
-
-// Columns (or rows) whose fp32 pixel centre lies in [lo, hi]: first index
-// with centre <= hi, last index with centre >= lo (centres decrease with the
-// index).  Exactly the comparisons the fine pass makes.
-__device__ __forceinline__ float pc_hi(int i, int S) {
-    float h, l;
-    pix_coord(i, S, h, l);
-    return h;
-}
-__device__ __forceinline__ void centre_range(float lo, float hi, int S, int &i0, int &i1) {
-    float Sf = (float)S;
-    int a = (int)ceilf(fminf(fmaxf(((Sf - 1.f) - hi * Sf) * 0.5f, -1.f), Sf));
-    a = max(0, min(a, S));
-    while (a > 0 && pc_hi(a - 1, S) <= hi) --a;
-    while (a < S && pc_hi(a, S) > hi) ++a;
-    int b = (int)floorf(fminf(fmaxf(((Sf - 1.f) - lo * Sf) * 0.5f, -1.f), Sf));
-    b = max(-1, min(b, S - 1));
-    while (b < S - 1 && pc_hi(b + 1, S) >= lo) ++b;
-    while (b >= 0 && pc_hi(b, S) < lo) --b;
-    i0 = a;
-    i1 = b;
-}
-
-// Bins (bx0..bx1, by0..by1) of a face: the bin's pixel-centre span meets the
-// inflated bbox.  Empty when bx0 > bx1 or by0 > by1.
-__device__ __forceinline__ void bin_rect(const FaceRec &R, int S, int bin, int &bx0, int &bx1, int &by0,
-                                         int &by1) {
-    if (!(R.c.x <= R.c.y) || !(R.c.z <= R.c.w)) { bx0 = 1; bx1 = 0; by0 = 1; by1 = 0; return; }
-    int c0, c1, r0, r1;
-    centre_range(R.c.x, R.c.y, S, c0, c1);
-    centre_range(R.c.z, R.c.w, S, r0, r1);
-    if (c0 > S - 1 || c1 < 0 || r0 > S - 1 || r1 < 0) { bx0 = 1; bx1 = 0; by0 = 1; by1 = 0; return; }
-    bx0 = c0 / bin;
-    bx1 = c1 / bin;
-    by0 = r0 / bin;
-    by1 = r1 / bin;
 }
 
 __global__ void __launch_bounds__(256) k_stage(StageArgs a) {
@@ -417,38 +356,6 @@ __device__ __forceinline__ void write_pixel_vec(const FineOut &o, int64_t pix, i
     if constexpr (BL) fb.end(bl, pix);
 }
 
-// large-K variant: per-thread sorted lists in shared memory, [k][thread]
-struct SmemTopK {
-    float *z;
-    int *f;
-    int stride, K;
-    int n;  // entries held (< K while the list is not full)
-    __device__ __forceinline__ void init() { n = 0; }
-    // K-th smallest depth so far (infinite until K candidates were kept)
-    __device__ __forceinline__ float thr() const {
-        return n < K ? __int_as_float(0x7f800000) : z[(K - 1) * stride];
-    }
-    __device__ __forceinline__ bool admits(float zz, int ff) const {
-        return n < K || key_less(zz, ff, z[(K - 1) * stride], f[(K - 1) * stride]);
-    }
-    // insertion from the end of the held entries: candidates arrive nearly in
-    // depth order, so most insertions are appends
-    __device__ __forceinline__ void insert(float zz, int ff) {
-        int k = n < K ? n : K - 1;
-        while (k > 0) {
-            float zp = z[(k - 1) * stride];
-            int fp = f[(k - 1) * stride];
-            if (!key_less(zz, ff, zp, fp)) break;
-            z[k * stride] = zp;
-            f[k * stride] = fp;
-            --k;
-        }
-        z[k * stride] = zz;
-        f[k * stride] = ff;
-        if (n < K) ++n;
-    }
-};
-
 __device__ __forceinline__ void write_pixel_smem(const FineOut &o, int64_t pix, int K, const SmemTopK &tk,
                                                  const FaceRec *rec, const PixC &p, const EvalFlags &fl) {
     const int64_t s0 = pix * (int64_t)K;
@@ -537,60 +444,12 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
         // walked.  K > 16: every segment is sorted first and written back to
         // the (block-owned) list, so that the same shared memory then holds
         // the per-pixel lists.
-        auto sort_segment = [&](int seg, int m) {
-            int n2 = 32;
-            while (n2 < m) n2 <<= 1;
-            if (n2 <= BD) {
-                // one entry per thread: partners closer than 32 trade through
-                // shuffles, farther ones through shared memory
-                unsigned long long v = tid < m ? a.lists[off + seg + tid] : ~0ull;
-#pragma unroll 1
-                for (int k2 = 2; k2 <= n2; k2 <<= 1) {
-#pragma unroll 1
-                    for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
-                        unsigned long long o;
-                        if (j2 >= 32) {
-                            s_sort[tid] = v;
-                            __syncthreads();
-                            o = s_sort[tid ^ j2];
-                            __syncthreads();
-                        } else {
-                            o = __shfl_xor_sync(0xffffffffu, v, j2);
-                        }
-                        const bool keep_min = ((tid & j2) == 0) == ((tid & k2) == 0);
-                        v = keep_min ? (o < v ? o : v) : (o > v ? o : v);
-                    }
-                }
-                s_sort[tid] = v;
-                __syncthreads();
-                return;
-            }
-            for (int i = tid; i < n2; i += BD) s_sort[i] = i < m ? a.lists[off + seg + i] : ~0ull;
-            __syncthreads();
-            // bitonic sort in shared memory (padding entries sort last)
-#pragma unroll 1
-            for (int k2 = 2; k2 <= n2; k2 <<= 1) {
-#pragma unroll 1
-                for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
-                    for (int i = tid; i < (n2 >> 1); i += BD) {
-                        const int lo = ((i & ~(j2 - 1)) << 1) | (i & (j2 - 1));
-                        const int hi = lo + j2;
-                        const unsigned long long x = s_sort[lo], y = s_sort[hi];
-                        if ((x > y) == ((lo & k2) == 0)) {
-                            s_sort[lo] = y;
-                            s_sort[hi] = x;
-                        }
-                    }
-                    __syncthreads();
-                }
-            }
-        };
         if constexpr (KM > 0) {
             tk.init();
         } else {
             for (int seg = 0; seg < cnt; seg += a.sort_cap) {
                 const int m = min(a.sort_cap, cnt - seg);
-                sort_segment(seg, m);
+                sort_entries<BD>(s_sort, a.lists + off + seg, m);
                 for (int i = tid; i < m; i += BD) a.lists[off + seg + i] = s_sort[i];
                 __syncthreads();
             }
@@ -602,7 +461,7 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
         }
         for (int seg = 0; seg < cnt; seg += a.sort_cap) {
             const int m = min(a.sort_cap, cnt - seg);
-            if constexpr (KM > 0) sort_segment(seg, m);
+            if constexpr (KM > 0) sort_entries<BD>(s_sort, a.lists + off + seg, m);
             const unsigned long long *ent = (KM > 0) ? s_sort : a.lists + off + seg;
             // Chunks of BD faces, front to back: every lane walks the staged
             // faces in order.  Faces are culled 32 at a time for the whole

@@ -33,7 +33,12 @@ BLEND_RGB = 1
 
 EXPORTED = ("rast_workspace_bytes", "rast_mesh_fwd", "rast_mesh_bwd", "blend_fwd", "blend_bwd",
             "rast_query_status", "rast_bin_occupancy", "rast_strerror", "rast_mesh_fwd_static",
-            "blend_rast_bwd", "rast_blend_fwd")
+            "blend_rast_bwd", "rast_blend_fwd",
+            "pts_workspace_bytes", "pts_rasterize_fwd", "pts_rasterize_bwd", "pts_composite_fwd",
+            "pts_composite_bwd", "pts_bin_occupancy")
+
+PTS_ALPHA = 0
+PTS_NORM = 1
 
 
 class rast_params(ctypes.Structure):
@@ -55,6 +60,12 @@ class MeshRastError(RuntimeError):
 
 
 _lib = None
+
+
+class pts_params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("image_size", ctypes.c_int32), ("points_per_pixel", ctypes.c_int32),
+                ("bin_size", ctypes.c_int32), ("max_points_per_bin", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("radius", ctypes.c_float), ("reserved_f", ctypes.c_float), ("max_bin_entries", ctypes.c_int64)]
 
 
 def library_path() -> str:
@@ -97,6 +108,19 @@ def load(build_if_missing: bool = False):
     L.rast_bin_occupancy.restype = ctypes.c_int
     L.rast_mesh_fwd_static.argtypes = [P, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     L.rast_mesh_fwd_static.restype = ctypes.c_int
+    Q = ctypes.POINTER(pts_params)
+    L.pts_workspace_bytes.argtypes = [Q, i64]
+    L.pts_workspace_bytes.restype = sz
+    L.pts_rasterize_fwd.argtypes = [Q, vp, i64, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.pts_rasterize_fwd.restype = ctypes.c_int
+    L.pts_rasterize_bwd.argtypes = [Q, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.pts_rasterize_bwd.restype = ctypes.c_int
+    L.pts_composite_fwd.argtypes = [Q, ctypes.c_int32, vp, vp, vp, i64, ctypes.c_int32, vp, vp]
+    L.pts_composite_fwd.restype = ctypes.c_int
+    L.pts_composite_bwd.argtypes = [Q, ctypes.c_int32, vp, vp, vp, i64, ctypes.c_int32, vp, vp, vp, vp]
+    L.pts_composite_bwd.restype = ctypes.c_int
+    L.pts_bin_occupancy.argtypes = [Q, i64, vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64), vp]
+    L.pts_bin_occupancy.restype = ctypes.c_int
     L.rast_strerror.argtypes = [ctypes.c_int]
     L.rast_strerror.restype = ctypes.c_char_p
     _lib = L
@@ -293,3 +317,74 @@ def alloc_fragments(N, S, K, device="cuda"):
             torch.empty((N, S, S, K), dtype=torch.float32, device=device),
             torch.empty((N, S, S, K, 3), dtype=torch.float32, device=device),
             torch.empty((N, S, S, K), dtype=torch.float32, device=device))
+
+
+# ---------------------------------------------------------------------------
+# point clouds (include/points.h)
+# ---------------------------------------------------------------------------
+def make_pts_params(N, image_size, K, radius, bin_size=16, max_points_per_bin=4096, max_bin_entries=0):
+    return pts_params(int(N), int(image_size), int(K), int(bin_size), int(max_points_per_bin), 0, float(radius), 0.0,
+                      int(max_bin_entries))
+
+
+def pts_workspace_bytes(p, P):
+    return int(load().pts_workspace_bytes(ctypes.byref(p), int(P)))
+
+
+def alloc_pts_workspace(p, P, device="cuda"):
+    n = pts_workspace_bytes(p, P)
+    if n == 0:
+        raise MeshRastError("pts_workspace_bytes: invalid or unsupported parameters")
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def alloc_pts_fragments(N, S, K, device="cuda"):
+    return (torch.empty((N, S, S, K), dtype=torch.int64, device=device),
+            torch.empty((N, S, S, K), dtype=torch.float32, device=device),
+            torch.empty((N, S, S, K), dtype=torch.float32, device=device))
+
+
+def pts_rasterize_fwd(p, points, first_point, num_points, cams, idx, zbuf, dists, workspace, stream=None):
+    rc = load().pts_rasterize_fwd(
+        ctypes.byref(p), _ptr(points, torch.float32, "points"), points.shape[0],
+        _ptr(first_point, torch.int64, "first_point"), _ptr(num_points, torch.int64, "num_points"),
+        _ptr(cams, torch.float32, "cams"), _ptr(idx, torch.int64, "idx"), _ptr(zbuf, torch.float32, "zbuf"),
+        _ptr(dists, torch.float32, "dists"), _ptr(workspace, None, "workspace"),
+        workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "pts_rasterize_fwd")
+
+
+def pts_rasterize_bwd(p, points, first_point, num_points, cams, idx, grad_zbuf, grad_dists, grad_points, workspace,
+                      stream=None):
+    rc = load().pts_rasterize_bwd(
+        ctypes.byref(p), _ptr(points, torch.float32, "points"), points.shape[0],
+        _ptr(first_point, torch.int64, "first_point"), _ptr(num_points, torch.int64, "num_points"),
+        _ptr(cams, torch.float32, "cams"), _ptr(idx, torch.int64, "idx"), _ptr(grad_zbuf, torch.float32, "grad_zbuf"),
+        _ptr(grad_dists, torch.float32, "grad_dists"), _ptr(grad_points, torch.float32, "grad_points"),
+        _ptr(workspace, None, "workspace"), workspace.numel() * workspace.element_size(), _stream(stream))
+    _check(rc, "pts_rasterize_bwd")
+
+
+def pts_composite_fwd(p, mode, idx, dists, features, image, stream=None):
+    rc = load().pts_composite_fwd(ctypes.byref(p), int(mode), _ptr(idx, torch.int64, "idx"),
+                                  _ptr(dists, torch.float32, "dists"), _ptr(features, torch.float32, "features"),
+                                  features.shape[0], features.shape[1], _ptr(image, torch.float32, "image"),
+                                  _stream(stream))
+    _check(rc, "pts_composite_fwd")
+
+
+def pts_composite_bwd(p, mode, idx, dists, features, grad_image, grad_dists, grad_features, stream=None):
+    rc = load().pts_composite_bwd(ctypes.byref(p), int(mode), _ptr(idx, torch.int64, "idx"),
+                                  _ptr(dists, torch.float32, "dists"), _ptr(features, torch.float32, "features"),
+                                  features.shape[0], features.shape[1], _ptr(grad_image, torch.float32, "grad_image"),
+                                  _ptr(grad_dists, torch.float32, "grad_dists"),
+                                  _ptr(grad_features, torch.float32, "grad_features"), _stream(stream))
+    _check(rc, "pts_composite_bwd")
+
+
+def pts_bin_occupancy(p, P, workspace, stream=None):
+    mc = ctypes.c_int32(0)
+    tot = ctypes.c_int64(0)
+    _check(load().pts_bin_occupancy(ctypes.byref(p), int(P), _ptr(workspace, None, "workspace"), ctypes.byref(mc),
+                                    ctypes.byref(tot), _stream(stream)), "pts_bin_occupancy")
+    return int(mc.value), int(tot.value)

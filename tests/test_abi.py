@@ -69,6 +69,8 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(ops.rast_params) == 48
     assert ops.rast_params.max_bin_entries.offset == 40
     assert ctypes.sizeof(ops.blend_params) == 40
+    assert ctypes.sizeof(ops.pts_params) == 40
+    assert ops.pts_params.max_bin_entries.offset == 32
 
 
 def test_autotune_capacities_have_headroom():
