@@ -48,6 +48,11 @@ WORKLOADS = {
                          "blur=ln(1/1e-4-1)*1e-4, soft silhouette, fwd+bwd to verts"),
     "4": (4, "", "1 icosphere level 6 (81,920 faces) seen by 20 cameras (shared vertices), 512x512, K=50, "
                  "blur=ln(1/1e-4-1)*1e-4, soft silhouette, fwd+bwd to verts"),
+    "points": (None, "alpha", "point clouds: 8 x 200,000 points sampled from displaced level-4 spheres, 256x256, "
+                              "K=50, splat radius 0.01 NDC, Alpha-composited silhouettes, fwd+bwd to points"),
+    "points_norm": (None, "norm", "point clouds: 8 x 200,000 points sampled from displaced level-4 spheres, "
+                                  "256x256, K=50, splat radius 0.01 NDC, Norm-composited silhouettes, fwd+bwd to "
+                                  "points"),
 }
 KERNELS_PER_STEP = {"fwd": 4, "bwd": 2}
 # DRAM bytes (read + write) per launch of a stage's main kernel, keyed by
@@ -528,6 +533,248 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+class PointPipeline:
+    """Static buffers + one CUDA graph per C-ABI call of the point renderer step:
+    rasterize, composite, composite adjoint, rasterizer adjoint."""
+
+    def __init__(self, w, bin_size, max_per_bin, max_entries, device):
+        import torch
+        from paper_2007_08501_gb300 import ops
+        self.torch, self.ops = torch, ops
+        b = w.batch
+        T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        self.points, self.first, self.num, self.cams = T(b.points), T(b.first_point), T(b.num_points), T(b.cams)
+        self.feats = T(b.features)
+        self.mode = w.mode
+        self.dev = device
+        N, S, K = b.N, w.image_size, w.K
+        self.p = ops.make_pts_params(N, S, K, w.radius, bin_size, max_per_bin, max_entries)
+        self.ws = ops.alloc_pts_workspace(self.p, b.P, device)
+        self.frag = ops.alloc_pts_fragments(N, S, K, device)
+        self.img = torch.empty((N, S, S, b.features.shape[1]), device=device)
+        rng = np.random.default_rng(w.grad_seed)
+        self.gimg = T(rng.normal(size=(N, S, S, b.features.shape[1])).astype(np.float32))
+        self.gd = torch.empty_like(self.frag[2])
+        self.gf = torch.empty_like(self.feats)
+        self.gp = torch.empty_like(self.points)
+        self.graphs = None
+
+    def stages(self):
+        ops = self.ops
+        idx, zb, di = self.frag
+        return [
+            ("rast_fwd", lambda: ops.pts_rasterize_fwd(self.p, self.points, self.first, self.num, self.cams, idx, zb,
+                                                       di, self.ws)),
+            ("composite_fwd", lambda: ops.pts_composite_fwd(self.p, self.mode, idx, di, self.feats, self.img)),
+            ("composite_bwd", lambda: ops.pts_composite_bwd(self.p, self.mode, idx, di, self.feats, self.gimg,
+                                                            self.gd, self.gf)),
+            ("rast_bwd", lambda: ops.pts_rasterize_bwd(self.p, self.points, self.first, self.num, self.cams, idx,
+                                                       None, self.gd, self.gp, self.ws)),
+        ]
+
+    run_eager = Pipeline.run_eager
+    capture = Pipeline.capture
+
+    def status(self):
+        return self.ops.rast_query_status(self.ws)
+
+
+def point_bytes(w):
+    b = w.batch
+    N, S, K, D = b.N, w.image_size, w.K, b.features.shape[1]
+    slots, pix, P = N * S * S * K, N * S * S, b.P
+    return {"rast_fwd": 12 * P + 16 * slots,                       # points in, idx + zbuf + dists out
+            "composite_fwd": 12 * slots + 4 * D * pix,             # idx + dists in, image out
+            "composite_bwd": 12 * slots + 4 * D * pix + 4 * slots + 4 * D * P,
+            "rast_bwd": 12 * P + 12 * slots + 12 * P}              # idx + grad dists in, grad points out
+
+
+def point_cpu_baseline(w, target_s=15.0):
+    from oracle import points as op
+    from paper_2007_08501_gb300 import workloads
+    c = op.Clouds.from_batch(w.batch)
+    r = float(np.float32(w.radius))
+    S, K = w.image_size, w.K
+    rng = np.random.default_rng(w.grad_seed)
+
+    def run(per_image, seed):
+        px = workloads.sample_pixels(w.batch.N, S, per_image, seed)
+        t0 = time.perf_counter()
+        idx, zb, di = op.rasterize(c, S, K, r, pixels=px)
+        g = rng.normal(size=(px.shape[0], w.batch.features.shape[1]))
+        op.composite_fwd(idx, di, w.batch.features, r, w.mode)
+        gd, _ = op.composite_bwd(idx, di, w.batch.features, r, g, w.mode)
+        op.rast_bwd(c, S, K, idx, None, gd, pixels=px)
+        return px.shape[0], time.perf_counter() - t0
+
+    n0, t0 = run(4, 11)
+    per_image = int(max(4, min(S * S, 4 * target_s / max(t0, 1e-3))))
+    n, t = run(per_image, 12)
+    return {"value": n * K / t / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d pixels (%d per image, seeded) through the FP64 point oracle (every point of the cloud "
+                      "per pixel + compositing fwd/bwd + adjoint), %.1f s" % (n, per_image, t)}
+
+
+def run_points(args):
+    import torch
+    from paper_2007_08501_gb300 import ops, workloads
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    ops.load()
+    _, variant, wdesc = WORKLOADS[args.workload]
+    w = workloads.point_workload(ops.PTS_ALPHA if variant == "alpha" else ops.PTS_NORM)
+    b = w.batch
+    slots = b.N * w.image_size * w.image_size * w.K
+    # bin size and capacities: one generous probe run per candidate bin size, then
+    # a few timed forwards with the sized capacities (outside the timed region)
+    best = None
+    for bs in ((args.bin_size,) if args.bin_size else (8, 16)):
+        probe = PointPipeline(w, bs, 1 << 16, 0, dev)
+        probe.stages()[0][1]()
+        mc_, tot_ = ops.pts_bin_occupancy(probe.p, b.P, probe.ws)
+        del probe
+        per_bin_ = max(64, int(np.ceil(mc_ * 1.25 / 64.0)) * 64)
+        entries_ = max(1024, int(np.ceil(tot_ * 1.25)))
+        trial = PointPipeline(w, bs, per_bin_, entries_, dev)
+        fwd = trial.stages()[0][1]
+        ts = []
+        for i in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fwd()
+            e1.record()
+            e1.synchronize()
+            if i >= 2:
+                ts.append(e0.elapsed_time(e1))
+        del trial
+        if best is None or statistics.median(ts) < best[0]:
+            best = (statistics.median(ts), bs, per_bin_, entries_, mc_, tot_)
+    _, bin_size, per_bin, entries, mc, tot = best
+    pipe = PointPipeline(w, bin_size, per_bin, entries, dev)
+    pipe.run_eager()
+    torch.cuda.synchronize()
+    st = pipe.status()
+    if st != 0:
+        raise RuntimeError("device status %d after the first step" % st)
+    pipe.capture()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    clocks = ClockSampler()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    per_step = timed_steps(pipe, args.steps, args.warmup, flush, use_graph=True)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(sum(s.values()) for s in per_step)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / args.steps
+    value = world * slots / (ms / 1e3) / 1e6
+    stages = {k: statistics.mean(s[k] for s in per_step) for k in per_step[0]}
+    dom = max(stages, key=stages.get)
+    alg = point_bytes(w)
+    peak, peak_kind = _peaks()
+    achieved = alg[dom] / (stages[dom] / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "algorithmic_bytes": alg[dom], "kernel": dom,
+                "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
+                else "fallback 6.8 TB/s"}
+    # end to end with host buffers
+    pin = lambda t: t.cpu().pin_memory()
+    h_in = [(pipe.points, pin(pipe.points)), (pipe.first, pin(pipe.first)), (pipe.num, pin(pipe.num)),
+            (pipe.cams, pin(pipe.cams)), (pipe.feats, pin(pipe.feats)), (pipe.gimg, pin(pipe.gimg))]
+    h_out = [(pipe.img, torch.empty_like(pipe.img, device="cpu").pin_memory()),
+             (pipe.gp, torch.empty_like(pipe.gp, device="cpu").pin_memory())]
+    e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for d_, h in h_in:
+            d_.copy_(h, non_blocking=True)
+        for _, g in pipe.graphs:
+            g.replay()
+        for d_, h in h_out:
+            h.copy_(d_, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        if i >= args.warmup:
+            e_ms.append(e0.elapsed_time(e1))
+    e2e_ms = statistics.mean(e_ms)
+    e2e = {"value": round(world * slots / (e2e_ms / 1e3) / 1e6, 1), "unit": UNIT, "ms_per_step": round(e2e_ms, 4),
+           "h2d_bytes_per_step": sum(h.numel() * h.element_size() for _, h in h_in),
+           "d2h_bytes_per_step": sum(h.numel() * h.element_size() for _, h in h_out)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = point_cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wdesc, "N": b.N, "image_size": w.image_size, "K": w.K, "points": b.P,
+                       "slots": slots, "radius": w.radius, "bin_size": bin_size, "max_points_per_bin": per_bin,
+                       "max_bin_entries": entries, "graph": "one CUDA graph per C-ABI call",
+                       "l2": "flushed between steps (256 MiB write), outside the timed events",
+                       "bin_occupancy": {"max_points_in_a_bin": mc, "total_entries": tot},
+                       "parallelism": "replicas x%d" % world},
+            "roofline": roofline, "stages_ms": {k: round(v, 4) for k, v in stages.items()},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 8 * args.steps, "clocks": clk, "status": st,
+            "paper_context": {"ms_per_step": 75.0, "hardware": "V100", "what": "8 clouds x 200k points, 256x256, "
+                              "K=50, fwd+bwd, ShapeNet samples (radius not stated)"}}), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference_points(args, variant, wdesc):
+    """The FP64 point oracle on host cores, a bounded pixel sample per step."""
+    from oracle import points as op
+    from paper_2007_08501_gb300 import workloads
+    w = workloads.point_workload(0 if variant == "alpha" else 1)
+    c = op.Clouds.from_batch(w.batch)
+    r = float(np.float32(w.radius))
+    S, K = w.image_size, w.K
+    per_image = 4
+    rng = np.random.default_rng(w.grad_seed)
+
+    def step(seed):
+        px = workloads.sample_pixels(w.batch.N, S, per_image, seed)
+        idx, zb, di = op.rasterize(c, S, K, r, pixels=px)
+        op.composite_fwd(idx, di, w.batch.features, r, w.mode)
+        gd, _ = op.composite_bwd(idx, di, w.batch.features, r, rng.normal(size=(px.shape[0], 1)), w.mode)
+        op.rast_bwd(c, S, K, idx, None, gd, pixels=px)
+        return px.shape[0]
+
+    for i in range(args.warmup):
+        step(100 + i)
+    t0 = time.perf_counter()
+    n = sum(step(1000 + i) for i in range(args.steps))
+    t = time.perf_counter() - t0
+    value = n * K / t / 1e6
+    sample = "%d pixels per step (%d per image, seeded), FP64 point oracle: rasterize + composite fwd/bwd + " \
+             "adjoint" % (per_image * w.batch.N, per_image)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": int(os.environ.get(
+            "WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "config": {"workload": wdesc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+
+
 def run_reference(args):
     """The FP64 CPU oracle, timed on host cores on a bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -537,6 +784,8 @@ def run_reference(args):
     from paper_2007_08501_gb300 import workloads
     oracle.build()
     widx, wvar, wdesc = WORKLOADS[args.workload]
+    if widx is None:
+        return run_reference_points(args, wvar, wdesc)
     w = workloads.workload(widx, wvar)
     m = oracle.Mesh.from_batch(w.batch)
     blur = float(np.float32(w.blur_radius))
@@ -578,5 +827,7 @@ if __name__ == "__main__":
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload.startswith("points"):
+        run_points(a)
     else:
         run_ours(a)

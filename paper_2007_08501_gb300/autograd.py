@@ -189,3 +189,60 @@ def render_meshes(verts, faces, first_face, num_faces, cams, raster: RasterSetti
         colors = torch.zeros(0, 3, device=verts.device)
     return _Render.apply(verts.contiguous(), colors.contiguous(), faces.contiguous(), first_face.contiguous(),
                          num_faces.contiguous(), cams.contiguous(), raster, blend, ws)
+
+
+# ---------------------------------------------------------------------------
+# point clouds (Section 3.2, differentiable point cloud renderer)
+# ---------------------------------------------------------------------------
+@dataclass
+class PointSettings:
+    image_size: int
+    points_per_pixel: int = 8
+    radius: float = 0.01             # NDC units
+    bin_size: int = 16               # 0: plain per-image form
+    max_points_per_bin: int = 8192
+    max_bin_entries: int = 0
+    mode: int = ops.PTS_ALPHA        # or ops.PTS_NORM
+
+    def params(self, N):
+        return ops.make_pts_params(N, self.image_size, self.points_per_pixel, self.radius, self.bin_size,
+                                   self.max_points_per_bin, self.max_bin_entries)
+
+
+class _RenderPoints(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, points, features, first_point, num_points, cams, settings, ws):
+        N = first_point.shape[0]
+        S, K = settings.image_size, settings.points_per_pixel
+        p = settings.params(N)
+        n = ops.pts_workspace_bytes(p, points.shape[0])
+        if ws.buf is None or ws.buf.numel() < n:
+            ws.buf = torch.empty(n, dtype=torch.uint8, device=points.device)
+        idx, zbuf, dists = ops.alloc_pts_fragments(N, S, K, points.device)
+        ops.pts_rasterize_fwd(p, points, first_point, num_points, cams, idx, zbuf, dists, ws.buf)
+        img = torch.empty((N, S, S, features.shape[1]), dtype=torch.float32, device=points.device)
+        ops.pts_composite_fwd(p, settings.mode, idx, dists, features, img)
+        ctx.save_for_backward(points, features, first_point, num_points, cams, idx, dists)
+        ctx.settings, ctx.ws = settings, ws
+        return img
+
+    @staticmethod
+    def backward(ctx, g_img):
+        points, features, first_point, num_points, cams, idx, dists = ctx.saved_tensors
+        s = ctx.settings
+        p = s.params(first_point.shape[0])
+        gd = torch.empty_like(dists)
+        gf = torch.empty_like(features)
+        ops.pts_composite_bwd(p, s.mode, idx, dists, features, g_img.contiguous(), gd, gf)
+        gp = torch.empty_like(points)
+        ops.pts_rasterize_bwd(p, points, first_point, num_points, cams, idx, None, gd, gp, ctx.ws.buf)
+        return gp, gf, None, None, None, None, None
+
+
+def render_points(points, features, first_point, num_points, cams, settings: PointSettings, ws: Workspace = None):
+    """(N, S, S, D) image of a packed batch of point clouds: K nearest splats per
+    pixel, Alpha or Norm compositing; differentiable in points and features."""
+    if ws is None:
+        ws = Workspace(points.device)
+    return _RenderPoints.apply(points.contiguous(), features.contiguous(), first_point.contiguous(),
+                               num_points.contiguous(), cams.contiguous(), settings, ws)

@@ -215,7 +215,7 @@ static int forward(const rast_params *p, const float *verts, int64_t V, const in
     ka.K = (int)K;
     ka.fl = fl;
     ka.out = out;
-    ka.sort_cap = mr::fine_sort_cap(p->max_faces_per_bin, (int)K);
+    ka.sort_cap = mr::fine_sort_cap(p->max_faces_per_bin, (int)K, p->bin_size * p->bin_size);
     std::memset(&ka.blend, 0, sizeof(ka.blend));
     if (blend && mr::fine_blends((int)K, blend->rgb != 0)) {
         ka.blend = *blend;

@@ -659,7 +659,8 @@ static void pt_fill_args(PtArgs &a, const pts_params *p, const float *points, in
     }
     a.queue = reinterpret_cast<unsigned *>(ws + 4);
     a.status = reinterpret_cast<unsigned *>(ws);
-    a.sort_cap = fine_sort_cap(p->max_points_per_bin, p->points_per_pixel);
+    a.sort_cap = fine_sort_cap(p->max_points_per_bin, p->points_per_pixel,
+                               p->bin_size > 0 ? p->bin_size * p->bin_size : 256);
 }
 
 template <int KM, int BS>

@@ -20,12 +20,18 @@ constexpr int kMaxK = 64;
 
 // Bin entries the fine pass sorts at a time: the bin capacity rounded up to a
 // power of two, at least 256 (one per thread of the largest block), at most
-// 8192 (64 KB of shared memory), at most 2048 when the per-pixel lists live in
-// shared memory too (K > 16).
-inline int fine_sort_cap(int max_faces_per_bin, int K) {
-    const int lim = K > 16 ? 2048 : 8192;
+// 8192 (64 KB of shared memory).  When the per-pixel lists live in shared
+// memory too (K > 16) the sort reuses their space, so the cap is also kept
+// within it (BD threads x K entries x 8 bytes), but never below 2048.
+inline int fine_sort_cap(int max_per_bin, int K, int BD) {
+    int lim = 8192;
+    if (K > 16) {
+        int fit = 2048;
+        while (fit * 2 <= BD * K && fit * 2 <= 8192) fit <<= 1;
+        lim = fit;
+    }
     int c = 256;
-    while (c < max_faces_per_bin && c < lim) c <<= 1;
+    while (c < max_per_bin && c < lim) c <<= 1;
     return c;
 }
 

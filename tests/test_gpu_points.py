@@ -160,3 +160,26 @@ def test_status_bits_and_empty_inputs():
     empty["first"] = torch.zeros(2, dtype=torch.int64, device="cuda")
     fr, st, _, _ = _fwd(empty, b.N, 32, 4, 0.05, 8)
     assert st == 0 and bool((fr[0] == -1).all())
+
+
+def test_render_points_autograd_equals_the_calls():
+    from paper_2007_08501_gb300 import autograd as ag
+    b = workloads.point_batch([3000, 5000], 41, level=3, D=3)
+    d = _dev(b)
+    st = ag.PointSettings(image_size=48, points_per_pixel=8, radius=0.05, bin_size=16, mode=ops.PTS_ALPHA)
+    pts = d["points"].clone().requires_grad_(True)
+    feats = d["feats"].clone().requires_grad_(True)
+    img = ag.render_points(pts, feats, d["first"], d["num"], d["cams"], st)
+    g = torch.from_numpy(np.random.default_rng(8).normal(size=tuple(img.shape)).astype(np.float32)).cuda()
+    (img * g).sum().backward()
+    (idx, zb, di), status, p, ws = _fwd(d, b.N, 48, 8, 0.05, 16)
+    assert status == 0
+    ref = torch.empty_like(img)
+    ops.pts_composite_fwd(p, ops.PTS_ALPHA, idx, di, d["feats"], ref)
+    assert torch.equal(ref, img.detach())
+    gd, gf = torch.empty_like(di), torch.empty_like(d["feats"])
+    ops.pts_composite_bwd(p, ops.PTS_ALPHA, idx, di, d["feats"], g, gd, gf)
+    gp = torch.empty_like(d["points"])
+    ops.pts_rasterize_bwd(p, d["points"], d["first"], d["num"], d["cams"], idx, None, gd, gp, ws)
+    assert torch.allclose(feats.grad, gf, rtol=1e-5, atol=1e-6)
+    assert torch.allclose(pts.grad, gp, rtol=1e-4, atol=1e-4 * gp.abs().max().item())
