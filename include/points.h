@@ -73,7 +73,9 @@ MESHRAST_API int pts_rasterize_fwd(const pts_params *p, const float *points, int
 
 /* Backward rasterization: dL/dpoints (P,3) (overwritten) from dL/dzbuf and
  * dL/ddists (either may be NULL), holding idx fixed; the distance and depth
- * of every non-empty slot are recomputed from idx and the points. */
+ * of every non-empty slot are recomputed from idx and the points (an id
+ * outside its image's range contributes nothing).  The workspace is checked
+ * as for pts_rasterize_fwd but not written. */
 MESHRAST_API int pts_rasterize_bwd(const pts_params *p, const float *points, int64_t P,
                                    const int64_t *first_point, const int64_t *num_points,
                                    const float *cams, const int64_t *idx,

@@ -16,6 +16,28 @@ __device__ __forceinline__ int find_mesh(const int64_t *first_face, int N, int64
     return ans;
 }
 
+// Image of element i of a packed batch (ranges first[n] .. first[n] + num[n]),
+// or -1.  Thread 0 looks up the block's first element once; threads whose
+// element lies in that image's range skip their own binary search.  Every
+// thread of the block must call it (it synchronises the block).
+__device__ __forceinline__ int block_find_mesh(const int64_t *first, const int64_t *num, int N, int64_t count,
+                                               int64_t i) {
+    __shared__ int s_n;
+    __shared__ long long s_lo, s_hi;
+    if (threadIdx.x == 0) {
+        const int64_t i0 = (int64_t)blockIdx.x * blockDim.x;
+        const int n0 = i0 < count ? find_mesh(first, N, i0) : -1;
+        s_n = n0;
+        s_lo = n0 >= 0 ? first[n0] : 0;
+        s_hi = n0 >= 0 ? first[n0] + num[n0] : 0;
+    }
+    __syncthreads();
+    if (i >= count) return -1;
+    if (s_n >= 0 && i >= s_lo && i < s_hi) return s_n;
+    const int n = find_mesh(first, N, i);
+    return (n >= 0 && i < first[n] + num[n]) ? n : -1;
+}
+
 // world -> view -> NDC of one corner, in double-float arithmetic
 __device__ __forceinline__ void project_corner(const float *cam, float px, float py, float pz, df &X, df &Y,
                                                df &Z) {

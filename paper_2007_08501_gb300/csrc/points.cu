@@ -79,10 +79,8 @@ __global__ void __launch_bounds__(256) k_pstage(PtArgs a, int do_count) {
     PtRec R;
     R.a = make_float4(0.f, 0.f, 0.f, 0.f);
     R.b = make_float4(__int_as_float(0x7f800000), 0.f, 0.f, 0.f);
-    int n = -1;
+    int n = block_find_mesh(a.first, a.num, a.N, a.P, i);
     if (i < a.P) {
-        n = find_mesh(a.first, a.N, i);
-        if (n >= 0 && i >= a.first[n] + a.num[n]) n = -1;
         if (n >= 0) {
             const float *cam = a.cams + 16 * n;
             const float px = a.points[3 * i], py = a.points[3 * i + 1], pz = a.points[3 * i + 2];
@@ -438,36 +436,40 @@ __global__ void __launch_bounds__(256) k_pcomp_fwd(CompArgs a) {
     for (int ch = 0; ch < a.D; ++ch) a.image[pix * a.D + ch] = acc[ch] * sc;
 }
 
-// one thread per pixel of a 16 x 16 tile; feature gradients are summed over
-// the warp's lanes holding the same point before the atomics
+// One thread per pixel of a 16 x 16 tile; feature gradients are summed over
+// the warp's lanes holding the same point before the atomics.  The forward
+// recompute keeps only the transmittance at the start of every chunk of 8
+// slots (in shared memory); the reverse pass recomputes each chunk's
+// opacities and transmittances into registers.
+constexpr int kCompChunk = 8;
+constexpr int kCompChunks = (kMaxK + kCompChunk - 1) / kCompChunk;
+
 template <int DM>
 __global__ void __launch_bounds__(256) k_pcomp_bwd(CompArgs a) {
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    __shared__ float s_T[kCompChunks][256];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
     const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
     const bool valid = row < a.S && col < a.S;
     const int64_t pix = ((int64_t)blockIdx.z * a.S + row) * a.S + col;
     float g[DM];
 #pragma unroll
     for (int ch = 0; ch < DM; ++ch) g[ch] = (valid && ch < a.D) ? a.grad_image[pix * a.D + ch] : 0.f;
-    // forward recompute: opacities and transmittances (local arrays, K <= 64);
-    // 1 - alpha = d / r^2 is taken directly (no cancellation)
-    float al[kMaxK], Tk[kMaxK];
+    // forward recompute; 1 - alpha = d / r^2 is taken directly (no cancellation)
     float T = 1.f, asum = 0.f, out[DM];
 #pragma unroll
     for (int ch = 0; ch < DM; ++ch) out[ch] = 0.f;
     for (int k = 0; valid && k < a.K; ++k) {
+        if (k % kCompChunk == 0) s_T[k / kCompChunk][tid] = T;
         const int64_t s = pix * a.K + k;
         const int i = pt_id(a, s);
-        al[k] = 0.f;
-        Tk[k] = T;
         if (i < 0) continue;
         const float q = __ldg(a.dists + s) * a.inv_r2;
-        al[k] = 1.f - q;
 #pragma unroll
         for (int ch = 0; ch < DM; ++ch)
-            if (ch < a.D) out[ch] += al[k] * __ldg(a.features + (int64_t)i * a.D + ch);
+            if (ch < a.D) out[ch] += (1.f - q) * __ldg(a.features + (int64_t)i * a.D + ch);
         T *= q;
-        asum += al[k];
+        asum += 1.f - q;
     }
     const bool norm = a.mode == PTS_COMPOSITE_NORM;
     const float inv_a = asum > 0.f ? 1.f / asum : 0.f;
@@ -486,42 +488,64 @@ __global__ void __launch_bounds__(256) k_pcomp_bwd(CompArgs a) {
         f_next[ch] = 0.f;
         if (norm) out[ch] *= inv_a;
     }
-    for (int k = a.K - 1; k >= 0; --k) {  // uniform trip count: every lane reaches the warp grouping
-        const int64_t s = pix * a.K + k;
-        const int i = valid ? pt_id(a, s) : -1;
-        float gf[DM];
-        float ga = 0.f;
+    const int nch = (a.K + kCompChunk - 1) / kCompChunk;
+    for (int c = nch - 1; c >= 0; --c) {  // uniform trip counts: every lane reaches the warp grouping
+        // this chunk's ids, 1 - alpha and transmittances, in registers
+        int ids[kCompChunk];
+        float qv[kCompChunk], Tv[kCompChunk];
+        float Tc = valid ? s_T[c][tid] : 1.f;
 #pragma unroll
-        for (int ch = 0; ch < DM; ++ch) {
-            gf[ch] = 0.f;
-            if (i < 0 || ch >= a.D) continue;
-            const float fc = __ldg(a.features + (int64_t)i * a.D + ch);
-            if (norm) {
-                gf[ch] = al[k] * inv_a * g[ch];
-                ga += g[ch] * (fc - out[ch]) * inv_a;
-            } else {
-                E[ch] = has_next ? (fc - f_next[ch]) + q_next * E[ch] : fc;
-                f_next[ch] = fc;
-                gf[ch] = al[k] * Tk[k] * g[ch];
-                ga += g[ch] * Tk[k] * E[ch];
+        for (int j = 0; j < kCompChunk; ++j) {
+            const int k = c * kCompChunk + j;
+            const int64_t s = pix * a.K + k;
+            ids[j] = (valid && k < a.K) ? pt_id(a, s) : -1;
+            qv[j] = ids[j] >= 0 ? __ldg(a.dists + s) * a.inv_r2 : 1.f;
+            Tv[j] = Tc;
+            Tc *= qv[j];
+        }
+#pragma unroll
+        for (int j = kCompChunk - 1; j >= 0; --j) {
+            const int k = c * kCompChunk + j;
+            if (k >= a.K) continue;  // uniform: K is the same for every lane
+            const int64_t s = pix * a.K + k;
+            const int i = ids[j];
+            const float al = 1.f - qv[j];
+            float gf[DM];
+            float ga = 0.f;
+#pragma unroll
+            for (int ch = 0; ch < DM; ++ch) {
+                gf[ch] = 0.f;
+                if (i < 0 || ch >= a.D) continue;
+                const float fc = __ldg(a.features + (int64_t)i * a.D + ch);
+                if (norm) {
+                    gf[ch] = al * inv_a * g[ch];
+                    ga += g[ch] * (fc - out[ch]) * inv_a;
+                } else {
+                    E[ch] = has_next ? (fc - f_next[ch]) + q_next * E[ch] : fc;
+                    f_next[ch] = fc;
+                    gf[ch] = al * Tv[j] * g[ch];
+                    ga += g[ch] * Tv[j] * E[ch];
+                }
             }
-        }
-        if (i >= 0) {
-            q_next = __ldg(a.dists + s) * a.inv_r2;  // 1 - alpha_k, exactly as in the forward
-            has_next = true;
-        }
-        if (valid) a.grad_dists[s] = (i < 0) ? 0.f : -ga * a.inv_r2;
-        const unsigned peers = __match_any_sync(0xffffffffu, i);
-        group_sum<DM>(peers, gf);
-        if (i >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+            if (i >= 0) {
+                q_next = qv[j];
+                has_next = true;
+            }
+            if (valid) a.grad_dists[s] = (i < 0) ? 0.f : -ga * a.inv_r2;
+            const unsigned peers = __match_any_sync(0xffffffffu, i);
+            group_sum<DM>(peers, gf);
+            if (i >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
 #pragma unroll
-            for (int ch = 0; ch < DM; ++ch)
-                if (ch < a.D) atomicAdd(a.grad_features + (int64_t)i * a.D + ch, gf[ch]);
+                for (int ch = 0; ch < DM; ++ch)
+                    if (ch < a.D) atomicAdd(a.grad_features + (int64_t)i * a.D + ch, gf[ch]);
+            }
         }
     }
 }
 
-// dL/d(zbuf, dists) -> dL/dpoints: d = |p - x|^2, x = f x_v / z_v, then R^T
+// dL/d(zbuf, dists) -> dL/dpoints: d = |p - x|^2, x = f x_v / z_v, then R^T.
+// The point is projected here in fp32 (its selection is fixed by idx; the
+// gradient needs no double-float positions), so no staging pass is needed.
 __global__ void __launch_bounds__(256) k_prast_bwd(PtArgs a, const float *grad_zbuf, const float *grad_dists,
                                                  float *grad_points) {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -530,34 +554,44 @@ __global__ void __launch_bounds__(256) k_prast_bwd(PtArgs a, const float *grad_z
     const bool valid = row < a.S && col < a.S;
     const PixC p = pixel_centre(row, col, a.S);
     const int64_t pix = ((int64_t)n * a.S + row) * a.S + col;
+    const float *cam = a.cams + 16 * n;
+    const int64_t lo = a.first[n], hi = lo + a.num[n];
     for (int k = 0; k < a.K; ++k) {
         const int64_t s = pix * a.K + k;
         int i = -1;
         if (valid) {
             const long long v = a.idx[s];
-            i = (v >= 0 && v < a.P) ? (int)v : -1;
+            // an id outside this image's range contributes nothing
+            i = (v >= 0 && v < a.P && v >= lo && v < hi) ? (int)v : -1;
         }
-        if (i >= 0 && a.cloud[i] != n) i = -1;  // culled or another image's point: no contribution
         float g3[3] = {0.f, 0.f, 0.f};
-        float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-        float z = 1.f;
+        float x = 0.f, y = 0.f, iz = 0.f;
         if (i >= 0) {
-            q = __ldg(reinterpret_cast<const float4 *>(a.rec + i));
-            z = __ldg(reinterpret_cast<const float *>(a.rec + i) + 4);
-            const float gd = grad_dists ? grad_dists[s] : 0.f;
-            const float gz = grad_zbuf ? grad_zbuf[s] : 0.f;
-            const float qx = __fadd_rn(__fsub_rn(p.xh, q.x), __fsub_rn(p.xl, q.z));
-            const float qy = __fadd_rn(__fsub_rn(p.yh, q.y), __fsub_rn(p.yl, q.w));
-            g3[0] = -2.f * gd * qx;  // dL/dx_ndc
-            g3[1] = -2.f * gd * qy;  // dL/dy_ndc
-            g3[2] = gz;              // dL/dz_view (direct)
+            const float d0 = __ldg(a.points + 3 * (int64_t)i) - cam[9];
+            const float d1 = __ldg(a.points + 3 * (int64_t)i + 1) - cam[10];
+            const float d2 = __ldg(a.points + 3 * (int64_t)i + 2) - cam[11];
+            const float xv = cam[0] * d0 + cam[1] * d1 + cam[2] * d2;
+            const float yv = cam[3] * d0 + cam[4] * d1 + cam[5] * d2;
+            const float zv = cam[6] * d0 + cam[7] * d1 + cam[8] * d2;
+            if (zv >= cam[13] && isfinite(zv)) {
+                iz = 1.f / zv;
+                x = cam[12] * xv * iz;
+                y = cam[12] * yv * iz;
+                const float gd = grad_dists ? grad_dists[s] : 0.f;
+                const float gz = grad_zbuf ? grad_zbuf[s] : 0.f;
+                const float qx = __fadd_rn(__fsub_rn(p.xh, x), p.xl);
+                const float qy = __fadd_rn(__fsub_rn(p.yh, y), p.yl);
+                g3[0] = -2.f * gd * qx;  // dL/dx_ndc
+                g3[1] = -2.f * gd * qy;  // dL/dy_ndc
+                g3[2] = gz;              // dL/dz_view (direct)
+            } else {
+                i = -1;                  // culled: never selected by the forward
+            }
         }
         const unsigned peers = __match_any_sync(0xffffffffu, i);
         group_sum<3>(peers, g3);
         if (i >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
-            const float *cam = a.cams + 16 * n;
-            const float fo = cam[12], iz = 1.f / z;
-            const float x = q.x + q.z, y = q.y + q.w;
+            const float fo = cam[12];
             const float gxv = g3[0] * fo * iz, gyv = g3[1] * fo * iz;
             const float gzv = g3[2] - (g3[0] * x + g3[1] * y) * iz;
             float *gp = grad_points + 3 * (int64_t)i;
@@ -815,10 +849,6 @@ int pts_rasterize_bwd(const pts_params *p, const float *points, int64_t P, const
     mr::PtArgs a;
     mr::pt_fill_args(a, p, points, P, first_point, num_points, cams, ws, L);
     a.idx = const_cast<int64_t *>(idx);
-    if (P > 0) {
-        mr::k_pstage<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(a, 0);
-        if (cudaGetLastError() != cudaSuccess) return MESHRAST_ERR_CUDA;
-    }
     const unsigned tiles = (unsigned)((p->image_size + 15) / 16);
     mr::k_prast_bwd<<<dim3(tiles, tiles, (unsigned)p->N), 256, 0, st>>>(a, grad_zbuf, grad_dists, grad_points);
     return cudaGetLastError() == cudaSuccess ? MESHRAST_OK : MESHRAST_ERR_CUDA;

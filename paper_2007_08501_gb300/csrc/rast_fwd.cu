@@ -29,7 +29,7 @@ namespace mr {
 // staging
 // ---------------------------------------------------------------------------
 // Build the record of face f; returns the mesh index or -1 when culled.
-__device__ int stage_face(const StageArgs &a, int64_t f, FaceRec &R) {
+__device__ int stage_face(const StageArgs &a, int64_t f, int n, FaceRec &R) {
     const float kInf = __int_as_float(0x7f800000);
     R.a = make_float4(0.f, 0.f, 0.f, 0.f);
     R.b = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -37,8 +37,7 @@ __device__ int stage_face(const StageArgs &a, int64_t f, FaceRec &R) {
     R.d = make_float4(0.f, 1.f, 1.f, 1.f);
     R.e = make_float4(0.f, 0.f, 0.f, 0.f);
     R.h = make_float4(0.f, 0.f, 0.f, 0.f);
-    int n = find_mesh(a.first_face, a.N, f);
-    if (n < 0 || f >= a.first_face[n] + a.num_faces[n]) return -1;
+    if (n < 0) return -1;
     unsigned bad = 0;
     int64_t vi[3];
 #pragma unroll
@@ -89,9 +88,9 @@ __device__ int stage_face(const StageArgs &a, int64_t f, FaceRec &R) {
 __global__ void __launch_bounds__(256) k_stage(StageArgs a) {
     const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     FaceRec R;
-    int n = -1;
+    int n = block_find_mesh(a.first_face, a.num_faces, a.N, a.F, f);
     if (f < a.F) {
-        n = stage_face(a, f, R);
+        n = stage_face(a, f, n, R);
         float4 *dst = reinterpret_cast<float4 *>(a.rec + f);
         dst[0] = R.a;
         dst[1] = R.b;
