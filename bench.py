@@ -48,6 +48,12 @@ WORKLOADS = {
                          "blur=ln(1/1e-4-1)*1e-4, soft silhouette, fwd+bwd to verts"),
     "4": (4, "", "1 icosphere level 6 (81,920 faces) seen by 20 cameras (shared vertices), 512x512, K=50, "
                  "blur=ln(1/1e-4-1)*1e-4, soft silhouette, fwd+bwd to verts"),
+    "1gouraud": (1, "", "8 icospheres level 4 (5,120 faces each), random cameras, 256x256, K=8, "
+                        "blur=ln(1/1e-4-1)*1e-4, Gouraud-shaded per-vertex colours (one point light) + softmax blend, "
+                        "fwd+bwd to verts, normals and colours"),
+    "1phong": (1, "", "8 icospheres level 4 (5,120 faces each), random cameras, 256x256, K=8, "
+                      "blur=ln(1/1e-4-1)*1e-4, Phong-shaded per-vertex colours (one point light) + softmax blend, "
+                      "fwd+bwd to verts, normals and colours"),
     "points": (None, "alpha", "point clouds: 8 x 200,000 points sampled from displaced level-4 spheres, 256x256, "
                               "K=50, splat radius 0.01 NDC, Alpha-composited silhouettes, fwd+bwd to points"),
     "points_norm": (None, "norm", "point clouds: 8 x 200,000 points sampled from displaced level-4 spheres, "
@@ -154,7 +160,7 @@ class ClockSampler:
 class Pipeline:
     """Static device buffers + one CUDA graph per C-ABI call."""
 
-    def __init__(self, w, bin_size, max_faces_per_bin, device, max_bin_entries=0, fused=True):
+    def __init__(self, w, bin_size, max_faces_per_bin, device, max_bin_entries=0, fused=True, shading=None):
         import torch
         from paper_2007_08501_gb300 import ops
         self.torch, self.ops = torch, ops
@@ -180,12 +186,31 @@ class Pipeline:
         self.gc = torch.empty_like(self.colors)
         self.gv = torch.empty_like(self.verts)
         self.fused = fused
+        self.shading = shading
+        if shading is not None:
+            self.normals = torch.nn.functional.normalize(self.verts, dim=1).contiguous()
+            self.sp = ops.make_shade_params((0.0, 3.0, -3.0), (0.3, 0.3, 0.3), (0.6, 0.6, 0.6), (0.3, 0.3, 0.3), 32.0,
+                                            shading, ops.SHADE_SOFTMAX)
+            self.gn = torch.empty_like(self.verts)
+            self.gvd = torch.empty_like(self.verts)
         self.graphs = None
 
     def stages(self):
         ops, p2f, zb, ba, di = (self.ops, *self.frag)
         N, S, K = self.N, self.S, self.K
         rgb = self.rgb
+        if self.shading is not None:
+            return [
+                ("rast_fwd", lambda: ops.rast_mesh_fwd(self.p, self.verts, self.faces, self.ff, self.nf, self.cams,
+                                                       p2f, zb, ba, di, self.ws)),
+                ("shade_fwd", lambda: ops.shade_fwd(self.bp, self.sp, N, S, K, p2f, zb, ba, di, self.faces,
+                                                    self.verts, self.normals, self.colors, self.cams, self.img)),
+                ("shade_bwd", lambda: ops.shade_bwd(self.bp, self.sp, N, S, K, p2f, zb, ba, di, self.faces,
+                                                    self.verts, self.normals, self.colors, self.cams, self.gimg,
+                                                    self.gz, self.gb, self.gd, self.gvd, self.gn, self.gc)),
+                ("rast_bwd", lambda: ops.rast_mesh_bwd(self.p, self.verts, self.faces, self.ff, self.nf, self.cams,
+                                                       p2f, self.gz, self.gb, self.gd, self.gv, self.ws)),
+            ]
         if self.fused:
             return [
                 ("fwd", lambda: ops.rast_blend_fwd(self.p, self.bp, self.verts, self.faces, self.ff, self.nf,
@@ -275,6 +300,8 @@ def algorithmic_bytes(w):
     return {
         "rast_fwd": mesh_in + 28 * slots,                                  # write fragments
         "fwd": mesh_in + 28 * slots + 16 * pix + rgb_extra,                # fused: fragments + rgba out
+        "shade_fwd": 28 * slots + 16 * pix + 24 * F + 36 * V,              # fragments + faces, verts, normals, colours
+        "shade_bwd": 28 * slots + 16 * pix + 20 * slots + 24 * F + 72 * V,
         "blend_fwd": 28 * slots + 16 * pix + rgb_extra,                    # read fragments, write rgba
         "blend_bwd": 28 * slots + 16 * pix + 20 * slots + rgb_extra + 12 * V,
         "rast_bwd": mesh_in + 28 * slots + 12 * V,                         # ids + grad fragments
@@ -383,8 +410,9 @@ def run_ours(args):
     tuned = tune.tune(T(b.verts), T(b.faces), T(b.first_face), T(b.num_faces), T(b.cams), w.image_size, w.K,
                       float(np.float32(w.blur_radius)), w.perspective_correct, w.clip_barycentric_coords,
                       bin_sizes=(args.bin_size,) if args.bin_size else (8, 16))
+    shading = {"1gouraud": ops.SHADE_GOURAUD, "1phong": ops.SHADE_PHONG}.get(args.workload)
     pipe = Pipeline(w, bin_size=tuned["bin_size"], max_faces_per_bin=tuned["max_faces_per_bin"], device=dev,
-                    max_bin_entries=tuned["max_bin_entries"])
+                    max_bin_entries=tuned["max_bin_entries"], shading=shading)
     pipe.run_eager()
     torch.cuda.synchronize()
     st = pipe.status()
@@ -469,7 +497,7 @@ def run_ours(args):
            "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     separate = None
-    if not args.no_separate:
+    if not args.no_separate and shading is None:
         # the same step as four C-ABI calls (rast_mesh_fwd, blend_fwd, blend_bwd, rast_mesh_bwd)
         sp = Pipeline(w, bin_size=tuned["bin_size"], max_faces_per_bin=tuned["max_faces_per_bin"], device=dev,
                       max_bin_entries=tuned["max_bin_entries"], fused=False)
@@ -518,10 +546,10 @@ def run_ours(args):
             "stages_ms": {k: round(v, 4) for k, v in stages.items()},
             "stages_hbm_frac": stage_frac,
             "cpu_baseline": cpu, "e2e": e2e,
-            "gpu_launches": sum(KERNELS_PER_STEP.values()) * args.steps,
+            "gpu_launches": (8 if shading is not None else sum(KERNELS_PER_STEP.values())) * args.steps,
             "ms_per_step_median": round(statistics.median(step_ms), 4),
             "fine_pass": {"face_pixel_tests": fine_tests,
-                          "tests_per_s": round(fine_tests / (stages["fwd"] / 1e3), 1),
+                          "tests_per_s": round(fine_tests / (stages.get("fwd", stages.get("rast_fwd")) / 1e3), 1),
                           "note": "sum over bins of (pixels in bin x faces in bin)"},
             "clocks": clk, "unfused": separate, "plain_form": plain, "fit_loop": fit_loop,
             "status": st,

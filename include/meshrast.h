@@ -230,6 +230,60 @@ MESHRAST_API int blend_rast_bwd(const rast_params *p, const blend_params *bp,
                   float *grad_verts, float *grad_vert_colors,
                   void *workspace, size_t workspace_bytes, void *stream);
 
+/* ---- lit shading (Section 3.2 "Shaders": flat, Gouraud and Phong shading
+ * with per-vertex colours, blended by hard assignment or softmax) ----------
+ * One point light and the textbook Phong reflection model, all in world
+ * space, E the camera centre of the pixel's image (cams row, entries 9..11):
+ *   m = n/|n|, l = (light - x)/|light - x|, v = (E - x)/|E - x|, c = m . l,
+ *   r = 2 c m - l, s = r . v,
+ *   phi(x, n, a) = a * (ambient + diffuse * max(c, 0))
+ *                  + specular * (c > 0 and s > 0 ? s^shininess : 0)
+ *   FLAT:    n = (P1 - P0) x (P2 - P0) (the face's winding), x = sum b_i P_i,
+ *            a = sum b_i A_i
+ *   GOURAUD: colour = sum b_i phi(P_i, N_i, A_i)
+ *   PHONG:   x = sum b_i P_i, n = sum b_i N_i, a = sum b_i A_i
+ * with P, N, A the face's vertex positions, normals and colours and b the
+ * fragment's barycentrics.  SOFTMAX blends the shaded colours with
+ * Algorithm 2 (alpha of Algorithm 1, as blend_fwd in MESHRAST_BLEND_RGB mode);
+ * HARD takes the nearest fragment's colour (bg where the pixel has none) and
+ * alpha 1 where covered. */
+#define MESHRAST_SHADE_FLAT    0
+#define MESHRAST_SHADE_GOURAUD 1
+#define MESHRAST_SHADE_PHONG   2
+#define MESHRAST_SHADE_SOFTMAX 0
+#define MESHRAST_SHADE_HARD    1
+typedef struct {
+    float light[3];               /* point light position (world) */
+    float ambient[3];
+    float diffuse[3];
+    float specular[3];
+    float shininess;              /* > 0 */
+    int32_t shading;              /* MESHRAST_SHADE_FLAT / _GOURAUD / _PHONG */
+    int32_t blend;                /* MESHRAST_SHADE_SOFTMAX / _HARD */
+    int32_t reserved;             /* must be 0 */
+} shade_params;
+
+/* Shaded image (N,S,S,4) = (r, g, b, alpha) of the Fragments (as from
+ * rast_mesh_fwd), overwritten.  bp gives sigma, gamma, znear, zfar, bg and
+ * eps (its mode is ignored).  verts, normals, vert_colors (V,3); cams (N,16).
+ * pix_to_face, dists and image must be 16-byte aligned. */
+MESHRAST_API int shade_fwd(const blend_params *bp, const shade_params *sp, int64_t N, int64_t S, int64_t K,
+              const int64_t *pix_to_face, const float *zbuf, const float *bary, const float *dists,
+              const int64_t *faces, int64_t F, const float *verts, const float *normals,
+              const float *vert_colors, int64_t V, const float *cams, float *image, void *stream);
+
+/* Adjoint of shade_fwd for upstream grad_image (N,S,S,4): grad_zbuf,
+ * grad_dists (N,S,S,K) and grad_bary (N,S,S,K,3) are overwritten (feed them
+ * to rast_mesh_bwd); grad_verts (the lighting's direct dependence on the
+ * positions, to add to rast_mesh_bwd's), grad_normals and grad_vert_colors
+ * (V,3) are overwritten. */
+MESHRAST_API int shade_bwd(const blend_params *bp, const shade_params *sp, int64_t N, int64_t S, int64_t K,
+              const int64_t *pix_to_face, const float *zbuf, const float *bary, const float *dists,
+              const int64_t *faces, int64_t F, const float *verts, const float *normals,
+              const float *vert_colors, int64_t V, const float *cams, const float *grad_image,
+              float *grad_zbuf, float *grad_bary, float *grad_dists, float *grad_verts,
+              float *grad_normals, float *grad_vert_colors, void *stream);
+
 /* Waits for `stream`, then copies the workspace status word to *status
  * (host memory).  Returns MESHRAST_ERR_CUDA if the stream failed. */
 MESHRAST_API int rast_query_status(const void *workspace, uint32_t *status, void *stream);

@@ -206,13 +206,32 @@ int ors_shade_fwd(int64_t npix, int64_t K, const int64_t *image, const int64_t *
 /* Adjoint of ors_shade_fwd for grad_rgba (npix, 4).  grad_zbuf, grad_dists
  * (npix, K) and grad_bary (npix, K, 3) are overwritten; grad_verts (the
  * direct dependence of the lighting on positions), grad_normals and
- * grad_colors (V, 3) are accumulated (the caller zeroes them). */
+ * grad_colors (V, 3) are accumulated (the caller zeroes them).  abs_vnc (may
+ * be NULL; 3 x V x 3: verts, normals, colours) accumulates the magnitudes of
+ * the per-slot contributions to those sums. */
+static void ors_scatter(const int64_t *fv, const double *gP, const double *gN, const double *gA, double *grad_verts,
+                        double *grad_normals, double *grad_colors, double *abs_vnc, int64_t V) {
+    for (int i = 0; i < 3; i++) {
+        const int64_t vi = fv[i];
+        for (int j = 0; j < 3; j++) {
+            grad_verts[3 * vi + j] += gP[3 * i + j];
+            grad_normals[3 * vi + j] += gN[3 * i + j];
+            grad_colors[3 * vi + j] += gA[3 * i + j];
+            if (abs_vnc) {
+                abs_vnc[3 * vi + j] += fabs(gP[3 * i + j]);
+                abs_vnc[3 * V + 3 * vi + j] += fabs(gN[3 * i + j]);
+                abs_vnc[6 * V + 3 * vi + j] += fabs(gA[3 * i + j]);
+            }
+        }
+    }
+}
+
 int ors_shade_bwd(int64_t npix, int64_t K, const int64_t *image, const int64_t *p2f, const double *zbuf,
                   const double *bary, const double *dists, const int64_t *faces, const double *verts,
                   const double *normals, const double *colors, const double *cams, const double *light,
                   const double *blend, int shading, int blend_mode, const double *grad_rgba, double *grad_zbuf,
                   double *grad_bary, double *grad_dists, double *grad_verts, double *grad_normals,
-                  double *grad_colors) {
+                  double *grad_colors, double *abs_vnc, int64_t V) {
     ors_light Lt;
     ors_unpack(light, &Lt);
     const double sigma = blend[0], gamma = blend[1], znear = blend[2], zfar = blend[3], eps = blend[4];
@@ -232,14 +251,7 @@ int ors_shade_bwd(int64_t npix, int64_t K, const int64_t *image, const int64_t *
             double c[3], gP[9] = {0}, gN[9] = {0}, gA[9] = {0};
             ors_slot_colour(shading, &Lt, E, verts, normals, colors, faces + 3 * f, bary + 3 * p * K, c, g,
                             grad_bary + 3 * p * K, gP, gN, gA);
-            for (int i = 0; i < 3; i++) {
-                const int64_t vi = faces[3 * f + i];
-                for (int j = 0; j < 3; j++) {
-                    grad_verts[3 * vi + j] += gP[3 * i + j];
-                    grad_normals[3 * vi + j] += gN[3 * i + j];
-                    grad_colors[3 * vi + j] += gA[3 * i + j];
-                }
-            }
+            ors_scatter(faces + 3 * f, gP, gN, gA, grad_verts, grad_normals, grad_colors, abs_vnc, V);
             continue;
         }
         double keep = 1.0, zmax = eps;
@@ -283,15 +295,72 @@ int ors_shade_bwd(int64_t npix, int64_t K, const int64_t *image, const int64_t *
             double c[3], gP[9] = {0}, gN[9] = {0}, gA[9] = {0};
             ors_slot_colour(shading, &Lt, E, verts, normals, colors, faces + 3 * f, bary + 3 * s, c, gc_all + 3 * k,
                             grad_bary + 3 * s, gP, gN, gA);
-            for (int i = 0; i < 3; i++) {
-                const int64_t vi = faces[3 * f + i];
-                for (int j = 0; j < 3; j++) {
-                    grad_verts[3 * vi + j] += gP[3 * i + j];
-                    grad_normals[3 * vi + j] += gN[3 * i + j];
-                    grad_colors[3 * vi + j] += gA[3 * i + j];
-                }
-            }
+            ors_scatter(faces + 3 * f, gP, gN, gA, grad_verts, grad_normals, grad_colors, abs_vnc, V);
         }
+    }
+    return 0;
+}
+
+/* Kink margins of the reflection model: for each pixel, the smallest of |c|
+ * (the diffuse and specular terms switch on at c = 0) and, where c > 0, |s|
+ * (the specular term switches on at s = 0), over every evaluation of phi the
+ * pixel's blend uses (one per slot, three per slot for Gouraud; slot 0 only
+ * for the hard blend).  Gradients are discontinuous there. */
+static double ors_phi_margin(const ors_light *Lt, const double *E, const double *x, const double *n) {
+    double u[3], w[3], m[3], l[3], v[3];
+    for (int j = 0; j < 3; j++) { u[j] = Lt->L[j] - x[j]; w[j] = E[j] - x[j]; }
+    const double lu = sqrt(dot3(u, u)), lw = sqrt(dot3(w, w)), nn = sqrt(dot3(n, n));
+    for (int j = 0; j < 3; j++) { l[j] = u[j] / lu; v[j] = w[j] / lw; m[j] = n[j] / nn; }
+    const double c = dot3(m, l);
+    double r[3];
+    for (int j = 0; j < 3; j++) r[j] = 2.0 * c * m[j] - l[j];
+    const double sv = dot3(r, v);
+    double mg = fabs(c);
+    if (c > 0.0 && fabs(sv) < mg) mg = fabs(sv);
+    return mg;
+}
+
+int ors_shade_margins(int64_t npix, int64_t K, const int64_t *image, const int64_t *p2f, const double *bary,
+                      const int64_t *faces, const double *verts, const double *normals, const double *cams,
+                      const double *light, int shading, int blend_mode, double *margin) {
+    ors_light Lt;
+    ors_unpack(light, &Lt);
+    for (int64_t p = 0; p < npix; p++) {
+        const double *E = cams + 16 * image[p] + 9;
+        double mg = 1e300;
+        const int64_t kk = blend_mode == 1 ? 1 : K;
+        for (int64_t k = 0; k < kk; k++) {
+            const int64_t s = p * K + k;
+            const int64_t f = p2f[s];
+            if (f < 0) continue;
+            const int64_t *fv = faces + 3 * f;
+            const double *b = bary + 3 * s;
+            const double *P[3] = {verts + 3 * fv[0], verts + 3 * fv[1], verts + 3 * fv[2]};
+            const double *Nn[3] = {normals + 3 * fv[0], normals + 3 * fv[1], normals + 3 * fv[2]};
+            if (shading == 1) {
+                for (int i = 0; i < 3; i++) {
+                    const double m1 = ors_phi_margin(&Lt, E, P[i], Nn[i]);
+                    if (m1 < mg) mg = m1;
+                }
+                continue;
+            }
+            double x[3] = {0, 0, 0}, n[3] = {0, 0, 0};
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < 3; j++) x[j] += b[i] * P[i][j];
+            if (shading == 2) {
+                for (int i = 0; i < 3; i++)
+                    for (int j = 0; j < 3; j++) n[j] += b[i] * Nn[i][j];
+            } else {
+                double e1[3], e2[3];
+                for (int j = 0; j < 3; j++) { e1[j] = P[1][j] - P[0][j]; e2[j] = P[2][j] - P[0][j]; }
+                n[0] = e1[1] * e2[2] - e1[2] * e2[1];
+                n[1] = e1[2] * e2[0] - e1[0] * e2[2];
+                n[2] = e1[0] * e2[1] - e1[1] * e2[0];
+            }
+            const double m1 = ors_phi_margin(&Lt, E, x, n);
+            if (m1 < mg) mg = m1;
+        }
+        margin[p] = mg;
     }
     return 0;
 }

@@ -43,7 +43,9 @@ def _load():
         common = [_i64, _i64, _i64p, _i64p, _f64p, _f64p, _f64p, _i64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p,
                   _int, _int]
         L.ors_shade_fwd.argtypes = common + [_f64p]
-        L.ors_shade_bwd.argtypes = common + [_f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p]
+        L.ors_shade_bwd.argtypes = common + [_f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _i64]
+        L.ors_shade_margins.argtypes = [_i64, _i64, _i64p, _i64p, _f64p, _i64p, _f64p, _f64p, _f64p, _f64p, _int,
+                                        _int, _f64p]
         _lib = L
     return _lib
 
@@ -86,8 +88,9 @@ def shade_fwd(image, p2f, zbuf, bary, dists, faces, verts, normals, colors, cams
 
 
 def shade_bwd(image, p2f, zbuf, bary, dists, faces, verts, normals, colors, cams, light, blend, shading, grad_rgba,
-              blend_mode=SOFTMAX):
-    """(grad_zbuf, grad_bary, grad_dists, grad_verts (direct), grad_normals, grad_colors)."""
+              blend_mode=SOFTMAX, with_abs=False):
+    """(grad_zbuf, grad_bary, grad_dists, grad_verts (direct), grad_normals, grad_colors[, abs]) where abs
+    (3, V, 3) holds the magnitudes of the per-slot contributions to the last three."""
     npix, K, arrs, ptrs = _args(image, p2f, zbuf, bary, dists, faces, verts, normals, colors, cams, light, blend)
     V = arrs[6].shape[0]
     gz, gd = np.zeros((npix, K)), np.zeros((npix, K))
@@ -95,5 +98,21 @@ def shade_bwd(image, p2f, zbuf, bary, dists, faces, verts, normals, colors, cams
     gv, gn, gc = np.zeros((V, 3)), np.zeros((V, 3)), np.zeros((V, 3))
     g = _d(grad_rgba).reshape(npix, 4)
     P = lambda a: a.ctypes.data_as(_f64p)
-    _load().ors_shade_bwd(npix, K, *ptrs, shading, blend_mode, P(g), P(gz), P(gb), P(gd), P(gv), P(gn), P(gc))
-    return gz, gb, gd, gv, gn, gc
+    ab = np.zeros((3, V, 3))
+    _load().ors_shade_bwd(npix, K, *ptrs, shading, blend_mode, P(g), P(gz), P(gb), P(gd), P(gv), P(gn), P(gc), P(ab),
+                          V)
+    return (gz, gb, gd, gv, gn, gc, ab) if with_abs else (gz, gb, gd, gv, gn, gc)
+
+
+def shade_margins(image, p2f, bary, faces, verts, normals, cams, light, shading, blend_mode=SOFTMAX):
+    """Per pixel: the smallest |cos| (and |r . v| where lit) over the reflection evaluations
+    the blend uses -- the distance to a kink of the reflection model."""
+    p2f = _i(p2f)
+    K = p2f.shape[-1]
+    npix = p2f.size // K
+    arrs = [_i(image).reshape(npix), p2f.reshape(npix, K), _d(bary).reshape(npix, K, 3), _i(faces).reshape(-1, 3),
+            _d(verts).reshape(-1, 3), _d(normals).reshape(-1, 3), _d(cams).reshape(-1, 16), _d(light)]
+    ptrs = [a.ctypes.data_as(_i64p if a.dtype == np.int64 else _f64p) for a in arrs]
+    out = np.empty(npix)
+    _load().ors_shade_margins(npix, K, *ptrs, shading, blend_mode, out.ctypes.data_as(_f64p))
+    return out

@@ -246,3 +246,53 @@ def render_points(points, features, first_point, num_points, cams, settings: Poi
         ws = Workspace(points.device)
     return _RenderPoints.apply(points.contiguous(), features.contiguous(), first_point.contiguous(),
                                num_points.contiguous(), cams.contiguous(), settings, ws)
+
+
+# ---------------------------------------------------------------------------
+# lit shading (flat / Gouraud / Phong with one point light; softmax or hard)
+# ---------------------------------------------------------------------------
+@dataclass
+class ShadeSettings:
+    light: tuple = (0.0, 0.0, -3.0)      # point light position (world)
+    ambient: tuple = (0.5, 0.5, 0.5)
+    diffuse: tuple = (0.3, 0.3, 0.3)
+    specular: tuple = (0.2, 0.2, 0.2)
+    shininess: float = 64.0
+    shading: int = ops.SHADE_PHONG
+    blend: int = ops.SHADE_SOFTMAX
+
+    def params(self):
+        return ops.make_shade_params(self.light, self.ambient, self.diffuse, self.specular, self.shininess,
+                                     self.shading, self.blend)
+
+
+class _Shade(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, pix_to_face, zbuf, bary, dists, verts, normals, colors, faces, cams, bs, ss):
+        N, S, _, K = pix_to_face.shape
+        img = torch.empty((N, S, S, 4), dtype=torch.float32, device=pix_to_face.device)
+        ops.shade_fwd(bs.params(), ss.params(), N, S, K, pix_to_face, zbuf, bary, dists, faces, verts, normals,
+                      colors, cams, img)
+        ctx.save_for_backward(pix_to_face, zbuf, bary, dists, verts, normals, colors, faces, cams)
+        ctx.bs, ctx.ss = bs, ss
+        return img
+
+    @staticmethod
+    def backward(ctx, g_img):
+        pix_to_face, zbuf, bary, dists, verts, normals, colors, faces, cams = ctx.saved_tensors
+        N, S, _, K = pix_to_face.shape
+        gz, gb, gd = torch.empty_like(zbuf), torch.empty_like(bary), torch.empty_like(dists)
+        gv, gn, gc = torch.empty_like(verts), torch.empty_like(normals), torch.empty_like(colors)
+        ops.shade_bwd(ctx.bs.params(), ctx.ss.params(), N, S, K, pix_to_face, zbuf, bary, dists, faces, verts,
+                      normals, colors, cams, g_img.contiguous(), gz, gb, gd, gv, gn, gc)
+        return None, gz, gb, gd, gv, gn, gc, None, None, None, None
+
+
+def shade(pix_to_face, zbuf, bary, dists, verts, normals, colors, faces, cams, blend: BlendSettings = None,
+          shading: ShadeSettings = None):
+    """RGBA (N, S, S, 4) of lit fragments: flat / Gouraud / Phong reflection of one point
+    light, blended by softmax (Algorithm 2) or hard assignment.  Differentiable in the
+    fragments (chain into rasterize_meshes), positions, normals and colours."""
+    return _Shade.apply(pix_to_face, zbuf, bary, dists, verts.contiguous(), normals.contiguous(),
+                        colors.contiguous(), faces.contiguous(), cams.contiguous(), blend or BlendSettings(),
+                        shading or ShadeSettings())

@@ -35,7 +35,10 @@ EXPORTED = ("rast_workspace_bytes", "rast_mesh_fwd", "rast_mesh_bwd", "blend_fwd
             "rast_query_status", "rast_bin_occupancy", "rast_strerror", "rast_mesh_fwd_static",
             "blend_rast_bwd", "rast_blend_fwd",
             "pts_workspace_bytes", "pts_rasterize_fwd", "pts_rasterize_bwd", "pts_composite_fwd",
-            "pts_composite_bwd", "pts_bin_occupancy")
+            "pts_composite_bwd", "pts_bin_occupancy", "shade_fwd", "shade_bwd")
+
+SHADE_FLAT, SHADE_GOURAUD, SHADE_PHONG = 0, 1, 2
+SHADE_SOFTMAX, SHADE_HARD = 0, 1
 
 PTS_ALPHA = 0
 PTS_NORM = 1
@@ -60,6 +63,12 @@ class MeshRastError(RuntimeError):
 
 
 _lib = None
+
+
+class shade_params(ctypes.Structure):
+    _fields_ = [("light", ctypes.c_float * 3), ("ambient", ctypes.c_float * 3), ("diffuse", ctypes.c_float * 3),
+                ("specular", ctypes.c_float * 3), ("shininess", ctypes.c_float), ("shading", ctypes.c_int32),
+                ("blend", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class pts_params(ctypes.Structure):
@@ -108,6 +117,12 @@ def load(build_if_missing: bool = False):
     L.rast_bin_occupancy.restype = ctypes.c_int
     L.rast_mesh_fwd_static.argtypes = [P, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     L.rast_mesh_fwd_static.restype = ctypes.c_int
+    H = ctypes.POINTER(shade_params)
+    L.shade_fwd.argtypes = [B, H, i64, i64, i64, vp, vp, vp, vp, vp, i64, vp, vp, vp, i64, vp, vp, vp]
+    L.shade_fwd.restype = ctypes.c_int
+    L.shade_bwd.argtypes = [B, H, i64, i64, i64, vp, vp, vp, vp, vp, i64, vp, vp, vp, i64, vp, vp, vp, vp, vp, vp, vp,
+                            vp, vp]
+    L.shade_bwd.restype = ctypes.c_int
     Q = ctypes.POINTER(pts_params)
     L.pts_workspace_bytes.argtypes = [Q, i64]
     L.pts_workspace_bytes.restype = sz
@@ -388,3 +403,41 @@ def pts_bin_occupancy(p, P, workspace, stream=None):
     _check(load().pts_bin_occupancy(ctypes.byref(p), int(P), _ptr(workspace, None, "workspace"), ctypes.byref(mc),
                                     ctypes.byref(tot), _stream(stream)), "pts_bin_occupancy")
     return int(mc.value), int(tot.value)
+
+
+# ---------------------------------------------------------------------------
+# lit shading (flat / Gouraud / Phong, softmax or hard blend)
+# ---------------------------------------------------------------------------
+def make_shade_params(light, ambient=(0.5, 0.5, 0.5), diffuse=(0.3, 0.3, 0.3), specular=(0.2, 0.2, 0.2),
+                      shininess=64.0, shading=SHADE_PHONG, blend=SHADE_SOFTMAX):
+    f3 = lambda v: (ctypes.c_float * 3)(*[float(x) for x in v])
+    return shade_params(f3(light), f3(ambient), f3(diffuse), f3(specular), float(shininess), int(shading), int(blend),
+                        0)
+
+
+def shade_fwd(bp, sp, N, S, K, pix_to_face, zbuf, bary, dists, faces, verts, normals, vert_colors, cams, image,
+              stream=None):
+    rc = load().shade_fwd(ctypes.byref(bp), ctypes.byref(sp), int(N), int(S), int(K),
+                          _ptr(pix_to_face, torch.int64, "pix_to_face"), _ptr(zbuf, torch.float32, "zbuf"),
+                          _ptr(bary, torch.float32, "bary"), _ptr(dists, torch.float32, "dists"),
+                          _ptr(faces, torch.int64, "faces"), faces.shape[0], _ptr(verts, torch.float32, "verts"),
+                          _ptr(normals, torch.float32, "normals"), _ptr(vert_colors, torch.float32, "vert_colors"),
+                          verts.shape[0], _ptr(cams, torch.float32, "cams"), _ptr(image, torch.float32, "image"),
+                          _stream(stream))
+    _check(rc, "shade_fwd")
+
+
+def shade_bwd(bp, sp, N, S, K, pix_to_face, zbuf, bary, dists, faces, verts, normals, vert_colors, cams, grad_image,
+              grad_zbuf, grad_bary, grad_dists, grad_verts, grad_normals, grad_vert_colors, stream=None):
+    rc = load().shade_bwd(ctypes.byref(bp), ctypes.byref(sp), int(N), int(S), int(K),
+                          _ptr(pix_to_face, torch.int64, "pix_to_face"), _ptr(zbuf, torch.float32, "zbuf"),
+                          _ptr(bary, torch.float32, "bary"), _ptr(dists, torch.float32, "dists"),
+                          _ptr(faces, torch.int64, "faces"), faces.shape[0], _ptr(verts, torch.float32, "verts"),
+                          _ptr(normals, torch.float32, "normals"), _ptr(vert_colors, torch.float32, "vert_colors"),
+                          verts.shape[0], _ptr(cams, torch.float32, "cams"),
+                          _ptr(grad_image, torch.float32, "grad_image"), _ptr(grad_zbuf, torch.float32, "grad_zbuf"),
+                          _ptr(grad_bary, torch.float32, "grad_bary"), _ptr(grad_dists, torch.float32, "grad_dists"),
+                          _ptr(grad_verts, torch.float32, "grad_verts"),
+                          _ptr(grad_normals, torch.float32, "grad_normals"),
+                          _ptr(grad_vert_colors, torch.float32, "grad_vert_colors"), _stream(stream))
+    _check(rc, "shade_bwd")

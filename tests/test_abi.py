@@ -70,6 +70,7 @@ def test_struct_layouts_match_header():
     assert ops.rast_params.max_bin_entries.offset == 40
     assert ctypes.sizeof(ops.blend_params) == 40
     assert ctypes.sizeof(ops.pts_params) == 40
+    assert ctypes.sizeof(ops.shade_params) == 64
     assert ops.pts_params.max_bin_entries.offset == 32
 
 
