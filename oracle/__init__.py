@@ -30,15 +30,17 @@ _int = ctypes.c_int
 
 def build(force: bool = False) -> str:
     """Compile ``oracle.c`` into ``liboracle.so`` next to it (gcc, no FMA contraction),
-    and the point-cloud (``points.c``) and shading (``shading.c``) oracles beside it."""
+    and the point-cloud (``points.c``), shading (``shading.c``) and nearest-neighbour
+    (``knn.c``) oracles beside it."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
                                "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
-    from . import points, shading
+    from . import knn, points, shading
     points.build(force)
     shading.build(force)
+    knn.build(force)
     return _LIB_PATH
 
 
