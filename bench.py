@@ -56,6 +56,12 @@ WORKLOADS = {
                       "fwd+bwd to verts, normals and colours"),
     "points": (None, "alpha", "point clouds: 8 x 200,000 points sampled from displaced level-4 spheres, 256x256, "
                               "K=50, splat radius 0.01 NDC, Alpha-composited silhouettes, fwd+bwd to points"),
+    "knn": (None, "knn", "exact KNN, 32 pairs of point clouds sampled from displaced level-4 spheres, |P| = |Q| = "
+                         "50,000, D = 3, K = 8, forward"),
+    "knn_het": (None, "knn_het", "exact KNN, 32 pairs of point clouds sampled from displaced level-4 spheres, |P|, |Q| "
+                                 "uniform in [10,000, 90,000], D = 3, K = 8, forward"),
+    "chamfer": (None, "chamfer", "Chamfer loss, 32 pairs of point clouds sampled from displaced level-4 spheres, "
+                                 "|P| = 1,000, |Q| = 50,000, D = 3, forward + backward"),
     "points_norm": (None, "norm", "point clouds: 8 x 200,000 points sampled from displaced level-4 spheres, "
                                   "256x256, K=50, splat radius 0.01 NDC, Norm-composited silhouettes, fwd+bwd to "
                                   "points"),
@@ -812,6 +818,8 @@ def run_reference(args):
     from paper_2007_08501_gb300 import workloads
     oracle.build()
     widx, wvar, wdesc = WORKLOADS[args.workload]
+    if args.workload in KNN_WORKLOADS:
+        return run_reference_knn(args, wdesc)
     if widx is None:
         return run_reference_points(args, wvar, wdesc)
     w = workloads.workload(widx, wvar)
@@ -851,10 +859,229 @@ def run_reference(args):
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# exact KNN and the Chamfer loss (Section 3.1 operators)
+# ---------------------------------------------------------------------------
+KNN_WORKLOADS = ("knn", "knn_het", "chamfer")
+KNN_METRIC = "exact KNN / Chamfer ms per batch & candidate distances per second (Gpair/s), % FP32 ALU roofline"
+KNN_UNIT = "Gpair/s"
+# FP32 lane operations one candidate distance needs at least: D subtractions,
+# one multiply and D - 1 fused multiply-adds (D = 3)
+KNN_OPS_PER_PAIR = 6
+FP32_LANE_OPS_PEAK = 152 * 128 * 2.07e9   # SMs x FP32 lanes x max SM clock (derived, not measured)
+
+
+class KnnPipeline:
+    """Static buffers + one CUDA graph per C-ABI call: knn_points, or
+    chamfer_fwd then chamfer_bwd."""
+
+    def __init__(self, w, device):
+        import torch
+        from paper_2007_08501_gb300 import ops
+        self.torch, self.ops = torch, ops
+        c = w.pairs
+        T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(device)
+        self.p, self.q = T(c.p), T(c.q)
+        self.f1, self.l1, self.f2, self.l2 = T(c.first1), T(c.len1), T(c.first2), T(c.len2)
+        self.K, self.chamfer = w.K, w.chamfer
+        self.dev = device
+        self.ws = ops.alloc_knn_workspace(c.N, device)
+        P1, P2 = c.p.shape[0], c.q.shape[0]
+        if self.chamfer:
+            self.idx_pq = torch.empty(P1, dtype=torch.int64, device=device)
+            self.d_pq = torch.empty(P1, device=device)
+            self.idx_qp = torch.empty(P2, dtype=torch.int64, device=device)
+            self.d_qp = torch.empty(P2, device=device)
+            self.per = torch.empty(c.N, device=device)
+            self.loss = torch.empty(1, device=device)
+            self.gl = torch.ones(1, device=device)
+            self.gp, self.gq = torch.empty_like(self.p), torch.empty_like(self.q)
+        else:
+            self.idx = torch.empty((P1, w.K), dtype=torch.int64, device=device)
+            self.dists = torch.empty((P1, w.K), device=device)
+        self.graphs = None
+
+    def stages(self):
+        ops = self.ops
+        if not self.chamfer:
+            return [("knn", lambda: ops.knn_points(self.p, self.f1, self.l1, self.q, self.f2, self.l2, self.K,
+                                                   self.idx, self.dists, self.ws))]
+        return [
+            ("chamfer_fwd", lambda: ops.chamfer_fwd(self.p, self.f1, self.l1, self.q, self.f2, self.l2, self.idx_pq,
+                                                    self.d_pq, self.idx_qp, self.d_qp, self.per, self.loss, self.ws)),
+            ("chamfer_bwd", lambda: ops.chamfer_bwd(self.p, self.f1, self.l1, self.q, self.f2, self.l2, self.idx_pq,
+                                                    self.idx_qp, self.gl, None, self.gp, self.gq)),
+        ]
+
+    run_eager = Pipeline.run_eager
+    capture = Pipeline.capture
+
+    def inputs(self):
+        return [self.p, self.f1, self.l1, self.q, self.f2, self.l2]
+
+    def outputs(self):
+        return [self.loss, self.gp, self.gq] if self.chamfer else [self.idx, self.dists]
+
+
+def knn_cpu_baseline(w, target_s=10.0, seed=17):
+    """The oracle on host cores (one core): (candidate distances per second, seconds, sample text).
+    KNN: a seeded sample of query rows per cloud, sized to take about target_s.
+    Chamfer: the whole Eq. 1 loss and gradient (KNN both ways + FP64 sums) on
+    the first cloud pairs of the batch, as many as fit in about target_s."""
+    from oracle import knn as ok
+    from paper_2007_08501_gb300 import workloads
+    c = w.pairs
+    if w.chamfer:
+        def run(npair):
+            sub = workloads.CloudPairs(c.p[:int(c.first1[npair - 1] + c.len1[npair - 1])], c.first1[:npair],
+                                       c.len1[:npair], c.q[:int(c.first2[npair - 1] + c.len2[npair - 1])],
+                                       c.first2[:npair], c.len2[:npair])
+            t0 = time.perf_counter()
+            _, _, ipq, iqp = ok.chamfer(sub.p, sub.first1, sub.len1, sub.q, sub.first2, sub.len2)
+            ok.chamfer_grad(sub.p, sub.first1, sub.len1, sub.q, sub.first2, sub.len2, ipq, iqp, np.ones(npair))
+            return workloads.pairs_per_batch(sub, both_ways=True), time.perf_counter() - t0
+        n, t = run(1)
+        k = int(max(1, min(c.N, target_s / max(t, 1e-3))))
+        n, t = run(k)
+        return n / t, t, "the first %d of %d cloud pairs through the oracle's Chamfer loss and gradient (KNN " \
+                         "both ways in C, sums in FP64), %.1f s" % (k, c.N, t)
+    rng = np.random.default_rng(seed)
+
+    def run(per_cloud):
+        rows = np.concatenate([f + rng.choice(n, size=min(per_cloud, n), replace=False)
+                               for f, n in zip(c.first1, c.len1) if n > 0])
+        npairs = int(np.sum(c.len2 * np.minimum(per_cloud, c.len1)))
+        t0 = time.perf_counter()
+        ok.knn(c.p, c.first1, c.len1, c.q, c.first2, c.len2, w.K, rows=rows)
+        return npairs, time.perf_counter() - t0, rows.size
+
+    n, t, _ = run(2)
+    per_cloud = int(max(2, 2 * target_s / max(t, 1e-3)))
+    n, t, nrows = run(per_cloud)
+    return n / t, t, "%d seeded query rows (%d per cloud) against every candidate of their cloud through the " \
+                     "oracle's KNN (K = %d), %.1f s" % (nrows, per_cloud, w.K, t)
+
+
+def run_knn(args):
+    import torch
+    from paper_2007_08501_gb300 import ops, workloads
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    ops.load()
+    wdesc = WORKLOADS[args.workload][2]
+    w = workloads.knn_workload(args.workload)
+    c = w.pairs
+    pairs = workloads.pairs_per_batch(c, both_ways=w.chamfer)
+    pipe = KnnPipeline(w, dev)
+    pipe.run_eager()
+    torch.cuda.synchronize()
+    pipe.capture()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    clocks = ClockSampler()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    per_step = timed_steps(pipe, args.steps, args.warmup, flush, use_graph=True)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(sum(s.values()) for s in per_step)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / args.steps
+    value = world * pairs / (ms / 1e3) / 1e9
+    stages = {k: statistics.mean(s[k] for s in per_step) for k in per_step[0]}
+    dom = "chamfer_fwd" if w.chamfer else "knn"
+    achieved = pairs * KNN_OPS_PER_PAIR / (stages[dom] / 1e3)
+    roofline = {"bound": "alu", "achieved": round(achieved / 1e12, 3), "peak": round(FP32_LANE_OPS_PEAK / 1e12, 2),
+                "unit": "T FP32 lane-op/s", "frac": round(achieved / FP32_LANE_OPS_PEAK, 4), "traffic": None,
+                "kernel": "k_knn (%s call)" % dom,
+                "ops_per_pair": KNN_OPS_PER_PAIR, "pairs_per_launch": pairs,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (one lane-op per lane per clock)"}
+    # end to end with host buffers: inputs in, results out, every step
+    pin = lambda t: t.cpu().pin_memory()
+    h_in = [(d_, pin(d_)) for d_ in pipe.inputs()]
+    h_out = [(d_, torch.empty_like(d_, device="cpu").pin_memory()) for d_ in pipe.outputs()]
+    e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for d_, h in h_in:
+            d_.copy_(h, non_blocking=True)
+        for _, g in pipe.graphs:
+            g.replay()
+        for d_, h in h_out:
+            h.copy_(d_, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        if i >= args.warmup:
+            e_ms.append(e0.elapsed_time(e1))
+    e2e_ms = statistics.mean(e_ms)
+    e2e = {"value": round(world * pairs / (e2e_ms / 1e3) / 1e9, 2), "unit": KNN_UNIT, "ms_per_step": round(e2e_ms, 4),
+           "h2d_bytes_per_step": sum(h.numel() * h.element_size() for _, h in h_in),
+           "d2h_bytes_per_step": sum(h.numel() * h.element_size() for _, h in h_out)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, t, sample = knn_cpu_baseline(w)
+        cpu = {"value": round(v / 1e9, 5), "unit": KNN_UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        print(json.dumps({
+            "metric": KNN_METRIC, "value": round(value, 2), "unit": KNN_UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": wdesc, "N": c.N, "P1": int(c.p.shape[0]), "P2": int(c.q.shape[0]), "D": 3,
+                       "K": w.K, "candidate_distances_per_step": pairs, "graph": "one CUDA graph per C-ABI call",
+                       "l2": "flushed between steps (256 MiB write), outside the timed events",
+                       "parallelism": "replicas x%d" % world},
+            "roofline": roofline, "stages_ms": {k: round(v, 4) for k, v in stages.items()},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": (5 if w.chamfer else 2) * args.steps, "clocks": clk,
+            "ms_per_step_median": round(statistics.median(sum(s.values()) for s in per_step), 4)}), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_reference_knn(args, wdesc):
+    """The oracle's KNN on host cores, a bounded sample of query rows per step."""
+    from paper_2007_08501_gb300 import workloads
+    w = workloads.knn_workload(args.workload)
+    for i in range(args.warmup):
+        knn_cpu_baseline(w, 0.5, seed=100 + i)
+    n = t = 0.0
+    sample = ""
+    for i in range(args.steps):
+        v, ti, sample = knn_cpu_baseline(w, 5.0, seed=1000 + i)
+        n += v * ti
+        t += ti
+    value = n / t / 1e9
+    print(json.dumps({
+        "impl": "reference", "metric": KNN_METRIC, "value": value, "unit": KNN_UNIT,
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t / args.steps * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic", "config": {"workload": wdesc},
+        "cpu_baseline": {"value": value, "unit": KNN_UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "per step: " + sample},
+        "e2e": {"value": value, "unit": KNN_UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}), flush=True)
+
+
 if __name__ == "__main__":
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload in KNN_WORKLOADS:
+        run_knn(a)
     elif a.workload.startswith("points"):
         run_points(a)
     else:

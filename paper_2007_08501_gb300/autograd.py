@@ -9,7 +9,8 @@ differentiates through ``blend_bwd``.  ``render_meshes`` does both in one
 Function: its forward is ``rast_blend_fwd`` (the fine pass blends as it
 writes the fragments) and its backward ``blend_rast_bwd`` (the blend adjoint
 goes straight into the rasterizer adjoint without materialising fragment
-gradients).
+gradients).  ``knn_points`` and ``chamfer_distance`` (Section 3.1, Eq. 1)
+wrap the exact nearest-neighbour search on packed point-cloud batches.
 """
 from __future__ import annotations
 
@@ -296,3 +297,66 @@ def shade(pix_to_face, zbuf, bary, dists, verts, normals, colors, faces, cams, b
     return _Shade.apply(pix_to_face, zbuf, bary, dists, verts.contiguous(), normals.contiguous(),
                         colors.contiguous(), faces.contiguous(), cams.contiguous(), blend or BlendSettings(),
                         shading or ShadeSettings())
+
+
+# ---------------------------------------------------------------------------
+# exact KNN and the Chamfer loss (Section 3.1, 3D operators; Eq. 1)
+# ---------------------------------------------------------------------------
+class _KnnPoints(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, p1, p2, first1, len1, first2, len2, K):
+        idx = torch.empty((p1.shape[0], K), dtype=torch.int64, device=p1.device)
+        dists = torch.empty((p1.shape[0], K), dtype=torch.float32, device=p1.device)
+        ws = ops.alloc_knn_workspace(first1.shape[0], p1.device)
+        ops.knn_points(p1, first1, len1, p2, first2, len2, K, idx, dists, ws)
+        ctx.save_for_backward(p1, p2, idx)
+        ctx.mark_non_differentiable(idx)
+        return dists, idx
+
+    @staticmethod
+    def backward(ctx, g_dists, g_idx):
+        p1, p2, idx = ctx.saved_tensors
+        g1, g2 = torch.empty_like(p1), torch.empty_like(p2)
+        ops.knn_points_bwd(p1, p2, idx, g_dists.contiguous(), g1, g2)
+        return g1, g2, None, None, None, None, None
+
+
+def knn_points(p1, first1, len1, p2, first2, len2, K):
+    """(dists (P1, K), idx (P1, K)): the K nearest rows of p2 (same cloud) to
+    each row of p1, ascending squared distance; idx is -1 (dist +inf) past
+    the end of a small cloud.  Differentiable in p1 and p2 through dists."""
+    return _KnnPoints.apply(p1.contiguous(), p2.contiguous(), first1.contiguous(), len1.contiguous(),
+                            first2.contiguous(), len2.contiguous(), int(K))
+
+
+class _Chamfer(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, p, q, first1, len1, first2, len2):
+        dev = p.device
+        N = first1.shape[0]
+        idx_pq = torch.empty(p.shape[0], dtype=torch.int64, device=dev)
+        idx_qp = torch.empty(q.shape[0], dtype=torch.int64, device=dev)
+        d_pq = torch.empty(p.shape[0], dtype=torch.float32, device=dev)
+        d_qp = torch.empty(q.shape[0], dtype=torch.float32, device=dev)
+        per = torch.empty(N, dtype=torch.float32, device=dev)
+        loss = torch.empty((), dtype=torch.float32, device=dev)
+        ws = ops.alloc_knn_workspace(N, dev)
+        ops.chamfer_fwd(p, first1, len1, q, first2, len2, idx_pq, d_pq, idx_qp, d_qp, per, loss, ws)
+        ctx.save_for_backward(p, q, first1, len1, first2, len2, idx_pq, idx_qp)
+        return loss, per
+
+    @staticmethod
+    def backward(ctx, g_loss, g_per):
+        p, q, first1, len1, first2, len2, idx_pq, idx_qp = ctx.saved_tensors
+        gp, gq = torch.empty_like(p), torch.empty_like(q)
+        gl = None if g_loss is None else g_loss.reshape(1).contiguous()
+        gpp = None if g_per is None else g_per.contiguous()
+        ops.chamfer_bwd(p, first1, len1, q, first2, len2, idx_pq, idx_qp, gl, gpp, gp, gq)
+        return gp, gq, None, None, None, None
+
+
+def chamfer_distance(p, first1, len1, q, first2, len2):
+    """(loss, loss_per_pair): Eq. 1 for each pair of packed clouds (P_i, Q_i)
+    and the batch mean; differentiable in p and q (neighbours held fixed)."""
+    return _Chamfer.apply(p.contiguous(), q.contiguous(), first1.contiguous(), len1.contiguous(),
+                          first2.contiguous(), len2.contiguous())

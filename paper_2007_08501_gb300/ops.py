@@ -35,7 +35,8 @@ EXPORTED = ("rast_workspace_bytes", "rast_mesh_fwd", "rast_mesh_bwd", "blend_fwd
             "rast_query_status", "rast_bin_occupancy", "rast_strerror", "rast_mesh_fwd_static",
             "blend_rast_bwd", "rast_blend_fwd",
             "pts_workspace_bytes", "pts_rasterize_fwd", "pts_rasterize_bwd", "pts_composite_fwd",
-            "pts_composite_bwd", "pts_bin_occupancy", "shade_fwd", "shade_bwd")
+            "pts_composite_bwd", "pts_bin_occupancy", "shade_fwd", "shade_bwd",
+            "knn_workspace_bytes", "knn_points", "knn_points_bwd", "chamfer_fwd", "chamfer_bwd")
 
 SHADE_FLAT, SHADE_GOURAUD, SHADE_PHONG = 0, 1, 2
 SHADE_SOFTMAX, SHADE_HARD = 0, 1
@@ -138,6 +139,17 @@ def load(build_if_missing: bool = False):
     L.pts_bin_occupancy.restype = ctypes.c_int
     L.rast_strerror.argtypes = [ctypes.c_int]
     L.rast_strerror.restype = ctypes.c_char_p
+    i32 = ctypes.c_int32
+    L.knn_workspace_bytes.argtypes = [i64]
+    L.knn_workspace_bytes.restype = sz
+    L.knn_points.argtypes = [vp, i64, vp, vp, vp, i64, vp, vp, i64, i32, i32, vp, vp, vp, sz, vp]
+    L.knn_points.restype = ctypes.c_int
+    L.knn_points_bwd.argtypes = [vp, i64, vp, i64, i32, i32, vp, vp, vp, vp, vp]
+    L.knn_points_bwd.restype = ctypes.c_int
+    L.chamfer_fwd.argtypes = [vp, i64, vp, vp, vp, i64, vp, vp, i64, i32, vp, vp, vp, vp, vp, vp, vp, sz, vp]
+    L.chamfer_fwd.restype = ctypes.c_int
+    L.chamfer_bwd.argtypes = [vp, i64, vp, vp, vp, i64, vp, vp, i64, i32, vp, vp, vp, vp, vp, vp, vp]
+    L.chamfer_bwd.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -441,3 +453,70 @@ def shade_bwd(bp, sp, N, S, K, pix_to_face, zbuf, bary, dists, faces, verts, nor
                           _ptr(grad_normals, torch.float32, "grad_normals"),
                           _ptr(grad_vert_colors, torch.float32, "grad_vert_colors"), _stream(stream))
     _check(rc, "shade_bwd")
+
+
+# ---------------------------------------------------------------------------
+# exact K nearest neighbours and the Chamfer loss (packed point-cloud batches)
+# ---------------------------------------------------------------------------
+def knn_workspace_bytes(N):
+    return int(load().knn_workspace_bytes(int(N)))
+
+
+def alloc_knn_workspace(N, device="cuda"):
+    """256-byte aligned device workspace for knn_points / chamfer_fwd over N clouds."""
+    n = max(knn_workspace_bytes(N), 256)
+    return torch.empty(n // 8, dtype=torch.int64, device=device)
+
+
+def _ws(workspace):
+    return _ptr(workspace, None, "workspace"), workspace.numel() * workspace.element_size()
+
+
+def knn_points(p1, first1, len1, p2, first2, len2, K, idx, dists, workspace, stream=None):
+    """idx (P1, K) int64 and dists (P1, K) float32 are written (global rows of p2)."""
+    D = p1.shape[1]
+    if p2.shape[1] != D:
+        raise MeshRastError("p1 and p2 must have the same dimension")
+    w, wb = _ws(workspace)
+    rc = load().knn_points(_ptr(p1, torch.float32, "p1"), p1.shape[0], _ptr(first1, torch.int64, "first1"),
+                           _ptr(len1, torch.int64, "len1"), _ptr(p2, torch.float32, "p2"), p2.shape[0],
+                           _ptr(first2, torch.int64, "first2"), _ptr(len2, torch.int64, "len2"), first1.shape[0], D,
+                           int(K), _ptr(idx, torch.int64, "idx"), _ptr(dists, torch.float32, "dists"), w, wb,
+                           _stream(stream))
+    _check(rc, "knn_points")
+
+
+def knn_points_bwd(p1, p2, idx, grad_dists, grad_p1, grad_p2, stream=None):
+    rc = load().knn_points_bwd(_ptr(p1, torch.float32, "p1"), p1.shape[0], _ptr(p2, torch.float32, "p2"), p2.shape[0],
+                               p1.shape[1], idx.shape[1], _ptr(idx, torch.int64, "idx"),
+                               _ptr(grad_dists, torch.float32, "grad_dists"), _ptr(grad_p1, torch.float32, "grad_p1"),
+                               _ptr(grad_p2, torch.float32, "grad_p2"), _stream(stream))
+    _check(rc, "knn_points_bwd")
+
+
+def chamfer_fwd(p, first1, len1, q, first2, len2, idx_pq, d_pq, idx_qp, d_qp, loss_per_pair, loss, workspace,
+                stream=None):
+    D = p.shape[1]
+    if q.shape[1] != D:
+        raise MeshRastError("p and q must have the same dimension")
+    w, wb = _ws(workspace)
+    rc = load().chamfer_fwd(_ptr(p, torch.float32, "p"), p.shape[0], _ptr(first1, torch.int64, "first1"),
+                            _ptr(len1, torch.int64, "len1"), _ptr(q, torch.float32, "q"), q.shape[0],
+                            _ptr(first2, torch.int64, "first2"), _ptr(len2, torch.int64, "len2"), first1.shape[0], D,
+                            _ptr(idx_pq, torch.int64, "idx_pq"), _ptr(d_pq, torch.float32, "d_pq"),
+                            _ptr(idx_qp, torch.int64, "idx_qp"), _ptr(d_qp, torch.float32, "d_qp"),
+                            _ptr(loss_per_pair, torch.float32, "loss_per_pair"), _ptr(loss, torch.float32, "loss"),
+                            w, wb, _stream(stream))
+    _check(rc, "chamfer_fwd")
+
+
+def chamfer_bwd(p, first1, len1, q, first2, len2, idx_pq, idx_qp, grad_loss, grad_per_pair, grad_p, grad_q,
+                stream=None):
+    rc = load().chamfer_bwd(_ptr(p, torch.float32, "p"), p.shape[0], _ptr(first1, torch.int64, "first1"),
+                            _ptr(len1, torch.int64, "len1"), _ptr(q, torch.float32, "q"), q.shape[0],
+                            _ptr(first2, torch.int64, "first2"), _ptr(len2, torch.int64, "len2"), first1.shape[0],
+                            p.shape[1], _ptr(idx_pq, torch.int64, "idx_pq"), _ptr(idx_qp, torch.int64, "idx_qp"),
+                            _ptr(grad_loss, torch.float32, "grad_loss"),
+                            _ptr(grad_per_pair, torch.float32, "grad_per_pair"), _ptr(grad_p, torch.float32, "grad_p"),
+                            _ptr(grad_q, torch.float32, "grad_q"), _stream(stream))
+    _check(rc, "chamfer_bwd")

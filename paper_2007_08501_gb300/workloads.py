@@ -381,3 +381,76 @@ def sample_pixels(N, S, per_image, seed):
         idx = np.sort(rng.choice(S * S, size=m, replace=False))
         out.append(np.stack([np.full(m, n), idx // S, idx % S], 1))
     return np.concatenate(out, 0).astype(np.int64) if out else np.zeros((0, 3), np.int64)
+
+
+# --------------------------------------------------------------------------
+# nearest neighbours and Chamfer (Section 3.1; App. A: points sampled
+# uniformly from a mesh surface, homogeneous or heterogeneous batch sizes)
+# --------------------------------------------------------------------------
+@dataclass
+class CloudPairs:
+    p: np.ndarray        # (P1, 3) f32 query clouds, packed
+    first1: np.ndarray   # (N,) i64
+    len1: np.ndarray     # (N,) i64
+    q: np.ndarray        # (P2, 3) f32 candidate clouds, packed
+    first2: np.ndarray
+    len2: np.ndarray
+
+    @property
+    def N(self):
+        return int(self.first1.shape[0])
+
+
+def _packed_surface_samples(counts, seed_base, level, sigma):
+    pts = []
+    for i, n in enumerate(counts):
+        rng = np.random.default_rng(seed_base + i)
+        v, f = displaced_sphere(level, sigma, rng)
+        pts.append(sample_surface(v, f, int(n), rng))
+    counts = np.asarray(counts, np.int64)
+    first = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int64) if len(counts) else counts
+    return (np.concatenate(pts, 0) if pts else np.zeros((0, 3))).astype(np.float32), first, counts
+
+
+def cloud_pairs(len1, len2, seed_base, level=4, sigma=0.05):
+    """Pair i: |P_i| = len1[i] and |Q_i| = len2[i] points sampled from two
+    displaced spheres (seeds seed_base + i and seed_base + 50000 + i)."""
+    p, f1, l1 = _packed_surface_samples(len1, seed_base, level, sigma)
+    q, f2, l2 = _packed_surface_samples(len2, seed_base + 50000, level, sigma)
+    return CloudPairs(p, f1, l1, q, f2, l2)
+
+
+@dataclass
+class KnnWorkload:
+    name: str
+    pairs: CloudPairs
+    K: int
+    chamfer: bool        # Chamfer loss forward + backward instead of KNN forward
+    grad_seed: int = 0
+
+
+def knn_workload(kind: str) -> KnnWorkload:
+    """The operator benchmarks of Section 3.1 (batch size 32):
+    'knn'      |P| = |Q| = 50,000 per cloud, K = 8, forward;
+    'knn_het'  |P|, |Q| uniform in [10,000, 90,000] (mean 50,000), K = 8, forward;
+    'chamfer'  |P| = 1,000, |Q| = 50,000, Chamfer loss forward + backward."""
+    B = 32
+    if kind == "knn":
+        return KnnWorkload("32 pairs of clouds, |P| = |Q| = 50,000, K = 8", cloud_pairs([50_000] * B, [50_000] * B,
+                                                                                        7000), 8, False)
+    if kind == "knn_het":
+        rng = np.random.default_rng(7100)
+        l1 = rng.integers(10_000, 90_001, size=B)
+        l2 = rng.integers(10_000, 90_001, size=B)
+        return KnnWorkload("32 pairs of clouds, |P|, |Q| uniform in [10k, 90k], K = 8", cloud_pairs(l1, l2, 7200),
+                           8, False)
+    if kind == "chamfer":
+        return KnnWorkload("32 pairs of clouds, |P| = 1,000, |Q| = 50,000, Chamfer fwd+bwd",
+                           cloud_pairs([1_000] * B, [50_000] * B, 7400), 1, True, grad_seed=7500)
+    raise ValueError(kind)
+
+
+def pairs_per_batch(pairs: CloudPairs, both_ways=False):
+    """Candidate distances one KNN pass evaluates: sum_i |P_i| |Q_i| (twice for Chamfer)."""
+    n = int(np.sum(pairs.len1.astype(np.int64) * pairs.len2.astype(np.int64)))
+    return 2 * n if both_ways else n

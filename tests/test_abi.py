@@ -64,6 +64,24 @@ def test_pure_host_entry_points(lib):
                        None) == ops.MESHRAST_ERR_INVALID_ARG
 
 
+def test_knn_host_checks(lib):
+    from paper_2007_08501_gb300 import ops
+    ops._lib = None
+    L = ops.load()
+    assert L.knn_workspace_bytes(0) == 256 and L.knn_workspace_bytes(-1) == 0
+    assert L.knn_workspace_bytes(1000) % 256 == 0 and L.knn_workspace_bytes(1000) >= 2 * 1001 * 8
+    # argument errors come back before anything touches a device
+    for D, K in ((0, 1), (5, 1), (3, 0), (3, 33)):
+        assert L.knn_points(None, 0, None, None, None, 0, None, None, 0, D, K, None, None, None, 0,
+                            None) == ops.MESHRAST_ERR_INVALID_ARG
+    assert L.knn_points(None, 0, None, None, None, 0, None, None, 0, 3, 4, None, None, None, 0,
+                        None) == ops.MESHRAST_ERR_WORKSPACE
+    assert L.chamfer_fwd(None, 0, None, None, None, 0, None, None, 1, 3, None, None, None, None, None, None, None,
+                         0, None) == ops.MESHRAST_ERR_INVALID_ARG
+    assert L.chamfer_bwd(None, 0, None, None, None, 0, None, None, -1, 3, None, None, None, None, None, None,
+                         None) == ops.MESHRAST_ERR_INVALID_ARG
+
+
 def test_struct_layouts_match_header():
     from paper_2007_08501_gb300 import ops
     assert ctypes.sizeof(ops.rast_params) == 48
