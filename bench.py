@@ -67,13 +67,14 @@ WORKLOADS = {
                                   "points"),
 }
 KERNELS_PER_STEP = {"fwd": 4, "bwd": 2}
-# DRAM bytes (read + write) per launch of a stage's main kernel, keyed by
-# (workload, stage, bin size), from one ncu capture with the current kernel
-# source (summaries in profiles/); a combination without an entry reports null.
+# DRAM bytes (read + write) per C-ABI call of a stage -- every kernel of the
+# call, one ncu capture (gpu__time_duration, dram__bytes_read/write, default
+# cache control) with the current kernel source -- keyed by (workload, stage,
+# bin size); a combination without an entry reports null.
 TRAFFIC_BYTES = {
-    ("1", "fwd", 8): {"kernel": "k_fine<8,8,0>", "bytes": 10693376 + 66129664},
-    ("1", "bwd", 8): {"kernel": "k_blend_rast_bwd<8,1>", "bytes": 104484352 + 3294464},
-    ("1", "bwd", 16): {"kernel": "k_blend_rast_bwd<8,1>", "bytes": 104484352 + 3294464},
+    ("1", "fwd", 16): {"kernel": "rast_blend_fwd call: k_stage + k_scan + k_fill + k_fine<8,16,0> + k_blend_fwd<8>",
+                       "bytes": 160671143},
+    ("1", "bwd", 16): {"kernel": "blend_rast_bwd call: k_stage + k_blend_rast_bwd<8,1>", "bytes": 105950868},
 }
 
 

@@ -7,12 +7,12 @@
 //                per block)) and their exclusive prefix, so that one launch
 //                covers a heterogeneous batch without a host round trip
 //   k_knn<D,KM,QB>  one block per tile of queries of one cloud: the cloud's
-//                candidates pass through shared memory in chunks (one array
-//                per coordinate); a group of G consecutive lanes shares QB
+//                candidates pass through shared memory in chunks (pairs of
+//                candidates interleaved by coordinate); a group of G consecutive lanes shares QB
 //                queries and splits the candidates among its lanes; distances
 //                of two candidates at a time in packed f32x2 arithmetic (two
 //                lanes of fp32 per instruction, each rounded as plain fp32);
-//                register top-K per query (KM >= K slots); the group's lists
+//                register top-K per query (K of KM slots); the group's lists
 //                merge through warp shuffles.  Two problems (both directions
 //                of a Chamfer loss) can share one launch.
 //   k_pair_sums / k_mean   per-pair Chamfer terms and the batch mean, fixed
@@ -126,24 +126,39 @@ __device__ __forceinline__ void f2_split(unsigned long long v, float &lo, float 
 // ranking key: ascending distance, then ascending candidate row
 __device__ __forceinline__ bool nn_before(float d, int j, float e, int k) { return d < e || (d == e && j < k); }
 
-// sorted list of the KM best (distance, local row) pairs; only the first K count
+// the K best (distance, local row) pairs so far, ascending, right-aligned in
+// KM slots: slots below KM - K hold -inf and never move, so the K-th best --
+// the admission threshold and the entry a new one evicts -- is always slot
+// KM - 1 (no register array is ever indexed by a run-time value)
 template <int KM>
 struct NnList {
     float z[KM];
     int f[KM];
-    __device__ __forceinline__ void init() {
+    __device__ __forceinline__ void init(int K) {
 #pragma unroll
-        for (int k = 0; k < KM; ++k) { z[k] = __int_as_float(0x7f800000); f[k] = INT_MAX; }
+        for (int k = 0; k < KM; ++k) {
+            z[k] = k < KM - K ? __int_as_float(0xff800000) : __int_as_float(0x7f800000);
+            f[k] = INT_MAX;
+        }
     }
-    // entry K-1 (the admission threshold)
-    __device__ __forceinline__ void kth(int K, float &kz, int &kf) const {
-        kz = z[0];
-        kf = f[0];
+    // insertion during the scan: a thread meets its candidates in increasing
+    // row order, so a new entry goes after the entries of equal distance and
+    // the distance alone decides
+    __device__ __forceinline__ void push(float d, int j) {
+        z[KM - 1] = d;
+        f[KM - 1] = j;
 #pragma unroll
-        for (int k = 1; k < KM; ++k)
-            if (k == K - 1) { kz = z[k]; kf = f[k]; }
+        for (int k = KM - 1; k > 0; --k) {
+            const bool sw = z[k] < z[k - 1];
+            const float tz = z[k - 1];
+            const int tf = f[k - 1];
+            z[k - 1] = sw ? z[k] : tz;
+            f[k - 1] = sw ? f[k] : tf;
+            z[k] = sw ? tz : z[k];
+            f[k] = sw ? tf : f[k];
+        }
     }
-    // the last slot is beyond the first K or is the evicted K-th entry
+    // insertion of another lane's entry (full ranking key)
     __device__ __forceinline__ void insert(float d, int j) {
         z[KM - 1] = d;
         f[KM - 1] = j;
@@ -160,8 +175,57 @@ struct NnList {
     }
 };
 
+// chunk layout: candidates 2p and 2p + 1 form pair p; SA[p] = (x, x', y, y'),
+// SB[p] = (z, z', w, w'), so one 16-byte load gives two coordinates of both
+template <int D>
+struct PairCoords {
+    unsigned long long c[D];
+};
+
+template <int D>
+__device__ __forceinline__ PairCoords<D> load_pair(const float4 *SA, const float4 *SB, int p) {
+    PairCoords<D> r;
+    if (D >= 2) {
+        const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(SA + p);
+        r.c[0] = a.x;
+        r.c[D >= 2 ? 1 : 0] = a.y;
+    } else {
+        r.c[0] = *reinterpret_cast<const unsigned long long *>(SA + p);
+    }
+    if (D == 4) {
+        const ulonglong2 b = *reinterpret_cast<const ulonglong2 *>(SB + p);
+        r.c[D >= 3 ? 2 : 0] = b.x;
+        r.c[D >= 4 ? 3 : 0] = b.y;
+    } else if (D == 3) {
+        r.c[D >= 3 ? 2 : 0] = *reinterpret_cast<const unsigned long long *>(SB + p);
+    }
+    return r;
+}
+
+// squared distances of one query (coordinates duplicated in both lanes) to a pair
+template <int D>
+__device__ __forceinline__ void pair_dist(const unsigned long long (&q)[D], const PairCoords<D> &X, float &s0,
+                                          float &s1) {
+    unsigned long long dx = f2_sub(q[0], X.c[0]);
+    unsigned long long s = f2_mul(dx, dx);
+#pragma unroll
+    for (int c = 1; c < D; ++c) {
+        dx = f2_sub(q[c], X.c[c]);
+        s = f2_fma(dx, dx, s);
+    }
+    f2_split(s, s0, s1);
+}
+
+template <int KM>
+__device__ __forceinline__ void take1(NnList<KM> &L, float &thr, float d, int j) {
+    const bool lt = d < thr;
+    thr = lt ? d : thr;
+    L.z[0] = lt ? d : L.z[0];
+    L.f[0] = lt ? j : L.f[0];
+}
+
 template <int D, int KM, int QB>
-__global__ void __launch_bounds__(kThreads) k_knn(KnnArgs a) {
+__global__ void __launch_bounds__(kThreads, KM <= 2 ? 4 : 1) k_knn(KnnArgs a) {
     const int pb = (a.nprob > 1 && (int)blockIdx.x >= a.pr[1].block0) ? 1 : 0;
     const KnnProblem &P = a.pr[pb];
     const long long b = (long long)blockIdx.x - P.block0;
@@ -196,49 +260,72 @@ __global__ void __launch_bounds__(kThreads) k_knn(KnnArgs a) {
     float thr[QB];
 #pragma unroll
     for (int u = 0; u < QB; ++u) {
-        L[u].init();
+        L[u].init(K);
         thr[u] = __int_as_float(0x7f800000);
     }
 
-    __shared__ __align__(16) float S[D][kChunk + 2];
+    __shared__ __align__(16) float4 SA[kChunk / 2 + 1];
+    __shared__ __align__(16) float4 SB[D > 2 ? kChunk / 2 + 1 : 1];
+    float *fa = reinterpret_cast<float *>(SA), *fb = reinterpret_cast<float *>(SB);
     for (int base = 0; base < cn; base += kChunk) {
         const int cnt = min(kChunk, cn - base);
         __syncthreads();   // the previous chunk is consumed
         const float *src = P.p2 + (c0 + base) * D;
         for (int e = threadIdx.x; e < cnt * D; e += kThreads) {
-            const int pt = e / D;
-            S[e - pt * D][pt] = src[e];
+            const int pt = e / D, c = e - pt * D;
+            (c < 2 ? fa : fb)[(pt >> 1) * 4 + (c & 1) * 2 + (pt & 1)] = src[e];
         }
-        if ((cnt & 1) && threadIdx.x < D) S[threadIdx.x][cnt] = threadIdx.x == 0 ? __int_as_float(0x7f800000) : 0.f;
+        if ((cnt & 1) && threadIdx.x < D) {   // the odd slot: x = +inf, never admitted
+            const int c = threadIdx.x;
+            (c < 2 ? fa : fb)[(cnt >> 1) * 4 + (c & 1) * 2 + 1] = c == 0 ? __int_as_float(0x7f800000) : 0.f;
+        }
         __syncthreads();
         const int npair = (cnt + 1) >> 1;
-#pragma unroll 2
-        for (int jp = gl; jp < npair; jp += G) {
-            unsigned long long X[D];
-#pragma unroll
-            for (int c = 0; c < D; ++c) X[c] = *reinterpret_cast<const unsigned long long *>(&S[c][2 * jp]);
+        int jp = gl;
+        // two pairs per step: one admission test per query for four candidates
+        for (; jp + G < npair; jp += 2 * G) {
+            const PairCoords<D> X = load_pair<D>(SA, SB, jp);
+            const PairCoords<D> Y = load_pair<D>(SA, SB, jp + G);
 #pragma unroll
             for (int u = 0; u < QB; ++u) {
-                unsigned long long dx = f2_sub(qq[u][0], X[0]);
-                unsigned long long s = f2_mul(dx, dx);
-#pragma unroll
-                for (int c = 1; c < D; ++c) {
-                    dx = f2_sub(qq[u][c], X[c]);
-                    s = f2_fma(dx, dx, s);
-                }
-                float s0, s1;
-                f2_split(s, s0, s1);
-                if (fminf(s0, s1) < thr[u]) {
-                    // one insertion site per query keeps the unrolled list in registers
+                float s0, s1, t0, t1;
+                pair_dist<D>(qq[u], X, s0, s1);
+                pair_dist<D>(qq[u], Y, t0, t1);
+                if (fminf(fminf(s0, s1), fminf(t0, t1)) < thr[u]) {
+                    const int ja = base + 2 * jp, jb = base + 2 * (jp + G);
+                    if (KM == 1) {   // predicated, in row order
+                        take1(L[u], thr[u], s0, ja);
+                        take1(L[u], thr[u], s1, ja + 1);
+                        take1(L[u], thr[u], t0, jb);
+                        take1(L[u], thr[u], t1, jb + 1);
+                    } else {
+                        // in row order; one insertion site per query keeps the
+                        // unrolled list in registers
 #pragma unroll 1
-                    for (int h = 0; h < 2; ++h) {
-                        const float d = h ? s1 : s0;
-                        if (d < thr[u]) {
-                            int kf;
-                            L[u].insert(d, base + 2 * jp + h);
-                            L[u].kth(K, thr[u], kf);
+                        for (int h = 0; h < 4; ++h) {
+                            const float d = h == 0 ? s0 : (h == 1 ? s1 : (h == 2 ? t0 : t1));
+                            if (d < thr[u]) {
+                                L[u].push(d, (h < 2 ? ja : jb) + (h & 1));
+                                thr[u] = L[u].z[KM - 1];
+                            }
                         }
                     }
+                }
+            }
+        }
+        if (jp < npair) {
+            const PairCoords<D> X = load_pair<D>(SA, SB, jp);
+#pragma unroll
+            for (int u = 0; u < QB; ++u) {
+                float s0, s1;
+                pair_dist<D>(qq[u], X, s0, s1);
+                if (s0 < thr[u]) {
+                    L[u].push(s0, base + 2 * jp);
+                    thr[u] = L[u].z[KM - 1];
+                }
+                if (s1 < thr[u]) {
+                    L[u].push(s1, base + 2 * jp + 1);
+                    thr[u] = L[u].z[KM - 1];
                 }
             }
         }
@@ -253,10 +340,7 @@ __global__ void __launch_bounds__(kThreads) k_knn(KnnArgs a) {
             for (int k = 0; k < KM; ++k) {
                 const float v = __shfl_down_sync(0xffffffffu, L[u].z[k], o);
                 const int w = __shfl_down_sync(0xffffffffu, L[u].f[k], o);
-                float kz;
-                int kf;
-                L[u].kth(K, kz, kf);
-                if (recv && k < K && nn_before(v, w, kz, kf)) L[u].insert(v, w);
+                if (recv && k >= KM - K && nn_before(v, w, L[u].z[KM - 1], L[u].f[KM - 1])) L[u].insert(v, w);
             }
         }
     }
@@ -266,10 +350,11 @@ __global__ void __launch_bounds__(kThreads) k_knn(KnnArgs a) {
         if (!valid[u]) continue;
 #pragma unroll
         for (int k = 0; k < KM; ++k) {
-            if (k >= K) break;
+            const int r = k - (KM - K);   // rank of slot k
+            if (r < 0) continue;
             const bool has = L[u].f[k] != INT_MAX;
-            P.idx[row[u] * K + k] = has ? c0 + L[u].f[k] : -1;
-            P.dists[row[u] * K + k] = has ? L[u].z[k] : __int_as_float(0x7f800000);
+            P.idx[row[u] * K + r] = has ? c0 + L[u].f[k] : -1;
+            P.dists[row[u] * K + r] = has ? L[u].z[k] : __int_as_float(0x7f800000);
         }
     }
 }
@@ -456,7 +541,7 @@ int km_for_knn(int K) {
     while (km < K) km <<= 1;
     return km;
 }
-int qb_for(int km) { return km == 1 ? 4 : (km == 2 ? 2 : 1); }
+int qb_for(int km) { return km <= 2 ? 4 : (km <= 8 ? 2 : 1); }
 
 // lanes per query group: enough threads to fill the GPU twice over, but at
 // least 256 candidates per lane on average
@@ -470,8 +555,11 @@ int group_for(long long P1, long long P2, long long N, int qb) {
 
 template <int D, int KM>
 cudaError_t launch_knn_t(const KnnArgs &a, int blocks, cudaStream_t st) {
-    constexpr int QB = KM == 1 ? 4 : (KM == 2 ? 2 : 1);
-    k_knn<D, KM, QB><<<blocks, kThreads, 0, st>>>(a);
+    constexpr int QB = KM <= 2 ? 4 : (KM <= 8 ? 2 : 1);
+    auto kern = k_knn<D, KM, QB>;
+    // shared memory for four 33 KB blocks per SM
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    kern<<<blocks, kThreads, 0, st>>>(a);
     return cudaGetLastError();
 }
 
