@@ -225,7 +225,7 @@ __device__ __forceinline__ void take1(NnList<KM> &L, float &thr, float d, int j)
 }
 
 template <int D, int KM, int QB>
-__global__ void __launch_bounds__(kThreads, KM <= 2 ? 4 : 1) k_knn(KnnArgs a) {
+__global__ void __launch_bounds__(kThreads, KM <= 2 ? 4 : (KM <= 8 ? 3 : 2)) k_knn(KnnArgs a) {
     const int pb = (a.nprob > 1 && (int)blockIdx.x >= a.pr[1].block0) ? 1 : 0;
     const KnnProblem &P = a.pr[pb];
     const long long b = (long long)blockIdx.x - P.block0;
@@ -266,21 +266,26 @@ __global__ void __launch_bounds__(kThreads, KM <= 2 ? 4 : 1) k_knn(KnnArgs a) {
 
     __shared__ __align__(16) float4 SA[kChunk / 2 + 1];
     __shared__ __align__(16) float4 SB[D > 2 ? kChunk / 2 + 1 : 1];
-    float *fa = reinterpret_cast<float *>(SA), *fb = reinterpret_cast<float *>(SB);
     for (int base = 0; base < cn; base += kChunk) {
         const int cnt = min(kChunk, cn - base);
         __syncthreads();   // the previous chunk is consumed
         const float *src = P.p2 + (c0 + base) * D;
-        for (int e = threadIdx.x; e < cnt * D; e += kThreads) {
-            const int pt = e / D, c = e - pt * D;
-            (c < 2 ? fa : fb)[(pt >> 1) * 4 + (c & 1) * 2 + (pt & 1)] = src[e];
-        }
-        if ((cnt & 1) && threadIdx.x < D) {   // the odd slot: x = +inf, never admitted
-            const int c = threadIdx.x;
-            (c < 2 ? fa : fb)[(cnt >> 1) * 4 + (c & 1) * 2 + 1] = c == 0 ? __int_as_float(0x7f800000) : 0.f;
+        const int npair = (cnt + 1) >> 1;
+        // one thread per pair: 2 D coalesced loads, one 16-byte (and one 8- or
+        // 16-byte) shared store; an odd last slot gets x = +inf (never admitted)
+#pragma unroll 1
+        for (int pp = threadIdx.x; pp < npair; pp += kThreads) {
+            float v0[4] = {0.f, 0.f, 0.f, 0.f}, v1[4] = {0.f, 0.f, 0.f, 0.f};
+            const bool two = 2 * pp + 1 < cnt;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                v0[c] = src[2 * pp * D + c];
+                v1[c] = two ? src[(2 * pp + 1) * D + c] : (c == 0 ? __int_as_float(0x7f800000) : 0.f);
+            }
+            SA[pp] = make_float4(v0[0], v1[0], v0[1], v1[1]);
+            if (D > 2) SB[pp] = make_float4(v0[2], v1[2], v0[3], v1[3]);
         }
         __syncthreads();
-        const int npair = (cnt + 1) >> 1;
         int jp = gl;
         // two pairs per step: one admission test per query for four candidates
         for (; jp + G < npair; jp += 2 * G) {
