@@ -515,6 +515,34 @@ def run_ours(args):
                     **{k + "_ms": v for k, v in sstages.items()}}
         del sp
 
+    # silhouette forward without Fragment data (the fine pass blends and writes
+    # only the image; nothing is left for a backward pass): forward-only use
+    sil_only = None
+    if shading is None and w.blend_mode != "rgb" and w.K <= 16 and tuned["bin_size"] > 0:
+        import torch as _t
+        img2 = _t.empty_like(pipe.img)
+        fn = lambda: ops.rast_blend_fwd(pipe.p, pipe.bp, pipe.verts, pipe.faces, pipe.ff, pipe.nf, pipe.cams, None,
+                                        None, None, None, None, img2, pipe.ws)
+        fn()
+        _t.cuda.synchronize()
+        g = _t.cuda.CUDAGraph()
+        with _t.cuda.graph(g):
+            fn()
+        ts = []
+        for i in range(args.warmup + args.steps):
+            flush.zero_()
+            e0, e1 = _t.cuda.Event(enable_timing=True), _t.cuda.Event(enable_timing=True)
+            e0.record()
+            g.replay()
+            e1.record()
+            e1.synchronize()
+            if i >= args.warmup:
+                ts.append(e0.elapsed_time(e1))
+        same = bool(_t.equal(img2, pipe.img))
+        sil_only = {"fwd_ms": round(statistics.mean(ts), 4), "fwd_with_fragments_ms": round(stages["fwd"], 4),
+                    "fragment_bytes_not_written": slots * 28, "image_identical": same}
+        del g, img2
+
     plain = None
     if not args.no_plain and args.workload == "1":
         pp = Pipeline(w, bin_size=0, max_faces_per_bin=1, device=dev)
@@ -558,7 +586,8 @@ def run_ours(args):
             "fine_pass": {"face_pixel_tests": fine_tests,
                           "tests_per_s": round(fine_tests / (stages.get("fwd", stages.get("rast_fwd")) / 1e3), 1),
                           "note": "sum over bins of (pixels in bin x faces in bin)"},
-            "clocks": clk, "unfused": separate, "plain_form": plain, "fit_loop": fit_loop,
+            "clocks": clk, "unfused": separate, "silhouette_without_fragments": sil_only, "plain_form": plain,
+            "fit_loop": fit_loop,
             "status": st,
             "wall_s_timed_region": round(wall, 3),
         }

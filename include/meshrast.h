@@ -180,7 +180,12 @@ MESHRAST_API int blend_fwd(const blend_params *bp, int64_t N, int64_t S, int64_t
  * Outputs (all overwritten): the Fragments as in rast_mesh_fwd, and image
  * (N,S,S,4) as in blend_fwd; N, S, K come from p.  vert_colors may be NULL in
  * MESHRAST_BLEND_SIL mode.  image, pix_to_face, dists (and zbuf) must be
- * 16-byte aligned.  Status word as in rast_mesh_fwd. */
+ * 16-byte aligned.  Status word as in rast_mesh_fwd.
+ * Silhouette without Fragment data: in MESHRAST_BLEND_SIL mode with
+ * bin_size 8 or 16 and K <= 16, pix_to_face, zbuf, bary and dists may all be
+ * NULL; the fine pass then writes only the image (the same values as with
+ * the Fragments written), and nothing is left for a backward pass.  NULL
+ * Fragment pointers in any other case are MESHRAST_ERR_INVALID_ARG. */
 MESHRAST_API int rast_blend_fwd(const rast_params *p, const blend_params *bp,
                   const float *verts, int64_t V,
                   const int64_t *faces, int64_t F,

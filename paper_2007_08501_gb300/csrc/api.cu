@@ -140,7 +140,12 @@ static int forward(const rast_params *p, const float *verts, int64_t V, const in
     if (F > 0 && (!faces || (V > 0 && !verts))) return MESHRAST_ERR_INVALID_ARG;
     const int64_t S = p->image_size, K = p->faces_per_pixel;
     const int64_t slots = (int64_t)p->N * S * S * K;
-    if (slots > 0 && (!pix_to_face || !zbuf || !bary || !dists)) return MESHRAST_ERR_INVALID_ARG;
+    const bool binned = p->bin_size > 0;
+    // no Fragment data at all: only when the fine pass itself blends the silhouette
+    const bool no_frag = !pix_to_face && !zbuf && !bary && !dists;
+    const bool fine_blend = blend && binned && mr::fine_blends((int)K, blend->rgb != 0);
+    if (slots > 0 && (!pix_to_face || !zbuf || !bary || !dists) && !(no_frag && fine_blend))
+        return MESHRAST_ERR_INVALID_ARG;
     WsLayout L;
     int rc = check_ws(p, V, F, workspace, workspace_bytes, &L);
     if (rc) return rc;
@@ -148,7 +153,6 @@ static int forward(const rast_params *p, const float *verts, int64_t V, const in
     char *ws = reinterpret_cast<char *>(workspace);
     if (cudaMemsetAsync(ws, 0, 256, st) != cudaSuccess) return MESHRAST_ERR_CUDA;
     if (p->N == 0) return MESHRAST_OK;
-    const bool binned = p->bin_size > 0;
     if (binned && L.NB > 0) {
         if (cudaMemsetAsync(ws + L.counts, 0, (size_t)L.NB * 4, st) != cudaSuccess) return MESHRAST_ERR_CUDA;
     }
@@ -217,8 +221,9 @@ static int forward(const rast_params *p, const float *verts, int64_t V, const in
     ka.out = out;
     ka.sort_cap = mr::fine_sort_cap(p->max_faces_per_bin, (int)K, p->bin_size * p->bin_size);
     std::memset(&ka.blend, 0, sizeof(ka.blend));
-    if (blend && mr::fine_blends((int)K, blend->rgb != 0)) {
+    if (fine_blend) {
         ka.blend = *blend;
+        ka.blend.frag = no_frag ? 0 : 1;
         if (blended) *blended = true;
     }
     return mr::launch_fine(ka, p->bin_size, st) == cudaSuccess ? MESHRAST_OK : MESHRAST_ERR_CUDA;
@@ -346,10 +351,16 @@ int rast_blend_fwd(const rast_params *p, const blend_params *bp, const float *ve
     if (rc) return rc;
     const bool rgb = bp->mode == MESHRAST_BLEND_RGB;
     const int64_t P = N * S * S;
+    const bool no_frag = !pix_to_face && !zbuf && !bary && !dists;
     if (P > 0) {
         if (!image || !aligned16(image)) return MESHRAST_ERR_INVALID_ARG;
-        if (!pix_to_face || !dists || !aligned16(pix_to_face) || !aligned16(dists) || (zbuf && !aligned16(zbuf)))
+        if (no_frag) {
+            // silhouette without Fragment data: only where the fine pass blends
+            if (rgb || p->bin_size == 0 || !mr::fine_blends((int)K, false)) return MESHRAST_ERR_INVALID_ARG;
+        } else if (!pix_to_face || !dists || !aligned16(pix_to_face) || !aligned16(dists) ||
+                   (zbuf && !aligned16(zbuf))) {
             return MESHRAST_ERR_INVALID_ARG;
+        }
         if (rgb && (!faces || !vert_colors)) return MESHRAST_ERR_INVALID_ARG;
     }
     mr::FineBlend fbl;

@@ -269,13 +269,16 @@ __device__ __forceinline__ void write_pixel(const FineOut &o, int64_t pix, int K
         if (k >= K) break;
         const int64_t s = s0 + k;
         const int f = tk.f[k];
+        const bool store = !BL || bl.frag;
         if (f == 0x7fffffff) {
-            o.pix_to_face[s] = -1;
-            o.zbuf[s] = -1.f;
-            o.bary[3 * s] = -1.f;
-            o.bary[3 * s + 1] = -1.f;
-            o.bary[3 * s + 2] = -1.f;
-            o.dists[s] = -1.f;
+            if (store) {
+                o.pix_to_face[s] = -1;
+                o.zbuf[s] = -1.f;
+                o.bary[3 * s] = -1.f;
+                o.bary[3 * s + 1] = -1.f;
+                o.bary[3 * s + 2] = -1.f;
+                o.dists[s] = -1.f;
+            }
         } else {
             FaceRec R;
             const float4 *src = reinterpret_cast<const float4 *>(rec + f);
@@ -286,12 +289,14 @@ __device__ __forceinline__ void write_pixel(const FineOut &o, int64_t pix, int K
             R.e = __ldg(src + 4);
             float bp[3], d;
             face_fragment(R, p, fl, bp, d);
-            o.pix_to_face[s] = f;
-            o.zbuf[s] = tk.z[k];
-            o.bary[3 * s] = bp[0];
-            o.bary[3 * s + 1] = bp[1];
-            o.bary[3 * s + 2] = bp[2];
-            o.dists[s] = d;
+            if (store) {
+                o.pix_to_face[s] = f;
+                o.zbuf[s] = tk.z[k];
+                o.bary[3 * s] = bp[0];
+                o.bary[3 * s + 1] = bp[1];
+                o.bary[3 * s + 2] = bp[2];
+                o.dists[s] = d;
+            }
             if constexpr (BL) fb.slot(bl, f, tk.z[k], d, bp);
         }
     }
@@ -312,6 +317,7 @@ __device__ __forceinline__ void write_pixel_vec(const FineOut &o, int64_t pix, i
     }
     FwdBlend fb;
     if constexpr (BL) fb.begin(bl, tk.f[0] != 0x7fffffff, tk.z[0]);
+    const bool store = !BL || bl.frag;
     const int64_t s0 = pix * KM;
     longlong2 *ip = reinterpret_cast<longlong2 *>(o.pix_to_face + s0);
     float4 *zp = reinterpret_cast<float4 *>(o.zbuf + s0);
@@ -319,6 +325,7 @@ __device__ __forceinline__ void write_pixel_vec(const FineOut &o, int64_t pix, i
     float4 *bp = reinterpret_cast<float4 *>(o.bary + s0 * 3);
 #pragma unroll
     for (int j = 0; j < KM / 2; ++j) {
+        if (!store) break;
         longlong2 v;
         v.x = (tk.f[2 * j] == 0x7fffffff) ? -1ll : (long long)tk.f[2 * j];
         v.y = (tk.f[2 * j + 1] == 0x7fffffff) ? -1ll : (long long)tk.f[2 * j + 1];
@@ -346,6 +353,7 @@ __device__ __forceinline__ void write_pixel_vec(const FineOut &o, int64_t pix, i
             zz[i] = tk.z[k];
             if constexpr (BL) fb.slot(bl, tk.f[k], zz[i], dd[i], bb[i]);
         }
+        if (!store) continue;
         zp[j] = make_float4(zz[0], zz[1], zz[2], zz[3]);
         dp[j] = make_float4(dd[0], dd[1], dd[2], dd[3]);
         bp[3 * j] = make_float4(bb[0][0], bb[0][1], bb[0][2], bb[1][0]);

@@ -59,6 +59,7 @@ struct FineOut {
 // K <= 16): same arithmetic as blend_fwd.
 struct FineBlend {
     int on, rgb;
+    int frag;   // 0: blend only, no Fragment data written (silhouette, fine-pass blend)
     float sigma, gamma, znear, zfar, eps, bg0, bg1, bg2;
     const int64_t *faces;
     const float *colors;

@@ -64,6 +64,18 @@ def test_pure_host_entry_points(lib):
                        None) == ops.MESHRAST_ERR_INVALID_ARG
 
 
+def test_fragment_free_forward_is_refused_outside_the_fine_pass_blend(lib):
+    from paper_2007_08501_gb300 import ops
+    ops._lib = None
+    L = ops.load()
+    img = ctypes.c_void_p(256)   # never dereferenced: the call returns before any device work
+    for K, bin_size, mode in ((8, 16, ops.BLEND_RGB), (20, 16, ops.BLEND_SIL), (4, 0, ops.BLEND_SIL)):
+        p = ops.make_rast_params(1, 32, K, 1e-3, bin_size, 128)
+        bp = ops.make_blend_params(mode=mode)
+        assert L.rast_blend_fwd(ctypes.byref(p), ctypes.byref(bp), None, 0, None, 0, None, None, None, None,
+                                None, None, None, None, img, None, 0, None) == ops.MESHRAST_ERR_INVALID_ARG
+
+
 def test_knn_host_checks(lib):
     from paper_2007_08501_gb300 import ops
     ops._lib = None

@@ -217,3 +217,38 @@ def test_fused_forward_equals_rasterize_then_blend(mode, K, bin_size, clip):
     orc = oracle.blend_fwd(fn[0].reshape(P, K), fn[1].reshape(P, K), fn[2].reshape(P, K, 3), fn[3].reshape(P, K),
                            b.faces, b.colors, _f32(SIGMA), _f32(GAMMA), _f32(ZNEAR), _f32(ZFAR), mode=mode)
     assert np.max(np.abs(img.cpu().numpy().reshape(P, 4) - orc)) <= 1e-5
+
+
+@pytest.mark.parametrize("K,bin_size", [(1, 8), (4, 16), (8, 16), (16, 8), (3, 16)])
+def test_silhouette_without_fragments_equals_the_fragment_writing_forward(K, bin_size):
+    # the fine pass blends and writes only the image: bit-identical to the call
+    # that also writes the Fragment data (same arithmetic, stores skipped)
+    b = workloads.sphere_batch([3, 2, 4], 0.05, seed_base=91)
+    d = to_dev(b)
+    N, S = b.N, 70
+    p = ops.make_rast_params(N, S, K, np.float32(BLUR), bin_size, 4096, True, True)
+    ws = ops.alloc_workspace(p, b.V, b.F)
+    bp = ops.make_blend_params(SIGMA, GAMMA, ZNEAR, ZFAR, (1.0, 1.0, 1.0), 1e-10, ops.BLEND_SIL)
+    frag = ops.alloc_fragments(N, S, K)
+    ref = torch.empty((N, S, S, 4), device="cuda")
+    args = (p, bp, d["verts"], d["faces"], d["first_face"], d["num_faces"], d["cams"], None)
+    ops.rast_blend_fwd(*args, *frag, ref, ws)
+    img = torch.full((N, S, S, 4), 7.0, device="cuda")
+    ops.rast_blend_fwd(*args, None, None, None, None, img, ws)
+    assert ops.rast_query_status(ws) == 0
+    assert torch.equal(img, ref)
+    assert float(img[..., 3].max()) > 0.5
+
+
+def test_fragment_free_forward_only_where_the_fine_pass_blends():
+    b = workloads.sphere_batch([2], 0.05, seed_base=92)
+    d = to_dev(b)
+    colors = torch.from_numpy(b.colors).cuda()
+    img = torch.empty((1, 32, 32, 4), device="cuda")
+    for K, bin_size, mode in ((8, 16, ops.BLEND_RGB), (20, 16, ops.BLEND_SIL), (4, 0, ops.BLEND_SIL)):
+        p = ops.make_rast_params(1, 32, K, np.float32(BLUR), bin_size, 4096, True, True)
+        ws = ops.alloc_workspace(p, b.V, b.F)
+        bp = ops.make_blend_params(SIGMA, GAMMA, ZNEAR, ZFAR, (1.0, 1.0, 1.0), 1e-10, mode)
+        with pytest.raises(ops.MeshRastError):
+            ops.rast_blend_fwd(p, bp, d["verts"], d["faces"], d["first_face"], d["num_faces"], d["cams"], colors,
+                               None, None, None, None, img, ws)
