@@ -98,6 +98,22 @@ def _args():
     return ap.parse_args()
 
 
+def max_over_ranks(x, dist, device):
+    """The slowest rank's value: every replica renders its own batch, and the
+    job ends when the last one finishes (identity without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms, scale=1e6):
+    """Units all ranks processed per second (/ scale), timed by the slowest rank."""
+    return world * units_per_rank / (ms / 1e3) / scale
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -449,13 +465,9 @@ def run_ours(args):
     wall = time.perf_counter() - t_wall
     clk = clocks.stop()
     step_ms = [sum(s.values()) for s in per_step]
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
     ms = total_ms / args.steps
-    value = world * slots / (ms / 1e3) / 1e6
+    value = whole_job_rate(slots, world, ms)
     st = pipe.status()
 
     stages = {k: statistics.mean(s[k] for s in per_step) for k in per_step[0]}
@@ -495,12 +507,8 @@ def run_ours(args):
         e1.synchronize()
         if i >= args.warmup:
             e_ms.append(e0.elapsed_time(e1))
-    e2e_ms = statistics.mean(e_ms)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": round(world * slots / (e2e_ms / 1e3) / 1e6, 1), "unit": UNIT,
+    e2e_ms = max_over_ranks(statistics.mean(e_ms), dist, dev)
+    e2e = {"value": round(whole_job_rate(slots, world, e2e_ms), 1), "unit": UNIT,
            "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     separate = None
@@ -739,13 +747,9 @@ def run_points(args):
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = sum(sum(s.values()) for s in per_step)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(sum(s.values()) for s in per_step), dist, dev)
     ms = total_ms / args.steps
-    value = world * slots / (ms / 1e3) / 1e6
+    value = whole_job_rate(slots, world, ms)
     stages = {k: statistics.mean(s[k] for s in per_step) for k in per_step[0]}
     dom = max(stages, key=stages.get)
     alg = point_bytes(w)
@@ -776,8 +780,8 @@ def run_points(args):
         e1.synchronize()
         if i >= args.warmup:
             e_ms.append(e0.elapsed_time(e1))
-    e2e_ms = statistics.mean(e_ms)
-    e2e = {"value": round(world * slots / (e2e_ms / 1e3) / 1e6, 1), "unit": UNIT, "ms_per_step": round(e2e_ms, 4),
+    e2e_ms = max_over_ranks(statistics.mean(e_ms), dist, dev)
+    e2e = {"value": round(whole_job_rate(slots, world, e2e_ms), 1), "unit": UNIT, "ms_per_step": round(e2e_ms, 4),
            "h2d_bytes_per_step": sum(h.numel() * h.element_size() for _, h in h_in),
            "d2h_bytes_per_step": sum(h.numel() * h.element_size() for _, h in h_out)}
     cpu = None
@@ -1024,13 +1028,9 @@ def run_knn(args):
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()
-    total_ms = sum(sum(s.values()) for s in per_step)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(sum(s.values()) for s in per_step), dist, dev)
     ms = total_ms / args.steps
-    value = world * pairs / (ms / 1e3) / 1e9
+    value = whole_job_rate(pairs, world, ms, 1e9)
     stages = {k: statistics.mean(s[k] for s in per_step) for k in per_step[0]}
     dom = "chamfer_fwd" if w.chamfer else "knn"
     achieved = pairs * KNN_OPS_PER_PAIR / (stages[dom] / 1e3)
@@ -1058,8 +1058,8 @@ def run_knn(args):
         e1.synchronize()
         if i >= args.warmup:
             e_ms.append(e0.elapsed_time(e1))
-    e2e_ms = statistics.mean(e_ms)
-    e2e = {"value": round(world * pairs / (e2e_ms / 1e3) / 1e9, 2), "unit": KNN_UNIT, "ms_per_step": round(e2e_ms, 4),
+    e2e_ms = max_over_ranks(statistics.mean(e_ms), dist, dev)
+    e2e = {"value": round(whole_job_rate(pairs, world, e2e_ms, 1e9), 2), "unit": KNN_UNIT, "ms_per_step": round(e2e_ms, 4),
            "h2d_bytes_per_step": sum(h.numel() * h.element_size() for _, h in h_in),
            "d2h_bytes_per_step": sum(h.numel() * h.element_size() for _, h in h_out)}
     cpu = None

@@ -1,0 +1,71 @@
+"""Replica runs under torch.distributed, on CPU (gloo, world size 2, 127.0.0.1):
+the benchmark's host logic for N > 1 -- the timed region ends with the
+slowest rank, the rate counts every rank's units -- and the reference arm's
+rank discipline (rank 0 alone works and prints).  The path itself has no
+collective: each rank renders its own copy of the batch."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket(socket.AF_INET, socket.SOCK_STREAM) as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, ms, q):
+    import torch
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    sys.path.insert(0, ROOT)
+    import bench
+    got = bench.max_over_ranks(ms[rank], dist, torch.device("cpu"))
+    q.put((rank, got, bench.whole_job_rate(1000, world, got)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_slowest_rank_sets_the_time_and_every_rank_counts():
+    mp = pytest.importorskip("torch.multiprocessing")
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    ms = [3.0, 5.0]
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, ms, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    try:
+        res = sorted(q.get(timeout=120) for _ in range(2))
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.kill()
+    assert [r for r, _, _ in res] == [0, 1]
+    for _, got, rate in res:
+        assert got == 5.0
+        assert rate == pytest.approx(2 * 1000 / 5e-3 / 1e6)
+    assert all(p.exitcode == 0 for p in procs)
+
+
+def test_single_process_is_the_identity():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(2.5, None, None) == 2.5
+    assert bench.whole_job_rate(4_194_304, 1, 0.5) == pytest.approx(8388.608)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
