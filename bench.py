@@ -75,6 +75,9 @@ TRAFFIC_BYTES = {
     ("1", "fwd", 16): {"kernel": "rast_blend_fwd call: k_stage + k_scan + k_fill + k_fine<8,16,0> + k_blend_fwd<8>",
                        "bytes": 160671143},
     ("1", "bwd", 16): {"kernel": "blend_rast_bwd call: k_stage + k_blend_rast_bwd<8,1>", "bytes": 105950868},
+    ("1", "fwd", 8): {"kernel": "rast_blend_fwd call: k_stage + k_scan + k_fill + k_fine<8,8,0> + k_blend_fwd<8>",
+                      "bytes": 166800670},
+    ("1", "bwd", 8): {"kernel": "blend_rast_bwd call: k_stage + k_blend_rast_bwd<8,1>", "bytes": 106005435},
 }
 
 
