@@ -78,6 +78,11 @@ TRAFFIC_BYTES = {
     ("1", "fwd", 8): {"kernel": "rast_blend_fwd call: k_stage + k_scan + k_fill + k_fine<8,8,0> + k_blend_fwd<8>",
                       "bytes": 166800670},
     ("1", "bwd", 8): {"kernel": "blend_rast_bwd call: k_stage + k_blend_rast_bwd<8,1>", "bytes": 106005435},
+    ("points", "rast_fwd", 8): {"kernel": "pts_rasterize_fwd call: k_pstage + k_scan + k_pfill + k_pfine<0,8>",
+                                "bytes": 552453578},
+    # the same rasterizer call (compositing mode does not enter it)
+    ("points_norm", "rast_fwd", 8): {"kernel": "pts_rasterize_fwd call: k_pstage + k_scan + k_pfill + "
+                                               "k_pfine<0,8>", "bytes": 552453578},
 }
 
 
@@ -758,8 +763,10 @@ def run_points(args):
     alg = point_bytes(w)
     peak, peak_kind = _peaks()
     achieved = alg[dom] / (stages[dom] / 1e3) / 1e9
+    tr = TRAFFIC_BYTES.get((args.workload, dom, bin_size))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "algorithmic_bytes": alg[dom], "kernel": dom,
+                "frac": round(achieved / peak, 4), "traffic": tr["bytes"] if tr else None,
+                "traffic_kernel": tr["kernel"] if tr else None, "algorithmic_bytes": alg[dom], "kernel": dom,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
                 else "fallback 6.8 TB/s"}
     # end to end with host buffers
