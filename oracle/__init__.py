@@ -65,29 +65,12 @@ def _open(path):
 
 
 def _load():
+    # ORACLE_MESH_LIB names another build of oracle.c: the mutation tests plant
+    # a mistake in a copy of the source and check that the pins fail
     global _lib
     if _lib is None:
-        _lib = _open(build())
+        _lib = _open(os.environ.get("ORACLE_MESH_LIB") or build())
     return _lib
-
-
-class use_library:
-    """Context manager: run the wrappers against another build of oracle.c
-    (the mutation tests plant mistakes in a copy and check that the pins fail)."""
-
-    def __init__(self, path):
-        self.path = path
-
-    def __enter__(self):
-        global _lib
-        self.prev = _load()
-        _lib = _open(self.path)
-        return self
-
-    def __exit__(self, *exc):
-        global _lib
-        _lib = self.prev
-        return False
 
 
 def compile_source(src_text, out_path):

@@ -47,7 +47,7 @@ def build(force: bool = False) -> str:
 def _load():
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
+        L = ctypes.CDLL(os.environ.get("ORACLE_KNN_LIB") or build())
         L.okn_knn.argtypes = [_f32p, _i64, _i64p, _i64p, _f32p, _i64p, _i64p, _i64, _int, _int, _i64p, _i64,
                               _i64p, _f32p]
         _lib = L

@@ -48,7 +48,7 @@ def build(force: bool = False) -> str:
 def _load():
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
+        L = ctypes.CDLL(os.environ.get("ORACLE_POINTS_LIB") or build())
         L.orp_rasterize.argtypes = [_f64p, _i64, _i64p, _i64p, _i64, _f64p, _i64, _i64, _dbl, _i64p, _i64,
                                     _i64p, _f64p, _f64p]
         L.orp_margins.argtypes = [_f64p, _i64, _i64p, _i64p, _i64, _f64p, _i64, _i64, _dbl, _i64p, _i64, _dbl,

@@ -39,7 +39,7 @@ def build(force: bool = False) -> str:
 def _load():
     global _lib
     if _lib is None:
-        L = ctypes.CDLL(build())
+        L = ctypes.CDLL(os.environ.get("ORACLE_SHADING_LIB") or build())
         common = [_i64, _i64, _i64p, _i64p, _f64p, _f64p, _f64p, _i64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p,
                   _int, _int]
         L.ors_shade_fwd.argtypes = common + [_f64p]

@@ -1,0 +1,88 @@
+"""The oracle pins catch plausible mistakes: each case plants one mistake in a
+copy of an oracle's C source (a transposed operand, a dropped term, a wrong
+sign, a reversed tie-break, a missing correction), builds it, and runs the
+pin tests of that oracle against the mutant in a subprocess: they must fail.
+A control run of an unmodified copy must pass, so that a failure means the
+pins saw the mistake and not a broken harness."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ORACLE = os.path.join(ROOT, "oracle")
+
+# source file, environment variable its wrapper reads, the pin tests that cover it
+TARGETS = {
+    "mesh": ("oracle.c", "ORACLE_MESH_LIB", ["tests/test_oracle_raster.py", "tests/test_oracle_blend.py"]),
+    "points": ("points.c", "ORACLE_POINTS_LIB", ["tests/test_oracle_points.py"]),
+    "shading": ("shading.c", "ORACLE_SHADING_LIB", ["tests/test_oracle_shading.py"]),
+    "knn": ("knn.c", "ORACLE_KNN_LIB", ["tests/test_oracle_knn.py"]),
+}
+
+MUTATIONS = [
+    # (target, what the mistake is, original text, mutated text)
+    ("mesh", "barycentric edge function with its operands transposed",
+     "o->b[0] = orc_edge(v1, v2, px, py) / F->A;", "o->b[0] = orc_edge(v2, v1, px, py) / F->A;"),
+    ("mesh", "perspective correction dropped",
+     "double t0 = o->b[0] / v0[2], t1 = o->b[1] / v1[2], t2 = o->b[2] / v2[2];",
+     "double t0 = o->b[0], t1 = o->b[1], t2 = o->b[2];"),
+    ("mesh", "clipped barycentric not renormalised",
+     "o->bp[0] = c0 / cs;", "o->bp[0] = c0;"),
+    ("mesh", "signed distance with the wrong sign inside",
+     "o->d = o->inside ? -o->s : o->s;", "o->d = o->inside ? o->s : -o->s;"),
+    ("mesh", "equal depths ordered by descending face id",
+     "if (x->f < y->f) return -1;\n    if (x->f > y->f) return 1;",
+     "if (x->f > y->f) return -1;\n    if (x->f < y->f) return 1;"),
+    ("points", "opacity against r instead of r squared",
+     "return 1.0 - d / (radius * radius);", "return 1.0 - d / radius;"),
+    ("points", "transmittance multiplied by the opacity",
+     "T *= 1.0 - a;", "T *= a;"),
+    ("shading", "reflection vector with the light term added",
+     "const double D = c > 0.0 ? c : 0.0;\n    double r[3];\n    for (int j = 0; j < 3; j++) r[j] = 2.0 * c * m[j] - l[j];",
+     "const double D = c > 0.0 ? c : 0.0;\n    double r[3];\n    for (int j = 0; j < 3; j++) r[j] = 2.0 * c * m[j] + l[j];"),
+    ("shading", "specular exponent off by one",
+     "const double Sp = spec_on ? pow(s, Lt->sh) : 0.0;", "const double Sp = spec_on ? pow(s, Lt->sh - 1.0) : 0.0;"),
+    ("knn", "the second coordinate's square rounded before the sum (no fma)",
+     "s = fmaf(dc, dc, s);", "s = s + dc * dc;"),
+    ("knn", "equal distances ranked by descending row",
+     "return d < e || (d == e && j < k);", "return d < e || (d == e && j > k);"),
+    ("knn", "the first candidate of every cloud skipped",
+     "for (int64_t j = first2[i]; j < first2[i] + len2[i]; ++j) {",
+     "for (int64_t j = first2[i] + 1; j < first2[i] + len2[i]; ++j) {"),
+    ("knn", "the kept list sorted in descending order",
+     "while (pos > 0 && ranks_before(d, j, od[pos - 1], oi[pos - 1])) {",
+     "while (pos > 0 && ranks_before(od[pos - 1], oi[pos - 1], d, j)) {"),
+]
+
+
+def _run_pins(target, lib_path):
+    _, env_name, tests = TARGETS[target]
+    env = dict(os.environ, **{env_name: lib_path})
+    r = subprocess.run([sys.executable, "-m", "pytest", *tests, "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return r.returncode, r.stdout[-2000:]
+
+
+def _build_variant(target, tmp_path, old=None, new=None):
+    src_name = TARGETS[target][0]
+    text = open(os.path.join(ORACLE, src_name)).read()
+    if old is not None:
+        assert text.count(old) == 1, "mutation site not found exactly once: %r" % old
+        text = text.replace(old, new)
+    return oracle.compile_source(text, str(tmp_path / ("lib_%s.so" % target)))
+
+
+@pytest.mark.parametrize("target", sorted(TARGETS))
+def test_control_copy_passes_its_pins(target, tmp_path):
+    rc, out = _run_pins(target, _build_variant(target, tmp_path))
+    assert rc == 0, out
+
+
+@pytest.mark.parametrize("target,what,old,new", MUTATIONS, ids=[m[1] for m in MUTATIONS])
+def test_planted_mistake_fails_a_pin(target, what, old, new, tmp_path):
+    rc, out = _run_pins(target, _build_variant(target, tmp_path, old, new))
+    assert rc == 1, "the pins did not catch: %s\n%s" % (what, out)
