@@ -225,7 +225,7 @@ __device__ __forceinline__ void take1(NnList<KM> &L, float &thr, float d, int j)
 }
 
 template <int D, int KM, int QB>
-__global__ void __launch_bounds__(kThreads, KM <= 2 ? 4 : (KM <= 8 ? 3 : 2)) k_knn(KnnArgs a) {
+__global__ void __launch_bounds__(kThreads, KM <= 2 ? 4 : 3) k_knn(KnnArgs a) {
     const int pb = (a.nprob > 1 && (int)blockIdx.x >= a.pr[1].block0) ? 1 : 0;
     const KnnProblem &P = a.pr[pb];
     const long long b = (long long)blockIdx.x - P.block0;
@@ -361,6 +361,123 @@ __global__ void __launch_bounds__(kThreads, KM <= 2 ? 4 : (KM <= 8 ? 3 : 2)) k_k
             P.idx[row[u] * K + r] = has ? c0 + L[u].f[k] : -1;
             P.dists[row[u] * K + r] = has ? L[u].z[k] : __int_as_float(0x7f800000);
         }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// K >= 5: one query per lane, every lane of a warp scanning the same
+// candidates; an admitted candidate is inserted by the whole warp into its
+// query's list in shared memory (lane k holds entry k; the lanes before the
+// new key keep theirs, the others shift by one), one admission at a time, so
+// that no lane idles through another lane's K-step insertion.  Keys pack the
+// fp32 distance bits (non-negative, so ordered as integers) above the local
+// candidate row: comparing keys is the (distance, row) ranking.
+// ---------------------------------------------------------------------------
+constexpr unsigned long long kEmptyKey = 0x7f800000ffffffffull;   // (+inf, no row)
+
+template <int KM>
+__device__ __forceinline__ void coop_admit(unsigned long long *W, unsigned pend, const float (&c)[4], int j0, int K,
+                                           float &thr) {
+    const int lane = threadIdx.x & 31;
+    while (pend) {
+        const int src = __ffs(pend) - 1;
+        pend &= pend - 1;
+        float th = __shfl_sync(0xffffffffu, thr, src);
+        unsigned long long *Lq = W + src * KM;
+#pragma unroll
+        for (int h = 0; h < 4; ++h) {
+            const float d = __shfl_sync(0xffffffffu, c[h], src);
+            if (!(d < th)) continue;   // uniform: d and th are the source lane's
+            const unsigned long long key = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned)(j0 + h);
+            const unsigned long long e = lane < K ? Lq[lane] : kEmptyKey;
+            const int pos = __popc(__ballot_sync(0xffffffffu, lane < K && e < key));
+            const unsigned long long prev = __shfl_up_sync(0xffffffffu, e, 1);
+            const unsigned long long ne = lane < pos ? e : (lane == pos ? key : prev);
+            if (lane < K) Lq[lane] = ne;
+            th = __uint_as_float((unsigned)(__shfl_sync(0xffffffffu, ne, K - 1) >> 32));
+            __syncwarp();
+        }
+        if (lane == src) thr = th;
+    }
+}
+
+template <int D, int KM>
+__global__ void __launch_bounds__(kThreads, KM <= 16 ? 3 : 2) k_knn_coop(KnnArgs a) {
+    const int pb = (a.nprob > 1 && (int)blockIdx.x >= a.pr[1].block0) ? 1 : 0;
+    const KnnProblem &P = a.pr[pb];
+    const long long b = (long long)blockIdx.x - P.block0;
+    const long long total = P.tiles[P.N];
+    if (b >= total) return;   // uniform for the block, before any barrier
+    int lo = 0, hi = P.N;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (P.tiles[mid] <= b) lo = mid; else hi = mid;
+    }
+    const int ci = lo;
+    const long long t = b - P.tiles[ci];
+    const int K = P.K;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const long long row = P.first1[ci] + t * P.qpb + threadIdx.x;
+    const bool valid = row < P.first1[ci] + P.len1[ci];
+    const long long c0 = P.first2[ci];
+    const int cn = (int)P.len2[ci];
+    unsigned long long qq[D];
+#pragma unroll
+    for (int c = 0; c < D; ++c) qq[c] = f2_dup(valid ? P.p1[row * D + c] : 0.f);
+
+    extern __shared__ unsigned long long s_lists[];   // [warp][query lane][KM]
+    unsigned long long *W = s_lists + (size_t)warp * 32 * KM;
+    for (int e = lane; e < 32 * KM; e += 32) W[e] = kEmptyKey;
+    __syncwarp();
+    float thr = valid ? __int_as_float(0x7f800000) : __int_as_float(0xff800000);   // a lane without a query admits nothing
+
+    __shared__ __align__(16) float4 SA[kChunk / 2 + 1];
+    __shared__ __align__(16) float4 SB[D > 2 ? kChunk / 2 + 1 : 1];
+    for (int base = 0; base < cn; base += kChunk) {
+        const int cnt = min(kChunk, cn - base);
+        __syncthreads();   // the previous chunk is consumed
+        const float *src = P.p2 + (c0 + base) * D;
+        const int npair = (cnt + 1) >> 1;
+#pragma unroll 1
+        for (int pp = threadIdx.x; pp < npair; pp += kThreads) {
+            float v0[4] = {0.f, 0.f, 0.f, 0.f}, v1[4] = {0.f, 0.f, 0.f, 0.f};
+            const bool two = 2 * pp + 1 < cnt;
+#pragma unroll
+            for (int c = 0; c < D; ++c) {
+                v0[c] = src[2 * pp * D + c];
+                v1[c] = two ? src[(2 * pp + 1) * D + c] : (c == 0 ? __int_as_float(0x7f800000) : 0.f);
+            }
+            SA[pp] = make_float4(v0[0], v1[0], v0[1], v1[1]);
+            if (D > 2) SB[pp] = make_float4(v0[2], v1[2], v0[3], v1[3]);
+        }
+        __syncthreads();
+        int jp = 0;
+        for (; jp + 1 < npair; jp += 2) {   // uniform: every lane takes the same candidates
+            const PairCoords<D> X = load_pair<D>(SA, SB, jp);
+            const PairCoords<D> Y = load_pair<D>(SA, SB, jp + 1);
+            float c[4];
+            pair_dist<D>(qq, X, c[0], c[1]);
+            pair_dist<D>(qq, Y, c[2], c[3]);
+            const unsigned pend = __ballot_sync(0xffffffffu, fminf(fminf(c[0], c[1]), fminf(c[2], c[3])) < thr);
+            if (pend) coop_admit<KM>(W, pend, c, base + 2 * jp, K, thr);
+        }
+        if (jp < npair) {
+            const PairCoords<D> X = load_pair<D>(SA, SB, jp);
+            float c[4];
+            pair_dist<D>(qq, X, c[0], c[1]);
+            c[2] = c[3] = __int_as_float(0x7f800000);
+            const unsigned pend = __ballot_sync(0xffffffffu, fminf(c[0], c[1]) < thr);
+            if (pend) coop_admit<KM>(W, pend, c, base + 2 * jp, K, thr);
+        }
+    }
+    __syncwarp();
+    if (!valid) return;
+    const unsigned long long *Lq = W + lane * KM;
+    for (int k = 0; k < K; ++k) {
+        const unsigned long long key = Lq[k];
+        const bool has = key != kEmptyKey;
+        P.idx[row * K + k] = has ? c0 + (long long)(unsigned)(key & 0xffffffffull) : -1;
+        P.dists[row * K + k] = has ? __uint_as_float((unsigned)(key >> 32)) : __int_as_float(0x7f800000);
     }
 }
 
@@ -546,7 +663,8 @@ int km_for_knn(int K) {
     while (km < K) km <<= 1;
     return km;
 }
-int qb_for(int km) { return km <= 2 ? 4 : (km <= 8 ? 2 : 1); }
+int qb_for(int km) { return km <= 2 ? 4 : (km <= 4 ? 2 : 1); }
+bool coop_for(int km) { return km >= 8; }   // K >= 5: warp-cooperative insertion, one query per lane
 
 // lanes per query group: enough threads to fill the GPU twice over, but at
 // least 256 candidates per lane on average
@@ -559,8 +677,18 @@ int group_for(long long P1, long long P2, long long N, int qb) {
 }
 
 template <int D, int KM>
+cudaError_t launch_knn_coop(const KnnArgs &a, int blocks, cudaStream_t st) {
+    auto kern = k_knn_coop<D, KM>;
+    const int dyn = kThreads * KM * (int)sizeof(unsigned long long);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    kern<<<blocks, kThreads, dyn, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int D, int KM>
 cudaError_t launch_knn_t(const KnnArgs &a, int blocks, cudaStream_t st) {
-    constexpr int QB = KM <= 2 ? 4 : (KM <= 8 ? 2 : 1);
+    constexpr int QB = KM <= 2 ? 4 : (KM <= 4 ? 2 : 1);
     auto kern = k_knn<D, KM, QB>;
     // shared memory for four 33 KB blocks per SM
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
@@ -574,9 +702,9 @@ cudaError_t launch_knn_d(const KnnArgs &a, int km, int blocks, cudaStream_t st) 
         case 1: return launch_knn_t<D, 1>(a, blocks, st);
         case 2: return launch_knn_t<D, 2>(a, blocks, st);
         case 4: return launch_knn_t<D, 4>(a, blocks, st);
-        case 8: return launch_knn_t<D, 8>(a, blocks, st);
-        case 16: return launch_knn_t<D, 16>(a, blocks, st);
-        default: return launch_knn_t<D, 32>(a, blocks, st);
+        case 8: return launch_knn_coop<D, 8>(a, blocks, st);
+        case 16: return launch_knn_coop<D, 16>(a, blocks, st);
+        default: return launch_knn_coop<D, 32>(a, blocks, st);
     }
 }
 
@@ -611,7 +739,7 @@ long long set_problem(KnnProblem &pr, const float *p1, int64_t P1, const int64_t
     pr.tiles = tiles;
     pr.N = (int)N;
     pr.K = K;
-    pr.G = group_for(P1, P2, N, qb);
+    pr.G = coop_for(km) ? 1 : group_for(P1, P2, N, qb);
     pr.qpb = kThreads / pr.G * qb;
     pr.block0 = block0;
     return (P1 + pr.qpb - 1) / pr.qpb + N;
