@@ -365,8 +365,8 @@ __global__ void __launch_bounds__(kThreads, KM <= 2 ? 4 : 3) k_knn(KnnArgs a) {
 }
 
 // ---------------------------------------------------------------------------
-// K >= 5: one query per lane, every lane of a warp scanning the same
-// candidates; an admitted candidate is inserted by the whole warp into its
+// K >= 5: QB queries per lane (2, or 1 for K > 8), every lane of a warp
+// scanning the same candidates; an admitted candidate is inserted by the whole warp into its
 // query's list in shared memory (lane k holds entry k; the lanes before the
 // new key keep theirs, the others shift by one), one admission at a time, so
 // that no lane idles through another lane's K-step insertion.  Keys pack the
@@ -401,7 +401,7 @@ __device__ __forceinline__ void coop_admit(unsigned long long *W, unsigned pend,
     }
 }
 
-template <int D, int KM>
+template <int D, int KM, int QB>
 __global__ void __launch_bounds__(kThreads, KM <= 16 ? 3 : 2) k_knn_coop(KnnArgs a) {
     const int pb = (a.nprob > 1 && (int)blockIdx.x >= a.pr[1].block0) ? 1 : 0;
     const KnnProblem &P = a.pr[pb];
@@ -417,19 +417,28 @@ __global__ void __launch_bounds__(kThreads, KM <= 16 ? 3 : 2) k_knn_coop(KnnArgs
     const long long t = b - P.tiles[ci];
     const int K = P.K;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const long long row = P.first1[ci] + t * P.qpb + threadIdx.x;
-    const bool valid = row < P.first1[ci] + P.len1[ci];
+    const long long qend = P.first1[ci] + P.len1[ci];
     const long long c0 = P.first2[ci];
     const int cn = (int)P.len2[ci];
-    unsigned long long qq[D];
+    // QB queries per lane: query u of the block's tile is row base + u * 256 + thread
+    unsigned long long qq[QB][D];
+    long long row[QB];
+    bool valid[QB];
+    float thr[QB];
 #pragma unroll
-    for (int c = 0; c < D; ++c) qq[c] = f2_dup(valid ? P.p1[row * D + c] : 0.f);
+    for (int u = 0; u < QB; ++u) {
+        row[u] = P.first1[ci] + t * P.qpb + u * kThreads + threadIdx.x;
+        valid[u] = row[u] < qend;
+#pragma unroll
+        for (int c = 0; c < D; ++c) qq[u][c] = f2_dup(valid[u] ? P.p1[row[u] * D + c] : 0.f);
+        // a lane without a query admits nothing
+        thr[u] = valid[u] ? __int_as_float(0x7f800000) : __int_as_float(0xff800000);
+    }
 
-    extern __shared__ unsigned long long s_lists[];   // [warp][query lane][KM]
-    unsigned long long *W = s_lists + (size_t)warp * 32 * KM;
-    for (int e = lane; e < 32 * KM; e += 32) W[e] = kEmptyKey;
+    extern __shared__ unsigned long long s_lists[];   // [warp][u][query lane][KM]
+    unsigned long long *W = s_lists + (size_t)warp * QB * 32 * KM;
+    for (int e = lane; e < QB * 32 * KM; e += 32) W[e] = kEmptyKey;
     __syncwarp();
-    float thr = valid ? __int_as_float(0x7f800000) : __int_as_float(0xff800000);   // a lane without a query admits nothing
 
     __shared__ __align__(16) float4 SA[kChunk / 2 + 1];
     __shared__ __align__(16) float4 SB[D > 2 ? kChunk / 2 + 1 : 1];
@@ -455,29 +464,39 @@ __global__ void __launch_bounds__(kThreads, KM <= 16 ? 3 : 2) k_knn_coop(KnnArgs
         for (; jp + 1 < npair; jp += 2) {   // uniform: every lane takes the same candidates
             const PairCoords<D> X = load_pair<D>(SA, SB, jp);
             const PairCoords<D> Y = load_pair<D>(SA, SB, jp + 1);
-            float c[4];
-            pair_dist<D>(qq, X, c[0], c[1]);
-            pair_dist<D>(qq, Y, c[2], c[3]);
-            const unsigned pend = __ballot_sync(0xffffffffu, fminf(fminf(c[0], c[1]), fminf(c[2], c[3])) < thr);
-            if (pend) coop_admit<KM>(W, pend, c, base + 2 * jp, K, thr);
+#pragma unroll
+            for (int u = 0; u < QB; ++u) {
+                float c[4];
+                pair_dist<D>(qq[u], X, c[0], c[1]);
+                pair_dist<D>(qq[u], Y, c[2], c[3]);
+                const unsigned pend =
+                    __ballot_sync(0xffffffffu, fminf(fminf(c[0], c[1]), fminf(c[2], c[3])) < thr[u]);
+                if (pend) coop_admit<KM>(W + u * 32 * KM, pend, c, base + 2 * jp, K, thr[u]);
+            }
         }
         if (jp < npair) {
             const PairCoords<D> X = load_pair<D>(SA, SB, jp);
-            float c[4];
-            pair_dist<D>(qq, X, c[0], c[1]);
-            c[2] = c[3] = __int_as_float(0x7f800000);
-            const unsigned pend = __ballot_sync(0xffffffffu, fminf(c[0], c[1]) < thr);
-            if (pend) coop_admit<KM>(W, pend, c, base + 2 * jp, K, thr);
+#pragma unroll
+            for (int u = 0; u < QB; ++u) {
+                float c[4];
+                pair_dist<D>(qq[u], X, c[0], c[1]);
+                c[2] = c[3] = __int_as_float(0x7f800000);
+                const unsigned pend = __ballot_sync(0xffffffffu, fminf(c[0], c[1]) < thr[u]);
+                if (pend) coop_admit<KM>(W + u * 32 * KM, pend, c, base + 2 * jp, K, thr[u]);
+            }
         }
     }
     __syncwarp();
-    if (!valid) return;
-    const unsigned long long *Lq = W + lane * KM;
-    for (int k = 0; k < K; ++k) {
-        const unsigned long long key = Lq[k];
-        const bool has = key != kEmptyKey;
-        P.idx[row * K + k] = has ? c0 + (long long)(unsigned)(key & 0xffffffffull) : -1;
-        P.dists[row * K + k] = has ? __uint_as_float((unsigned)(key >> 32)) : __int_as_float(0x7f800000);
+#pragma unroll
+    for (int u = 0; u < QB; ++u) {
+        if (!valid[u]) continue;
+        const unsigned long long *Lq = W + (u * 32 + lane) * KM;
+        for (int k = 0; k < K; ++k) {
+            const unsigned long long key = Lq[k];
+            const bool has = key != kEmptyKey;
+            P.idx[row[u] * K + k] = has ? c0 + (long long)(unsigned)(key & 0xffffffffull) : -1;
+            P.dists[row[u] * K + k] = has ? __uint_as_float((unsigned)(key >> 32)) : __int_as_float(0x7f800000);
+        }
     }
 }
 
@@ -663,8 +682,8 @@ int km_for_knn(int K) {
     while (km < K) km <<= 1;
     return km;
 }
-int qb_for(int km) { return km <= 2 ? 4 : (km <= 4 ? 2 : 1); }
-bool coop_for(int km) { return km >= 8; }   // K >= 5: warp-cooperative insertion, one query per lane
+int qb_for(int km) { return km <= 2 ? 4 : (km <= 8 ? 2 : 1); }
+bool coop_for(int km) { return km >= 8; }   // K >= 5: warp-cooperative insertion into shared-memory lists
 
 // lanes per query group: enough threads to fill the GPU twice over, but at
 // least 256 candidates per lane on average
@@ -678,8 +697,9 @@ int group_for(long long P1, long long P2, long long N, int qb) {
 
 template <int D, int KM>
 cudaError_t launch_knn_coop(const KnnArgs &a, int blocks, cudaStream_t st) {
-    auto kern = k_knn_coop<D, KM>;
-    const int dyn = kThreads * KM * (int)sizeof(unsigned long long);
+    constexpr int QB = KM <= 8 ? 2 : 1;
+    auto kern = k_knn_coop<D, KM, QB>;
+    const int dyn = QB * kThreads * KM * (int)sizeof(unsigned long long);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     kern<<<blocks, kThreads, dyn, st>>>(a);
