@@ -6,15 +6,20 @@
 //   k_knn_plan   one block per problem: tiles per cloud (ceil(len1 / queries
 //                per block)) and their exclusive prefix, so that one launch
 //                covers a heterogeneous batch without a host round trip
-//   k_knn<D,KM,QB>  one block per tile of queries of one cloud: the cloud's
-//                candidates pass through shared memory in chunks (pairs of
-//                candidates interleaved by coordinate); a group of G consecutive lanes shares QB
-//                queries and splits the candidates among its lanes; distances
-//                of two candidates at a time in packed f32x2 arithmetic (two
-//                lanes of fp32 per instruction, each rounded as plain fp32);
-//                register top-K per query (K of KM slots); the group's lists
-//                merge through warp shuffles.  Two problems (both directions
-//                of a Chamfer loss) can share one launch.
+//   k_knn<D,KM,QB>  (K <= 4) one block per tile of queries of one cloud: the
+//                cloud's candidates pass through shared memory in chunks
+//                (pairs of candidates interleaved by coordinate); a group of
+//                G consecutive lanes shares QB queries and splits the
+//                candidates among its lanes; distances of two candidates at a
+//                time in packed f32x2 arithmetic (two lanes of fp32 per
+//                instruction, each rounded as plain fp32); register top-K per
+//                query (K of KM slots); the group's lists merge through warp
+//                shuffles.  Two problems (both directions of a Chamfer loss)
+//                can share one launch.
+//   k_knn_coop<D,KM,QB>  (K >= 5) the same scan with every lane of a warp on
+//                the same candidates for its own queries; the lists live in
+//                shared memory and each admitted candidate is inserted by the
+//                whole warp (a ballot ranks it, later entries shift a lane)
 //   k_pair_sums / k_mean   per-pair Chamfer terms and the batch mean, fixed
 //                reduction order
 //   k_chamfer_bwd / k_knn_bwd   gradients, scatter to the neighbours with
