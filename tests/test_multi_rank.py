@@ -1,8 +1,9 @@
 """Replica runs under torch.distributed, on CPU (gloo, world size 2, 127.0.0.1):
 the benchmark's host logic for N > 1 -- the timed region ends with the
 slowest rank, the rate counts every rank's units -- and the reference arm's
-rank discipline (rank 0 alone works and prints).  The path itself has no
-collective: each rank renders its own copy of the batch."""
+rank discipline (rank 0 alone works and prints one JSON line of the
+benchmark's shape).  The path itself has no collective: each rank renders
+its own copy of the batch."""
 import os
 import socket
 import subprocess
@@ -69,3 +70,18 @@ def test_reference_arm_runs_on_rank_zero_only():
                         "--warmup", "0"], env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+@pytest.mark.parametrize("workload", ["1", "knn"])
+def test_reference_arm_prints_one_json_line(workload):
+    import json
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", workload,
+                        "--steps", "1", "--warmup", "0"], env=dict(os.environ, RANK="0", WORLD_SIZE="1"),
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] and d["higher_is_better"] is True
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
