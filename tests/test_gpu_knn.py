@@ -180,6 +180,7 @@ def test_chamfer_autograd_matches_the_direct_calls():
     loss, per = ag.chamfer_distance(P, _T(f1), _T(l1), Q, _T(f2), _T(l2))
     (2.0 * loss + (per * _T(np.array([0.5, -1.0], np.float32))).sum()).backward()
     r = _gpu_chamfer(p, f1, l1, q, f2, l2, g_per=[0.5, -1.0], g_loss=2.0)
-    assert torch.allclose(P.grad, _T(r["gp"]), rtol=1e-6, atol=1e-9)
-    assert torch.allclose(Q.grad, _T(r["gq"]), rtol=1e-6, atol=1e-9)
+    # the same kernels both ways; the float atomics may add in another order
+    for got, want in ((P.grad, _T(r["gp"])), (Q.grad, _T(r["gq"]))):
+        assert torch.linalg.norm(got - want) <= 1e-6 * torch.linalg.norm(want)
     assert float(loss) == pytest.approx(float(r["loss"][0]), rel=1e-7)

@@ -181,5 +181,6 @@ def test_render_points_autograd_equals_the_calls():
     ops.pts_composite_bwd(p, ops.PTS_ALPHA, idx, di, d["feats"], g, gd, gf)
     gp = torch.empty_like(d["points"])
     ops.pts_rasterize_bwd(p, d["points"], d["first"], d["num"], d["cams"], idx, None, gd, gp, ws)
-    assert torch.allclose(feats.grad, gf, rtol=1e-5, atol=1e-6)
-    assert torch.allclose(pts.grad, gp, rtol=1e-4, atol=1e-4 * gp.abs().max().item())
+    # the same kernels both ways; the float atomics may add in another order
+    assert torch.linalg.norm(feats.grad - gf) <= 1e-5 * torch.linalg.norm(gf)
+    assert torch.linalg.norm(pts.grad - gp) <= 1e-5 * torch.linalg.norm(gp)
