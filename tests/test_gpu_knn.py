@@ -59,7 +59,8 @@ def test_knn_heterogeneous_batch_bit_exact(D, K):
 
 @pytest.mark.parametrize("K", [1, 8, 32])
 def test_knn_few_queries_many_candidates(K):
-    # 32 lanes share each query (wide groups) and merge their lists
+    # K = 1: 32 lanes share each query (wide groups) and merge their lists;
+    # K >= 5: every lane on its own queries, lists inserted into by the warp
     rng = np.random.default_rng(K)
     p1, f1, l1 = _batch(rng, [40, 33], 3)
     p2, f2, l2 = _batch(rng, [40_000, 41_111], 3)
