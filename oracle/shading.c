@@ -91,10 +91,13 @@ static void ors_phi(const ors_light *Lt, const double *E, const double *x, const
 }
 
 /* Shaded colour of slot s (face f, barycentrics b) and, with g != NULL, the
- * adjoint: gb (3), and per corner gP[9], gN[9], gA[9] (accumulated). */
+ * adjoint: gb (3), and per corner gP[9], gN[9], gA[9] (accumulated).  agb
+ * (3, may be NULL) accumulates the magnitudes of the terms that form gb (an
+ * fp32 evaluation of gb carries rounding of that size). */
 static void ors_slot_colour(int shading, const ors_light *Lt, const double *E, const double *verts,
                             const double *normals, const double *colors, const int64_t *fv, const double *b,
-                            double out[3], const double *g, double *gb, double *gP, double *gN, double *gA) {
+                            double out[3], const double *g, double *gb, double *gP, double *gN, double *gA,
+                            double *agb) {
     const double *P[3], *Nn[3], *A[3];
     for (int i = 0; i < 3; i++) { P[i] = verts + 3 * fv[i]; Nn[i] = normals + 3 * fv[i]; A[i] = colors + 3 * fv[i]; }
     if (shading == 1) {  /* Gouraud */
@@ -105,6 +108,7 @@ static void ors_slot_colour(int shading, const ors_light *Lt, const double *E, c
             ors_phi(Lt, E, P[i], Nn[i], A[i], phi, g ? gi : NULL, gP + 3 * i, gN + 3 * i, gA + 3 * i);
             for (int ch = 0; ch < 3; ch++) out[ch] += b[i] * phi[ch];
             if (g) gb[i] += dot3(g, phi);
+            if (g && agb) agb[i] += fabs(dot3(g, phi));
         }
         return;
     }
@@ -129,11 +133,13 @@ static void ors_slot_colour(int shading, const ors_light *Lt, const double *E, c
     ors_phi(Lt, E, x, n, a, out, g, gx, gn, ga);
     for (int i = 0; i < 3; i++) {
         gb[i] += dot3(gx, P[i]) + dot3(ga, A[i]);
+        if (agb) agb[i] += fabs(dot3(gx, P[i])) + fabs(dot3(ga, A[i]));
         for (int j = 0; j < 3; j++) { gP[3 * i + j] += b[i] * gx[j]; gA[3 * i + j] += b[i] * ga[j]; }
     }
     if (shading == 2) {
         for (int i = 0; i < 3; i++) {
             gb[i] += dot3(gn, Nn[i]);
+            if (agb) agb[i] += fabs(dot3(gn, Nn[i]));
             for (int j = 0; j < 3; j++) gN[3 * i + j] += b[i] * gn[j];
         }
     } else {
@@ -171,7 +177,7 @@ int ors_shade_fwd(int64_t npix, int64_t K, const int64_t *image, const int64_t *
                 o[0] = bg[0]; o[1] = bg[1]; o[2] = bg[2]; o[3] = 0.0;
             } else {
                 ors_slot_colour(shading, &Lt, E, verts, normals, colors, faces + 3 * f, bary + 3 * p * K, o,
-                                NULL, NULL, NULL, NULL, NULL);
+                                NULL, NULL, NULL, NULL, NULL, NULL);
                 o[3] = 1.0;
             }
             continue;
@@ -192,7 +198,7 @@ int ors_shade_fwd(int64_t npix, int64_t K, const int64_t *image, const int64_t *
             const double w = ors_sigmoid(-dists[s] / sigma) * exp(((zfar - zbuf[s]) / (zfar - znear) - zmax) / gamma);
             double c[3];
             ors_slot_colour(shading, &Lt, E, verts, normals, colors, faces + 3 * f, bary + 3 * s, c, NULL, NULL,
-                            NULL, NULL, NULL);
+                            NULL, NULL, NULL, NULL);
             for (int ch = 0; ch < 3; ch++) num[ch] += w * c[ch];
             den += w;
         }
@@ -231,7 +237,7 @@ int ors_shade_bwd(int64_t npix, int64_t K, const int64_t *image, const int64_t *
                   const double *normals, const double *colors, const double *cams, const double *light,
                   const double *blend, int shading, int blend_mode, const double *grad_rgba, double *grad_zbuf,
                   double *grad_bary, double *grad_dists, double *grad_verts, double *grad_normals,
-                  double *grad_colors, double *abs_vnc, int64_t V) {
+                  double *grad_colors, double *abs_vnc, int64_t V, double *abs_bary) {
     ors_light Lt;
     ors_unpack(light, &Lt);
     const double sigma = blend[0], gamma = blend[1], znear = blend[2], zfar = blend[3], eps = blend[4];
@@ -239,6 +245,7 @@ int ors_shade_bwd(int64_t npix, int64_t K, const int64_t *image, const int64_t *
     for (int64_t s = 0; s < npix * K; s++) {
         grad_zbuf[s] = grad_dists[s] = 0.0;
         grad_bary[3 * s] = grad_bary[3 * s + 1] = grad_bary[3 * s + 2] = 0.0;
+        if (abs_bary) abs_bary[3 * s] = abs_bary[3 * s + 1] = abs_bary[3 * s + 2] = 0.0;
     }
     for (int64_t p = 0; p < npix; p++) {
         const double *E = cams + 16 * image[p] + 9;
@@ -250,7 +257,7 @@ int ors_shade_bwd(int64_t npix, int64_t K, const int64_t *image, const int64_t *
             if (f < 0) continue;
             double c[3], gP[9] = {0}, gN[9] = {0}, gA[9] = {0};
             ors_slot_colour(shading, &Lt, E, verts, normals, colors, faces + 3 * f, bary + 3 * p * K, c, g,
-                            grad_bary + 3 * p * K, gP, gN, gA);
+                            grad_bary + 3 * p * K, gP, gN, gA, abs_bary ? abs_bary + 3 * p * K : NULL);
             ors_scatter(faces + 3 * f, gP, gN, gA, grad_verts, grad_normals, grad_colors, abs_vnc, V);
             continue;
         }
@@ -270,7 +277,7 @@ int ors_shade_bwd(int64_t npix, int64_t K, const int64_t *image, const int64_t *
             if (f < 0) continue;
             wts[k] = ors_sigmoid(-dists[s] / sigma) * exp(((zfar - zbuf[s]) / (zfar - znear) - zmax) / gamma);
             ors_slot_colour(shading, &Lt, E, verts, normals, colors, faces + 3 * f, bary + 3 * s, cols + 3 * k,
-                            NULL, NULL, NULL, NULL, NULL);
+                            NULL, NULL, NULL, NULL, NULL, NULL);
             for (int ch = 0; ch < 3; ch++) num[ch] += wts[k] * cols[3 * k + ch];
             den += wts[k];
         }
@@ -294,7 +301,7 @@ int ors_shade_bwd(int64_t npix, int64_t K, const int64_t *image, const int64_t *
             for (int ch = 0; ch < 3; ch++) gc_all[3 * k + ch] = g[ch] * wts[k] / D;
             double c[3], gP[9] = {0}, gN[9] = {0}, gA[9] = {0};
             ors_slot_colour(shading, &Lt, E, verts, normals, colors, faces + 3 * f, bary + 3 * s, c, gc_all + 3 * k,
-                            grad_bary + 3 * s, gP, gN, gA);
+                            grad_bary + 3 * s, gP, gN, gA, abs_bary ? abs_bary + 3 * s : NULL);
             ors_scatter(faces + 3 * f, gP, gN, gA, grad_verts, grad_normals, grad_colors, abs_vnc, V);
         }
     }

@@ -43,7 +43,7 @@ def _load():
         common = [_i64, _i64, _i64p, _i64p, _f64p, _f64p, _f64p, _i64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p,
                   _int, _int]
         L.ors_shade_fwd.argtypes = common + [_f64p]
-        L.ors_shade_bwd.argtypes = common + [_f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _i64]
+        L.ors_shade_bwd.argtypes = common + [_f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _f64p, _i64, _f64p]
         L.ors_shade_margins.argtypes = [_i64, _i64, _i64p, _i64p, _f64p, _i64p, _f64p, _f64p, _f64p, _f64p, _int,
                                         _int, _f64p]
         _lib = L
@@ -88,9 +88,10 @@ def shade_fwd(image, p2f, zbuf, bary, dists, faces, verts, normals, colors, cams
 
 
 def shade_bwd(image, p2f, zbuf, bary, dists, faces, verts, normals, colors, cams, light, blend, shading, grad_rgba,
-              blend_mode=SOFTMAX, with_abs=False):
-    """(grad_zbuf, grad_bary, grad_dists, grad_verts (direct), grad_normals, grad_colors[, abs]) where abs
-    (3, V, 3) holds the magnitudes of the per-slot contributions to the last three."""
+              blend_mode=SOFTMAX, with_abs=False, with_abs_bary=False):
+    """(grad_zbuf, grad_bary, grad_dists, grad_verts (direct), grad_normals, grad_colors[, abs][, abs_bary])
+    where abs (3, V, 3) holds the magnitudes of the per-slot contributions to the last three and
+    abs_bary (npix, K, 3) the magnitudes of the terms that form each grad_bary component."""
     npix, K, arrs, ptrs = _args(image, p2f, zbuf, bary, dists, faces, verts, normals, colors, cams, light, blend)
     V = arrs[6].shape[0]
     gz, gd = np.zeros((npix, K)), np.zeros((npix, K))
@@ -99,9 +100,15 @@ def shade_bwd(image, p2f, zbuf, bary, dists, faces, verts, normals, colors, cams
     g = _d(grad_rgba).reshape(npix, 4)
     P = lambda a: a.ctypes.data_as(_f64p)
     ab = np.zeros((3, V, 3))
+    abb = np.zeros((npix, K, 3))
     _load().ors_shade_bwd(npix, K, *ptrs, shading, blend_mode, P(g), P(gz), P(gb), P(gd), P(gv), P(gn), P(gc), P(ab),
-                          V)
-    return (gz, gb, gd, gv, gn, gc, ab) if with_abs else (gz, gb, gd, gv, gn, gc)
+                          V, P(abb))
+    out = (gz, gb, gd, gv, gn, gc)
+    if with_abs:
+        out += (ab,)
+    if with_abs_bary:
+        out += (abb,)
+    return out
 
 
 def shade_margins(image, p2f, bary, faces, verts, normals, cams, light, shading, blend_mode=SOFTMAX):

@@ -185,3 +185,23 @@ def test_chamfer_autograd_matches_the_direct_calls():
     for got, want in ((P.grad, _T(r["gp"])), (Q.grad, _T(r["gq"]))):
         assert torch.linalg.norm(got - want) <= 1e-6 * torch.linalg.norm(want)
     assert float(loss) == pytest.approx(float(r["loss"][0]), rel=1e-7)
+
+
+def test_chamfer_benchmark_batch_in_full():
+    # the benchmark's Chamfer batch (32 pairs of 1,000 and 50,000 points), every
+    # neighbour both ways bit-exact, per-pair losses and both gradients
+    w = workloads.knn_workload("chamfer")
+    c = w.pairs
+    N = c.N
+    rng = np.random.default_rng(w.grad_seed)
+    g_per = rng.normal(size=N)
+    r = _gpu_chamfer(c.p, c.first1, c.len1, c.q, c.first2, c.len2, g_per=g_per, g_loss=1.0)
+    loss, per, ipq, iqp = ok.chamfer(c.p, c.first1, c.len1, c.q, c.first2, c.len2)
+    np.testing.assert_array_equal(r["idx_pq"], ipq)
+    np.testing.assert_array_equal(r["idx_qp"], iqp)
+    assert np.all(np.abs(r["per"] - per) <= 1e-5 * np.abs(per)), np.max(np.abs(r["per"] - per) / np.abs(per))
+    assert abs(r["loss"][0] - loss) <= 1e-5 * abs(loss)
+    gp, gq = ok.chamfer_grad(c.p, c.first1, c.len1, c.q, c.first2, c.len2, ipq, iqp, g_per + 1.0 / N)
+    for name, a, ref in (("grad_p", r["gp"], gp), ("grad_q", r["gq"], gq)):
+        worst, glob = grad_close(a, ref)
+        assert glob <= 1e-4 and worst <= 1, (name, worst, glob)

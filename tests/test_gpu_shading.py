@@ -109,3 +109,54 @@ def test_shade_autograd_chains_into_the_rasterizer():
     # same kernels both ways; the float atomics may add in another order
     for got, want in ((v.grad, tot), (n.grad, gn), (c.grad, gc)):
         assert torch.linalg.norm(got - want) <= 1e-5 * torch.linalg.norm(want)
+
+
+@pytest.mark.parametrize("shading", [ops.SHADE_GOURAUD, ops.SHADE_PHONG])
+def test_benchmark_batch_sampled_pixels(shading):
+    # the shaded benchmark step at full size (8 x 5,120 faces, 256x256, K = 8,
+    # the bench's light), checked on 256 seeded pixels per image: image values
+    # and the per-slot fragment gradients (which depend on the pixel alone)
+    w = workloads.workload(1, "")
+    b = w.batch
+    d = to_dev(b)
+    S, K = w.image_size, w.K
+    fr, st, _, _ = gpu_fwd(d, S, K, float(np.float32(w.blur_radius)), 16, True, True)
+    assert st == 0
+    p2f, zb, ba, di = fr
+    N = b.N
+    nrm = torch.nn.functional.normalize(d["verts"], dim=1).contiguous()
+    col = torch.from_numpy(b.colors).cuda()
+    light = dict(light=(0.0, 3.0, -3.0), ambient=(0.3, 0.3, 0.3), diffuse=(0.6, 0.6, 0.6), specular=(0.3, 0.3, 0.3),
+                 shininess=32.0)
+    bp = ops.make_blend_params(w.sigma, w.gamma, w.znear, w.zfar, (1.0, 1.0, 1.0), 1e-10, ops.BLEND_RGB)
+    sp = ops.make_shade_params(shading=shading, blend=ops.SHADE_SOFTMAX, **light)
+    img = torch.empty((N, S, S, 4), device="cuda")
+    ops.shade_fwd(bp, sp, N, S, K, p2f, zb, ba, di, d["faces"], d["verts"], nrm, col, d["cams"], img)
+    g = torch.from_numpy(workloads.upstream_grad(N, S, w.grad_seed)).cuda()
+    gz, gb, gd = torch.empty_like(zb), torch.empty_like(ba), torch.empty_like(di)
+    gv, gn, gc = torch.empty_like(d["verts"]), torch.empty_like(nrm), torch.empty_like(col)
+    ops.shade_bwd(bp, sp, N, S, K, p2f, zb, ba, di, d["faces"], d["verts"], nrm, col, d["cams"], g, gz, gb, gd, gv, gn,
+                  gc)
+    px = workloads.sample_pixels(N, S, 256, 77)
+    flat = (px[:, 0] * S + px[:, 1]) * S + px[:, 2]
+    P = N * S * S
+    pick = lambda t, *tail: t.cpu().numpy().reshape(P, *tail)[flat]
+    f_p2f, f_zb, f_ba, f_di = pick(p2f, K), pick(zb, K), pick(ba, K, 3), pick(di, K)
+    normals = nrm.cpu().numpy()
+    lt = osh.light_params(*[np.float32(v) for v in (light["light"], light["ambient"], light["diffuse"],
+                                                    light["specular"])], shininess=light["shininess"])
+    bl = osh.blend_params(_f32(w.sigma), _f32(w.gamma), _f32(w.znear), _f32(w.zfar), _f32(1e-10))
+    args = [px[:, 0], f_p2f, f_zb, f_ba, f_di, b.faces, b.verts, normals, b.colors, b.cams, lt, bl, shading]
+    ref = osh.shade_fwd(*args, blend_mode=osh.SOFTMAX)
+    assert np.max(np.abs(pick(img, 4) - ref)) <= 1e-5
+    # per-slot gradients, away from the reflection model's kinks
+    gs = pick(g, 4)
+    mg = osh.shade_margins(px[:, 0], f_p2f, f_ba, b.faces, b.verts, normals, b.cams, lt, shading, osh.SOFTMAX)
+    keep = mg >= 1e-4
+    rz, rb, rd, _, _, _, abb = osh.shade_bwd(*args, gs, blend_mode=osh.SOFTMAX, with_abs_bary=True)
+    # barycentric gradients sum position, normal and colour terms: judged against their magnitudes
+    for name, a, r, sc in (("grad_bary", pick(gb, K, 3), rb, abb), ("grad_zbuf", pick(gz, K), rz, None),
+                           ("grad_dists", pick(gd, K), rd, None)):
+        worst, glob, n_over = grad_close(a[keep], r[keep], scale=None if sc is None else sc[keep], return_count=True)
+        assert glob <= 1e-4 and worst <= 10 and n_over <= max(3, 0.01 * r[keep].size), (name, worst, glob, n_over)
+    assert keep.mean() > 0.9

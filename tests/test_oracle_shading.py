@@ -127,7 +127,9 @@ def test_adjoint_matches_central_differences(mode, blend_mode):
     bl = sh.blend_params(sigma=1e-3, gamma=5e-3)
     g = rng.normal(size=(npix, 4))
     args = [img, p2f, zb, ba, di, faces, verts, normals, colors, cams, light, bl, mode]
-    gz, gb, gd, gv, gn, gc = sh.shade_bwd(*args, g, blend_mode=blend_mode)
+    gz, gb, gd, gv, gn, gc, abb = sh.shade_bwd(*args, g, blend_mode=blend_mode, with_abs_bary=True)
+    # the term magnitudes bound each barycentric gradient (triangle inequality)
+    assert (abb >= np.abs(gb) - 1e-15).all() and abb.max() > 0
 
     def L(**kw):
         a = dict(zip(["img", "p2f", "zb", "ba", "di", "faces", "verts", "normals", "colors"], args[:9]))
