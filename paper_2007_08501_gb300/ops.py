@@ -472,11 +472,29 @@ def _ws(workspace):
     return _ptr(workspace, None, "workspace"), workspace.numel() * workspace.element_size()
 
 
+def _need(t, n, name):
+    """The C ABI trusts the sizes it derives from the shapes: a tensor with
+    another element count is refused here (a NULL pointer is left to the call)."""
+    if t is not None and t.numel() != n:
+        raise MeshRastError("%s must hold %d elements, got %d" % (name, n, t.numel()))
+
+
+def _clouds(p, first, length, name):
+    if p.dim() != 2:
+        raise MeshRastError("%s must be (points, D)" % name)
+    _need(length, first.numel(), "the cloud lengths of " + name)
+
+
 def knn_points(p1, first1, len1, p2, first2, len2, K, idx, dists, workspace, stream=None):
     """idx (P1, K) int64 and dists (P1, K) float32 are written (global rows of p2)."""
     D = p1.shape[1]
     if p2.shape[1] != D:
         raise MeshRastError("p1 and p2 must have the same dimension")
+    _clouds(p1, first1, len1, "p1")
+    _clouds(p2, first2, len2, "p2")
+    _need(first2, first1.numel(), "first2")
+    _need(idx, p1.shape[0] * int(K), "idx")
+    _need(dists, p1.shape[0] * int(K), "dists")
     w, wb = _ws(workspace)
     rc = load().knn_points(_ptr(p1, torch.float32, "p1"), p1.shape[0], _ptr(first1, torch.int64, "first1"),
                            _ptr(len1, torch.int64, "len1"), _ptr(p2, torch.float32, "p2"), p2.shape[0],
@@ -487,6 +505,11 @@ def knn_points(p1, first1, len1, p2, first2, len2, K, idx, dists, workspace, str
 
 
 def knn_points_bwd(p1, p2, idx, grad_dists, grad_p1, grad_p2, stream=None):
+    if idx.dim() != 2 or idx.shape[0] != p1.shape[0]:
+        raise MeshRastError("idx must be (P1, K)")
+    _need(grad_dists, idx.numel(), "grad_dists")
+    _need(grad_p1, p1.numel(), "grad_p1")
+    _need(grad_p2, p2.numel(), "grad_p2")
     rc = load().knn_points_bwd(_ptr(p1, torch.float32, "p1"), p1.shape[0], _ptr(p2, torch.float32, "p2"), p2.shape[0],
                                p1.shape[1], idx.shape[1], _ptr(idx, torch.int64, "idx"),
                                _ptr(grad_dists, torch.float32, "grad_dists"), _ptr(grad_p1, torch.float32, "grad_p1"),
@@ -499,6 +522,12 @@ def chamfer_fwd(p, first1, len1, q, first2, len2, idx_pq, d_pq, idx_qp, d_qp, lo
     D = p.shape[1]
     if q.shape[1] != D:
         raise MeshRastError("p and q must have the same dimension")
+    _clouds(p, first1, len1, "p")
+    _clouds(q, first2, len2, "q")
+    _need(first2, first1.numel(), "first2")
+    for t, n, name in ((idx_pq, p.shape[0], "idx_pq"), (d_pq, p.shape[0], "d_pq"), (idx_qp, q.shape[0], "idx_qp"),
+                       (d_qp, q.shape[0], "d_qp"), (loss_per_pair, first1.numel(), "loss_per_pair"), (loss, 1, "loss")):
+        _need(t, n, name)
     w, wb = _ws(workspace)
     rc = load().chamfer_fwd(_ptr(p, torch.float32, "p"), p.shape[0], _ptr(first1, torch.int64, "first1"),
                             _ptr(len1, torch.int64, "len1"), _ptr(q, torch.float32, "q"), q.shape[0],
@@ -512,6 +541,13 @@ def chamfer_fwd(p, first1, len1, q, first2, len2, idx_pq, d_pq, idx_qp, d_qp, lo
 
 def chamfer_bwd(p, first1, len1, q, first2, len2, idx_pq, idx_qp, grad_loss, grad_per_pair, grad_p, grad_q,
                 stream=None):
+    _clouds(p, first1, len1, "p")
+    _clouds(q, first2, len2, "q")
+    _need(first2, first1.numel(), "first2")
+    for t, n, name in ((idx_pq, p.shape[0], "idx_pq"), (idx_qp, q.shape[0], "idx_qp"), (grad_loss, 1, "grad_loss"),
+                       (grad_per_pair, first1.numel(), "grad_per_pair"), (grad_p, p.numel(), "grad_p"),
+                       (grad_q, q.numel(), "grad_q")):
+        _need(t, n, name)
     rc = load().chamfer_bwd(_ptr(p, torch.float32, "p"), p.shape[0], _ptr(first1, torch.int64, "first1"),
                             _ptr(len1, torch.int64, "len1"), _ptr(q, torch.float32, "q"), q.shape[0],
                             _ptr(first2, torch.int64, "first2"), _ptr(len2, torch.int64, "len2"), first1.shape[0],

@@ -109,3 +109,25 @@ def test_autotune_capacities_have_headroom():
     per_bin, entries = tune.capacities(218, 138191)
     assert per_bin % 64 == 0 and per_bin >= 218 * 1.25 and entries >= 138191 * 1.25
     assert tune.capacities(0, 0) == (64, 1024)
+
+
+def test_binding_refuses_mismatched_knn_tensors():
+    # the checks run before anything touches a device
+    import torch
+    from paper_2007_08501_gb300 import ops
+    p = torch.zeros(10, 3)
+    f, n = torch.zeros(2, dtype=torch.int64), torch.zeros(2, dtype=torch.int64)
+    cases = [
+        (lambda: ops.knn_points(p, f, n, p, f, n, 4, torch.zeros(10, 3, dtype=torch.int64), torch.zeros(10, 4), None),
+         "idx"),
+        (lambda: ops.knn_points(p, f, torch.zeros(3, dtype=torch.int64), p, f, n, 4, None, None, None), "lengths"),
+        (lambda: ops.knn_points(p, f, n, torch.zeros(10, 2), f, n, 4, None, None, None), "dimension"),
+        (lambda: ops.chamfer_fwd(p, f, n, p, f, n, None, None, None, None, torch.zeros(3), torch.zeros(1), None),
+         "loss_per_pair"),
+        (lambda: ops.chamfer_bwd(p, f, n, p, f, n, None, None, None, None, torch.zeros(9, 3), None), "grad_p"),
+        (lambda: ops.knn_points_bwd(p, p, torch.zeros(10, 2, dtype=torch.int64), torch.zeros(10, 3), None, None),
+         "grad_dists"),
+    ]
+    for call, what in cases:
+        with pytest.raises(ops.MeshRastError, match=what):
+            call()
