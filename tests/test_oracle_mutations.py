@@ -86,3 +86,49 @@ def test_control_copy_passes_its_pins(target, tmp_path):
 def test_planted_mistake_fails_a_pin(target, what, old, new, tmp_path):
     rc, out = _run_pins(target, _build_variant(target, tmp_path, old, new))
     assert rc == 1, "the pins did not catch: %s\n%s" % (what, out)
+
+
+# the numpy half of the nearest-neighbour oracle (Chamfer loss and gradients):
+# the mutant module is swapped in for the pin tests' oracle module in-process
+PY_MUTATIONS = [
+    ("the Chamfer distance taken as L1 instead of squared L2",
+     "np.sum((pts[rows] - other[nn[rows]]) ** 2) / n", "np.sum(np.abs(pts[rows] - other[nn[rows]])) / n"),
+    ("the Chamfer gradient without its factor 2",
+     "t = 2.0 * g / n * (pts[rows] - other[nn[rows]])", "t = g / n * (pts[rows] - other[nn[rows]])"),
+    ("the neighbour's Chamfer gradient with the wrong sign",
+     "np.add.at(go, nn[rows], -t)", "np.add.at(go, nn[rows], t)"),
+    ("the KNN distance gradient of the neighbour with the wrong sign",
+     "np.add.at(g2, idx[rows, k], -t)", "np.add.at(g2, idx[rows, k], t)"),
+]
+
+
+def _numpy_pins_failing(old, new, monkeypatch):
+    import types
+
+    import test_oracle_knn as pins
+    path = os.path.join(ORACLE, "knn.py")
+    text = open(path).read()
+    assert text.count(old) == 1, "mutation site not found exactly once: %r" % old
+    mutant = types.ModuleType("knn_mutant")
+    mutant.__file__ = path
+    exec(compile(text.replace(old, new), path, "exec"), mutant.__dict__)
+    monkeypatch.setattr(pins, "ok", mutant)
+    caught = 0
+    for test in (pins.test_chamfer_matches_the_pairwise_matrix_form, pins.test_chamfer_closed_forms,
+                 pins.test_chamfer_gradient_matches_central_differences,
+                 pins.test_knn_gradient_matches_central_differences):
+        try:
+            test()
+        except AssertionError:
+            caught += 1
+    return caught
+
+
+def test_numpy_oracle_control_copy_passes(monkeypatch):
+    old = PY_MUTATIONS[0][1]
+    assert _numpy_pins_failing(old, old, monkeypatch) == 0
+
+
+@pytest.mark.parametrize("what,old,new", PY_MUTATIONS, ids=[m[0] for m in PY_MUTATIONS])
+def test_planted_mistake_in_the_numpy_oracle_fails_a_pin(what, old, new, monkeypatch):
+    assert _numpy_pins_failing(old, new, monkeypatch) >= 1, "the pins did not catch: %s" % what
