@@ -177,6 +177,41 @@ def _stream(stream):
     return s.cuda_stream
 
 
+# The C ABI trusts the sizes it derives from the parameters and the leading
+# dimensions; a tensor too small for them is refused here instead of being
+# written past its end.
+def _atleast(t, n, name):
+    if t is not None and t.numel() < n:
+        raise MeshRastError("%s holds %d elements, the call needs %d" % (name, t.numel(), n))
+
+
+def _n(t):
+    return t.numel() if t is not None else 0
+
+
+def _rows_of(t, width, name):
+    if t is not None and (t.dim() != 2 or t.shape[1] != width):
+        raise MeshRastError("%s must be (rows, %d), got %s" % (name, width, tuple(t.shape)))
+
+
+def _batch_inputs(N, verts, faces, first, count, cams, vname="verts"):
+    _rows_of(verts, 3, vname)
+    _rows_of(faces, 3, "faces")
+    _atleast(first, N, "first index per image")
+    _atleast(count, N, "count per image")
+    _atleast(cams, 16 * N, "cams")
+
+
+def _slots(N, S, K, names_and_tensors):
+    slots = int(N) * int(S) * int(S) * int(K)
+    for name, t in names_and_tensors:
+        _atleast(t, 3 * slots if "bary" in name else slots, name)
+
+
+def _image(t, N, S, C, name):
+    _atleast(t, int(N) * int(S) * int(S) * int(C), name)
+
+
 def make_rast_params(N, image_size, K, blur_radius=0.0, bin_size=16, max_faces_per_bin=1024,
                      perspective_correct=True, clip_barycentric_coords=False, max_bin_entries=0):
     p = rast_params()
@@ -214,6 +249,9 @@ def rast_workspace_bytes(p: rast_params, V: int, F: int) -> int:
 
 def rast_mesh_fwd(p, verts, faces, first_face, num_faces, cams, pix_to_face, zbuf, bary, dists, workspace,
                   stream=None):
+    _batch_inputs(p.N, verts, faces, first_face, num_faces, cams)
+    _slots(p.N, p.image_size, p.faces_per_pixel,
+           (("pix_to_face", pix_to_face), ("zbuf", zbuf), ("bary", bary), ("dists", dists)))
     rc = load().rast_mesh_fwd(
         ctypes.byref(p), _ptr(verts, torch.float32, "verts"), verts.shape[0],
         _ptr(faces, torch.int64, "faces"), faces.shape[0],
@@ -230,6 +268,9 @@ def rast_mesh_fwd_static(p, verts, faces, first_face, num_faces, cams, pix_to_fa
     """rast_mesh_fwd without a workspace argument, for callers that cannot allocate
     device memory: the library uses its own built-in 16 MiB device array.  Returns
     the C return code (raises on error when ``check``)."""
+    _batch_inputs(p.N, verts, faces, first_face, num_faces, cams)
+    _slots(p.N, p.image_size, p.faces_per_pixel,
+           (("pix_to_face", pix_to_face), ("zbuf", zbuf), ("bary", bary), ("dists", dists)))
     rc = load().rast_mesh_fwd_static(
         ctypes.byref(p), _ptr(verts, torch.float32, "verts"), verts.shape[0],
         _ptr(faces, torch.int64, "faces"), faces.shape[0],
@@ -244,6 +285,10 @@ def rast_mesh_fwd_static(p, verts, faces, first_face, num_faces, cams, pix_to_fa
 
 def rast_mesh_bwd(p, verts, faces, first_face, num_faces, cams, pix_to_face, grad_zbuf, grad_bary, grad_dists,
                   grad_verts, workspace, stream=None):
+    _batch_inputs(p.N, verts, faces, first_face, num_faces, cams)
+    _slots(p.N, p.image_size, p.faces_per_pixel, (("pix_to_face", pix_to_face), ("grad_zbuf", grad_zbuf),
+                                                  ("grad_bary", grad_bary), ("grad_dists", grad_dists)))
+    _atleast(grad_verts, _n(verts), "grad_verts")
     rc = load().rast_mesh_bwd(
         ctypes.byref(p), _ptr(verts, torch.float32, "verts"), verts.shape[0],
         _ptr(faces, torch.int64, "faces"), faces.shape[0],
@@ -256,6 +301,10 @@ def rast_mesh_bwd(p, verts, faces, first_face, num_faces, cams, pix_to_face, gra
 
 
 def blend_fwd(bp, N, S, K, pix_to_face, zbuf, bary, dists, faces, vert_colors, image, stream=None):
+    _slots(N, S, K, (("pix_to_face", pix_to_face), ("zbuf", zbuf), ("bary", bary), ("dists", dists)))
+    _rows_of(faces, 3, "faces")
+    _rows_of(vert_colors, 3, "vert_colors")
+    _image(image, N, S, 4, "image")
     F = faces.shape[0] if faces is not None else 0
     V = vert_colors.shape[0] if vert_colors is not None else 0
     rc = load().blend_fwd(ctypes.byref(bp), int(N), int(S), int(K), _ptr(pix_to_face, torch.int64, "pix_to_face"),
@@ -268,6 +317,13 @@ def blend_fwd(bp, N, S, K, pix_to_face, zbuf, bary, dists, faces, vert_colors, i
 
 def blend_bwd(bp, N, S, K, pix_to_face, zbuf, bary, dists, faces, vert_colors, grad_image, grad_zbuf, grad_bary,
               grad_dists, grad_vert_colors, stream=None):
+    _slots(N, S, K, (("pix_to_face", pix_to_face), ("zbuf", zbuf), ("bary", bary), ("dists", dists),
+                     ("grad_zbuf", grad_zbuf), ("grad_bary", grad_bary), ("grad_dists", grad_dists)))
+    _rows_of(faces, 3, "faces")
+    _rows_of(vert_colors, 3, "vert_colors")
+    _image(grad_image, N, S, 4, "grad_image")
+    if vert_colors is not None:
+        _atleast(grad_vert_colors, vert_colors.numel(), "grad_vert_colors")
     F = faces.shape[0] if faces is not None else 0
     V = vert_colors.shape[0] if vert_colors is not None else 0
     rc = load().blend_bwd(ctypes.byref(bp), int(N), int(S), int(K), _ptr(pix_to_face, torch.int64, "pix_to_face"),
@@ -283,6 +339,11 @@ def blend_bwd(bp, N, S, K, pix_to_face, zbuf, bary, dists, faces, vert_colors, g
 def rast_blend_fwd(p, bp, verts, faces, first_face, num_faces, cams, vert_colors, pix_to_face, zbuf, bary, dists,
                    image, workspace, stream=None):
     """rast_mesh_fwd and blend_fwd in one call (the fine pass blends as it writes)."""
+    _batch_inputs(p.N, verts, faces, first_face, num_faces, cams)
+    _slots(p.N, p.image_size, p.faces_per_pixel,
+           (("pix_to_face", pix_to_face), ("zbuf", zbuf), ("bary", bary), ("dists", dists)))
+    _atleast(vert_colors, _n(verts), "vert_colors")
+    _image(image, p.N, p.image_size, 4, "image")
     rc = load().rast_blend_fwd(
         ctypes.byref(p), ctypes.byref(bp), _ptr(verts, torch.float32, "verts"), verts.shape[0],
         _ptr(faces, torch.int64, "faces"), faces.shape[0],
@@ -297,6 +358,13 @@ def rast_blend_fwd(p, bp, verts, faces, first_face, num_faces, cams, vert_colors
 def blend_rast_bwd(p, bp, verts, faces, first_face, num_faces, cams, pix_to_face, zbuf, bary, dists, vert_colors,
                    grad_image, grad_verts, grad_vert_colors, workspace, stream=None):
     """blend_bwd followed by rast_mesh_bwd in one pass (fragment gradients stay in registers)."""
+    _batch_inputs(p.N, verts, faces, first_face, num_faces, cams)
+    _slots(p.N, p.image_size, p.faces_per_pixel,
+           (("pix_to_face", pix_to_face), ("zbuf", zbuf), ("bary", bary), ("dists", dists)))
+    _atleast(vert_colors, _n(verts), "vert_colors")
+    _image(grad_image, p.N, p.image_size, 4, "grad_image")
+    _atleast(grad_verts, _n(verts), "grad_verts")
+    _atleast(grad_vert_colors, _n(verts), "grad_vert_colors")
     rc = load().blend_rast_bwd(
         ctypes.byref(p), ctypes.byref(bp), _ptr(verts, torch.float32, "verts"), verts.shape[0],
         _ptr(faces, torch.int64, "faces"), faces.shape[0],
@@ -372,6 +440,8 @@ def alloc_pts_fragments(N, S, K, device="cuda"):
 
 
 def pts_rasterize_fwd(p, points, first_point, num_points, cams, idx, zbuf, dists, workspace, stream=None):
+    _batch_inputs(p.N, points, None, first_point, num_points, cams, "points")
+    _slots(p.N, p.image_size, p.points_per_pixel, (("idx", idx), ("zbuf", zbuf), ("dists", dists)))
     rc = load().pts_rasterize_fwd(
         ctypes.byref(p), _ptr(points, torch.float32, "points"), points.shape[0],
         _ptr(first_point, torch.int64, "first_point"), _ptr(num_points, torch.int64, "num_points"),
@@ -383,6 +453,9 @@ def pts_rasterize_fwd(p, points, first_point, num_points, cams, idx, zbuf, dists
 
 def pts_rasterize_bwd(p, points, first_point, num_points, cams, idx, grad_zbuf, grad_dists, grad_points, workspace,
                       stream=None):
+    _batch_inputs(p.N, points, None, first_point, num_points, cams, "points")
+    _slots(p.N, p.image_size, p.points_per_pixel, (("idx", idx), ("grad_zbuf", grad_zbuf), ("grad_dists", grad_dists)))
+    _atleast(grad_points, _n(points), "grad_points")
     rc = load().pts_rasterize_bwd(
         ctypes.byref(p), _ptr(points, torch.float32, "points"), points.shape[0],
         _ptr(first_point, torch.int64, "first_point"), _ptr(num_points, torch.int64, "num_points"),
@@ -393,6 +466,10 @@ def pts_rasterize_bwd(p, points, first_point, num_points, cams, idx, grad_zbuf, 
 
 
 def pts_composite_fwd(p, mode, idx, dists, features, image, stream=None):
+    _slots(p.N, p.image_size, p.points_per_pixel, (("idx", idx), ("dists", dists)))
+    if features.dim() != 2:
+        raise MeshRastError("features must be (P, D)")
+    _image(image, p.N, p.image_size, features.shape[1], "image")
     rc = load().pts_composite_fwd(ctypes.byref(p), int(mode), _ptr(idx, torch.int64, "idx"),
                                   _ptr(dists, torch.float32, "dists"), _ptr(features, torch.float32, "features"),
                                   features.shape[0], features.shape[1], _ptr(image, torch.float32, "image"),
@@ -401,6 +478,11 @@ def pts_composite_fwd(p, mode, idx, dists, features, image, stream=None):
 
 
 def pts_composite_bwd(p, mode, idx, dists, features, grad_image, grad_dists, grad_features, stream=None):
+    _slots(p.N, p.image_size, p.points_per_pixel, (("idx", idx), ("dists", dists), ("grad_dists", grad_dists)))
+    if features.dim() != 2:
+        raise MeshRastError("features must be (P, D)")
+    _image(grad_image, p.N, p.image_size, features.shape[1], "grad_image")
+    _atleast(grad_features, features.numel(), "grad_features")
     rc = load().pts_composite_bwd(ctypes.byref(p), int(mode), _ptr(idx, torch.int64, "idx"),
                                   _ptr(dists, torch.float32, "dists"), _ptr(features, torch.float32, "features"),
                                   features.shape[0], features.shape[1], _ptr(grad_image, torch.float32, "grad_image"),
@@ -429,6 +511,13 @@ def make_shade_params(light, ambient=(0.5, 0.5, 0.5), diffuse=(0.3, 0.3, 0.3), s
 
 def shade_fwd(bp, sp, N, S, K, pix_to_face, zbuf, bary, dists, faces, verts, normals, vert_colors, cams, image,
               stream=None):
+    _slots(N, S, K, (("pix_to_face", pix_to_face), ("zbuf", zbuf), ("bary", bary), ("dists", dists)))
+    _rows_of(faces, 3, "faces")
+    _rows_of(verts, 3, "verts")
+    _atleast(normals, _n(verts), "normals")
+    _atleast(vert_colors, _n(verts), "vert_colors")
+    _atleast(cams, 16 * int(N), "cams")
+    _image(image, N, S, 4, "image")
     rc = load().shade_fwd(ctypes.byref(bp), ctypes.byref(sp), int(N), int(S), int(K),
                           _ptr(pix_to_face, torch.int64, "pix_to_face"), _ptr(zbuf, torch.float32, "zbuf"),
                           _ptr(bary, torch.float32, "bary"), _ptr(dists, torch.float32, "dists"),
@@ -441,6 +530,15 @@ def shade_fwd(bp, sp, N, S, K, pix_to_face, zbuf, bary, dists, faces, verts, nor
 
 def shade_bwd(bp, sp, N, S, K, pix_to_face, zbuf, bary, dists, faces, verts, normals, vert_colors, cams, grad_image,
               grad_zbuf, grad_bary, grad_dists, grad_verts, grad_normals, grad_vert_colors, stream=None):
+    _slots(N, S, K, (("pix_to_face", pix_to_face), ("zbuf", zbuf), ("bary", bary), ("dists", dists),
+                     ("grad_zbuf", grad_zbuf), ("grad_bary", grad_bary), ("grad_dists", grad_dists)))
+    _rows_of(faces, 3, "faces")
+    _rows_of(verts, 3, "verts")
+    for t, name in ((normals, "normals"), (vert_colors, "vert_colors"), (grad_verts, "grad_verts"),
+                    (grad_normals, "grad_normals"), (grad_vert_colors, "grad_vert_colors")):
+        _atleast(t, _n(verts), name)
+    _atleast(cams, 16 * int(N), "cams")
+    _image(grad_image, N, S, 4, "grad_image")
     rc = load().shade_bwd(ctypes.byref(bp), ctypes.byref(sp), int(N), int(S), int(K),
                           _ptr(pix_to_face, torch.int64, "pix_to_face"), _ptr(zbuf, torch.float32, "zbuf"),
                           _ptr(bary, torch.float32, "bary"), _ptr(dists, torch.float32, "dists"),

@@ -6,6 +6,7 @@ import glob
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -131,3 +132,54 @@ def test_binding_refuses_mismatched_knn_tensors():
     for call, what in cases:
         with pytest.raises(ops.MeshRastError, match=what):
             call()
+
+
+def test_binding_sizes_accept_the_documented_shapes_and_refuse_short_tensors(lib):
+    # correctly sized (CPU) tensors get past the size checks and stop at the
+    # CUDA check; one short tensor is refused by name; no device is touched
+    import torch
+    from paper_2007_08501_gb300 import ops, workloads
+    b = workloads.sphere_batch([1, 1], 0.05, seed_base=1)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a))
+    v, f, ff, nf, cams, col = T(b.verts), T(b.faces), T(b.first_face), T(b.num_faces), T(b.cams), T(b.colors)
+    N, S, K = b.N, 8, 2
+    p = ops.make_rast_params(N, S, K, 1e-3, 8, 64)
+    bp = ops.make_blend_params()
+    sp = ops.make_shade_params((0.0, 0.0, -3.0))
+    fr = (torch.zeros(N, S, S, K, dtype=torch.int64), torch.zeros(N, S, S, K), torch.zeros(N, S, S, K, 3),
+          torch.zeros(N, S, S, K))
+    img = torch.zeros(N, S, S, 4)
+    ws = torch.zeros(64, dtype=torch.uint8)
+    pp = ops.make_pts_params(N, S, K, 0.05, 8, 64)
+    pts = torch.zeros(20, 3)
+    pf, pn = torch.tensor([0, 10]), torch.tensor([10, 10])
+    pfr = (torch.zeros(N, S, S, K, dtype=torch.int64), torch.zeros(N, S, S, K), torch.zeros(N, S, S, K))
+    feats = torch.zeros(20, 2)
+    calls = {
+        "rast_mesh_fwd": lambda fr=fr: ops.rast_mesh_fwd(p, v, f, ff, nf, cams, *fr, ws),
+        "rast_mesh_bwd": lambda fr=fr: ops.rast_mesh_bwd(p, v, f, ff, nf, cams, fr[0], fr[1], fr[2], fr[3],
+                                                         torch.zeros_like(v), ws),
+        "blend_fwd": lambda fr=fr: ops.blend_fwd(bp, N, S, K, *fr, f, col, img),
+        "blend_bwd": lambda fr=fr: ops.blend_bwd(bp, N, S, K, *fr, f, col, img, fr[1], fr[2], fr[3],
+                                                 torch.zeros_like(col)),
+        "rast_blend_fwd": lambda fr=fr: ops.rast_blend_fwd(p, bp, v, f, ff, nf, cams, col, *fr, img, ws),
+        "blend_rast_bwd": lambda fr=fr: ops.blend_rast_bwd(p, bp, v, f, ff, nf, cams, *fr, col, img,
+                                                           torch.zeros_like(v), torch.zeros_like(col), ws),
+        "shade_fwd": lambda fr=fr: ops.shade_fwd(bp, sp, N, S, K, *fr, f, v, v, col, cams, img),
+        "shade_bwd": lambda fr=fr: ops.shade_bwd(bp, sp, N, S, K, *fr, f, v, v, col, cams, img, fr[1], fr[2], fr[3],
+                                                 torch.zeros_like(v), torch.zeros_like(v), torch.zeros_like(col)),
+        "pts_rasterize_fwd": lambda fr=pfr: ops.pts_rasterize_fwd(pp, pts, pf, pn, cams, *fr, ws),
+        "pts_rasterize_bwd": lambda fr=pfr: ops.pts_rasterize_bwd(pp, pts, pf, pn, cams, fr[0], fr[1], fr[2],
+                                                                  torch.zeros_like(pts), ws),
+        "pts_composite_fwd": lambda fr=pfr: ops.pts_composite_fwd(pp, 0, fr[0], fr[2], feats, torch.zeros(N, S, S, 2)),
+        "pts_composite_bwd": lambda fr=pfr: ops.pts_composite_bwd(pp, 0, fr[0], fr[2], feats, torch.zeros(N, S, S, 2),
+                                                                  fr[2], torch.zeros_like(feats)),
+    }
+    for name, call in calls.items():
+        with pytest.raises(ops.MeshRastError, match="CUDA tensor"):
+            call()
+    short = (fr[0], fr[1], fr[2][..., :2].contiguous(), fr[3])      # barycentrics: 2 of 3 per slot
+    with pytest.raises(ops.MeshRastError, match="bary holds"):
+        calls["rast_mesh_fwd"](short)
+    with pytest.raises(ops.MeshRastError, match="dists holds"):
+        calls["pts_rasterize_fwd"]((pfr[0], pfr[1], pfr[2][:, :, :, :1].contiguous()))
