@@ -18,8 +18,11 @@ ORACLE = os.path.join(ROOT, "oracle")
 # source file, environment variable its wrapper reads, the pin tests that cover it
 TARGETS = {
     "mesh": ("oracle.c", "ORACLE_MESH_LIB", ["tests/test_oracle_raster.py", "tests/test_oracle_blend.py"]),
+    # the same source; its margin flags are covered by their own pins
+    "mesh_margins": ("oracle.c", "ORACLE_MESH_LIB", ["tests/test_oracle_margins.py"]),
     "points": ("points.c", "ORACLE_POINTS_LIB", ["tests/test_oracle_points.py"]),
     "shading": ("shading.c", "ORACLE_SHADING_LIB", ["tests/test_oracle_shading.py"]),
+    "shading_margins": ("shading.c", "ORACLE_SHADING_LIB", ["tests/test_oracle_shade_margins.py"]),
     "knn": ("knn.c", "ORACLE_KNN_LIB", ["tests/test_oracle_knn.py"]),
 }
 
@@ -37,6 +40,26 @@ MUTATIONS = [
     ("mesh", "equal depths ordered by descending face id",
      "if (x->f < y->f) return -1;\n    if (x->f > y->f) return 1;",
      "if (x->f > y->f) return -1;\n    if (x->f < y->f) return 1;"),
+    # the margin flags the parity tests exclude pixels by
+    ("mesh_margins", "margin distance taken squared (flags 1 and 2)",
+     "double dist = sqrt(o.s);", "double dist = o.s;"),
+    ("mesh_margins", "depth ties looked for in the first pair only (flag 8)",
+     "for (int64_t i = 0; i + 1 < m && i < K; i++)", "for (int64_t i = 0; i + 1 < m && i < 1; i++)"),
+    ("mesh_margins", "blur boundary flagged inside the face too (flag 2)",
+     "if (blur > 0.0 && !o.inside && fabs(dist - rb) < eps) fl |= 2;",
+     "if (blur > 0.0 && fabs(dist - rb) < eps) fl |= 2;"),
+    ("mesh_margins", "cull-area margin absolute instead of relative (flag 4)",
+     "fabs(fabs(Fc.A) - ORC_CULL_AREA) < eps * ORC_CULL_AREA", "fabs(fabs(Fc.A) - ORC_CULL_AREA) < eps"),
+    ("mesh_margins", "znear margin of the corners dropped (flag 16)",
+     "if (fabs(Fc.P[i][2] - znear) < eps) fl |= 16;", "(void)znear;"),
+    ("mesh_margins", "edges meeting at their shared corner counted as a tie (flag 32)",
+     "if (a != o.edge && fabs(dd[a] - dd[o.edge]) < eps &&\n                        hypot(nx[a] - nx[o.edge], ny[a] - ny[o.edge]) > eps)",
+     "if (a != o.edge && fabs(dd[a] - dd[o.edge]) < eps)"),
+    ("mesh_margins", "clip kink flagged without clipping (flag 64)",
+     "                if (clip)\n                    for (int a = 0; a < 3; a++)\n                        if (fabs(o.bt[a]) < eps) fl |= 64;",
+     "                for (int a = 0; a < 3; a++)\n                        if (fabs(o.bt[a]) < eps) fl |= 64;"),
+    ("mesh_margins", "extrapolation weighed by its depth only (flag 128)",
+     "if (fabs(o.bt[a]) > mag) mag = fabs(o.bt[a]);", "(void)a;"),
     ("points", "opacity against r instead of r squared",
      "return 1.0 - d / (radius * radius);", "return 1.0 - d / radius;"),
     ("points", "transmittance multiplied by the opacity",
@@ -46,6 +69,16 @@ MUTATIONS = [
      "const double D = c > 0.0 ? c : 0.0;\n    double r[3];\n    for (int j = 0; j < 3; j++) r[j] = 2.0 * c * m[j] + l[j];"),
     ("shading", "specular exponent off by one",
      "const double Sp = spec_on ? pow(s, Lt->sh) : 0.0;", "const double Sp = spec_on ? pow(s, Lt->sh - 1.0) : 0.0;"),
+    # the kink margin the shading parity tests drop gradients by
+    ("shading_margins", "specular switch counted with the light behind the face",
+     "if (c > 0.0 && fabs(sv) < mg) mg = fabs(sv);", "if (fabs(sv) < mg) mg = fabs(sv);"),
+    ("shading_margins", "diffuse switch dropped from the margin",
+     "double mg = fabs(c);", "double mg = 1e300;"),
+    ("shading_margins", "hard blend margin taken over every slot",
+     "const int64_t kk = blend_mode == 1 ? 1 : K;", "const int64_t kk = K;"),
+    ("shading_margins", "Gouraud margin taken at the interpolated point",
+     "if (shading == 1) {\n                for (int i = 0; i < 3; i++) {\n                    const double m1",
+     "if (shading == 99) {\n                for (int i = 0; i < 3; i++) {\n                    const double m1"),
     ("knn", "the second coordinate's square rounded before the sum (no fma)",
      "s = fmaf(dc, dc, s);", "s = s + dc * dc;"),
     ("knn", "equal distances ranked by descending row",
