@@ -76,6 +76,32 @@ __device__ __forceinline__ void scatter_face(const BlendArgs &a, const RastBwdAr
     }
 }
 
+// Silhouette blend: only dL/d(dists) reaches the rasterizer, so a slot moves
+// the x, y of its nearest edge's two corners (acc[2 i + {0, 1}] for corner
+// i); one lane per face pulls them through the projection Jacobian and R^T.
+__device__ __forceinline__ void scatter_face_dist(const RastBwdArgs &r, int key, int nf, const FaceRec &R,
+                                                  const float (&acc)[6]) {
+    const float *cam = r.cams + 16 * nf;
+    const float fo = cam[12];
+    const float v0x = R.a.x + R.a.z, v0y = R.a.y + R.a.w;
+    const float Px[3] = {0.f, R.b.x, R.b.z}, Py[3] = {0.f, R.b.y, R.b.w};
+    const float iz[3] = {R.d.y, R.d.z, R.d.w};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float ax = acc[2 * i], ay = acc[2 * i + 1];
+        if (ax == 0.f && ay == 0.f) continue;  // a corner no lane's nearest edge touches
+        const float xn = v0x + Px[i], yn = v0y + Py[i];
+        const float gxv = ax * fo * iz[i];
+        const float gyv = ay * fo * iz[i];
+        const float gzv = -(ax * xn + ay * yn) * iz[i];
+        const int64_t v = __ldg(r.faces + 3 * (int64_t)key + i);
+        float *gv = r.grad_verts + 3 * v;
+        atomicAdd(gv + 0, cam[0] * gxv + cam[3] * gyv + cam[6] * gzv);
+        atomicAdd(gv + 1, cam[1] * gxv + cam[4] * gyv + cam[7] * gzv);
+        atomicAdd(gv + 2, cam[2] * gxv + cam[5] * gyv + cam[8] * gzv);
+    }
+}
+
 // Per-slot tail shared by both kernels: rasterizer adjoint of the slot's
 // fragment gradient, warp grouping by face, one lane per face scatters.
 // acc[9..17] holds the slot's colour gradients (RGB) on entry.
@@ -87,23 +113,37 @@ __device__ __forceinline__ void slot_tail(const BlendArgs &a, const RastBwdArgs 
     const int nf = fr >= 0 ? __ldg(r.face_mesh + fr) : -1;
     const bool live = nf >= 0 && (gz != 0.f || gd != 0.f || gb0 != 0.f || gb1 != 0.f || gb2 != 0.f);
     FaceRec R;
-    float g9[9];
+    if constexpr (!RGB) {
+        static_assert(NA == 6, "silhouette: x, y of three corners");
 #pragma unroll
-    for (int j = 0; j < 9; ++j) g9[j] = 0.f;
-    if (live) {
-        load_adjoint_rec(r.rec, fr, R);
-        slot_corner_grads(R, p, r.fl, gz, gd, gb0, gb1, gb2, g9);
-    }
+        for (int j = 0; j < 6; ++j) acc[j] = 0.f;
+        if (live) {
+            load_adjoint_rec(r.rec, fr, R);
+            slot_corner_grads_dist(R, p, gd, acc);
+        }
+        const int key = live ? fr : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        group_sum<6>(peers, acc);
+        if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) scatter_face_dist(r, key, nf, R, acc);
+    } else {
+        float g9[9];
 #pragma unroll
-    for (int j = 0; j < 9; ++j) acc[j] = g9[j];
-    const int key = RGB ? fr : (live ? fr : -1);
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const unsigned lv = __ballot_sync(0xffffffffu, live);
-    group_sum<NA>(peers, acc);
-    if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
-        const bool any_live = (lv & peers) != 0u;
-        if (any_live && !live) load_adjoint_rec(r.rec, fr, R);
-        scatter_face<RGB, NA>(a, r, key, any_live, nf, R, vi, acc);
+        for (int j = 0; j < 9; ++j) g9[j] = 0.f;
+        if (live) {
+            load_adjoint_rec(r.rec, fr, R);
+            slot_corner_grads(R, p, r.fl, gz, gd, gb0, gb1, gb2, g9);
+        }
+#pragma unroll
+        for (int j = 0; j < 9; ++j) acc[j] = g9[j];
+        const int key = fr;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const unsigned lv = __ballot_sync(0xffffffffu, live);
+        group_sum<NA>(peers, acc);
+        if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
+            const bool any_live = (lv & peers) != 0u;
+            if (any_live && !live) load_adjoint_rec(r.rec, fr, R);
+            scatter_face<RGB, NA>(a, r, key, any_live, nf, R, vi, acc);
+        }
     }
 }
 
@@ -118,7 +158,7 @@ constexpr int fused_min_blocks(int km, bool rgb) { return rgb ? (km >= 16 ? 2 : 
 
 template <int KM, bool RGB>
 __global__ void __launch_bounds__(256, fused_min_blocks(KM, RGB)) k_blend_rast_bwd(BlendArgs a, RastBwdArgs r) {
-    constexpr int NA = RGB ? 18 : 9;
+    constexpr int NA = RGB ? 18 : 6;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
     const bool valid = row < a.S && col < a.S;
@@ -248,7 +288,7 @@ __global__ void __launch_bounds__(256, fused_min_blocks(KM, RGB)) k_blend_rast_b
 // ---------------------------------------------------------------------------
 template <bool RGB>
 __global__ void __launch_bounds__(256) k_blend_rast_bwd_any(BlendArgs a, RastBwdArgs r) {
-    constexpr int NA = RGB ? 18 : 9;
+    constexpr int NA = RGB ? 18 : 6;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
     const bool valid = row < a.S && col < a.S;

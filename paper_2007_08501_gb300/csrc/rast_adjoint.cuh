@@ -15,6 +15,83 @@ __device__ __forceinline__ void edge_grad(float ax, float ay, float bx, float by
     gby += g * (ax - px);
 }
 
+// Pixel minus its nearest point on edge `edge` (0: v0v1, 1: v1v2, 2: v2v0) at
+// segment parameter t, for the gradient of the squared distance.  Near the
+// edge this residual is a difference of nearly equal coordinates, so it is
+// formed in double-float from the record's hi + lo corners: in the interior
+// of the segment as the perpendicular part cross(e, p - a) e_perp / |e|^2
+// (the cross product is the edge function, exact to ~1e-14), at a clamped end
+// as p minus that corner.  Its relative error stays ~1e-7 however close the
+// pixel is to the edge.
+__device__ __forceinline__ void corner_df(const FaceRec &R, int i, df &x, df &y) {
+    // corner i relative to corner 0, as a double-float (selects, no indexing)
+    x = (i == 0) ? df{0.f, 0.f} : (i == 1) ? df{R.b.x, R.e.x} : df{R.b.z, R.e.z};
+    y = (i == 0) ? df{0.f, 0.f} : (i == 1) ? df{R.b.y, R.e.y} : df{R.b.w, R.e.w};
+}
+
+__device__ __forceinline__ void edge_residual(const FaceRec &R, const PixC &p, int edge, float t, float &rx,
+                                              float &ry) {
+    const df qx = df_add(two_sum(p.xh, -R.a.x), two_sum(p.xl, -R.a.z));
+    const df qy = df_add(two_sum(p.yh, -R.a.y), two_sum(p.yl, -R.a.w));
+    const int ia = edge, ib = (edge == 2) ? 0 : edge + 1;
+    if (t <= 0.f || t >= 1.f) {
+        df cx, cy;
+        corner_df(R, (t <= 0.f) ? ia : ib, cx, cy);
+        const df dx = df_sub(qx, cx), dy = df_sub(qy, cy);
+        rx = __fadd_rn(dx.hi, dx.lo);
+        ry = __fadd_rn(dy.hi, dy.lo);
+        return;
+    }
+    df axd, ayd, bxd, byd;
+    corner_df(R, ia, axd, ayd);
+    corner_df(R, ib, bxd, byd);
+    const df ex = df_sub(bxd, axd), ey = df_sub(byd, ayd);
+    const df cr = df_cross(ex, ey, df_sub(qx, axd), df_sub(qy, ayd));
+    const float c = __fadd_rn(cr.hi, cr.lo);
+    const float exf = __fadd_rn(ex.hi, ex.lo), eyf = __fadd_rn(ey.hi, ey.lo);
+    const float s = __fdiv_rn(c, __fmaf_rn(exf, exf, __fmul_rn(eyf, eyf)));
+    rx = -eyf * s;
+    ry = exf * s;
+}
+
+// Gradient of the squared distance to the nearest edge segment, s = |r|^2 with
+// r = p - a - t (b - a): ds/da = -2 r (1 - t), ds/db = -2 r t (the t-derivative
+// vanishes at the nearest point).  gs = dL/ds; adds to the corners' x, y.
+__device__ __forceinline__ void dist_corner_grads(const FaceRec &R, const PixC &p, int edge, float tseg, float gs,
+                                                  float (&gx)[3], float (&gy)[3]) {
+    float rx, ry;
+    edge_residual(R, p, edge, tseg, rx, ry);
+    const int ia = edge, ib = (edge == 2) ? 0 : edge + 1;
+    const float wa = -2.f * gs * (1.f - tseg), wb = -2.f * gs * tseg;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const float w = (i == ia) ? wa : (i == ib) ? wb : 0.f;
+        gx[i] += w * rx;
+        gy[i] += w * ry;
+    }
+}
+
+// Corner gradients of a slot whose only upstream gradient is dL/d(dists) (the
+// silhouette blend): the barycentrics and the depth do not enter.
+// g[2*i + {0,1}] = dL/d(x_i, y_i) of corner i; the depths get nothing.
+__device__ __forceinline__ void slot_corner_grads_dist(const FaceRec &R, const PixC &p, float gd, float (&g)[6]) {
+    float qx, qy;
+    local_q(R, p, qx, qy);
+    float b0, b1, b2;
+    screen_bary(R, qx, qy, b0, b1, b2);
+    const bool inside = (b0 >= 0.f) && (b1 >= 0.f) && (b2 >= 0.f);  // the forward's sign test
+    int edge;
+    float tseg;
+    (void)nearest_edge(R, qx, qy, edge, tseg);
+    float gx[3] = {0.f, 0.f, 0.f}, gy[3] = {0.f, 0.f, 0.f};
+    dist_corner_grads(R, p, edge, tseg, inside ? -gd : gd, gx, gy);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        g[2 * i] = gx[i];
+        g[2 * i + 1] = gy[i];
+    }
+}
+
 // NDC-space corner gradients of one slot: g[3*i + {0,1,2}] = dL/d(x_i, y_i, z_i)
 // of corner i (NDC x, NDC y, view depth).  Uses the record's a, b, d and e.
 __device__ __forceinline__ void slot_corner_grads(const FaceRec &R, const PixC &p, const EvalFlags &fl, float gz,
@@ -102,15 +179,7 @@ __device__ __forceinline__ void slot_corner_grads(const FaceRec &R, const PixC &
     gy[2] += gA * (Px[1] - Px[0]);
     // distance to the nearest segment
     const float gs = inside ? -gd : gd;
-    if (gs != 0.f) {
-        const int ia = edge, ib = (edge == 2) ? 0 : edge + 1;
-        const float rx = qx - (Px[ia] + tseg * (Px[ib] - Px[ia]));
-        const float ry = qy - (Py[ia] + tseg * (Py[ib] - Py[ia]));
-        gx[ia] += gs * (-2.f * rx * (1.f - tseg));
-        gy[ia] += gs * (-2.f * ry * (1.f - tseg));
-        gx[ib] += gs * (-2.f * rx * tseg);
-        gy[ib] += gs * (-2.f * ry * tseg);
-    }
+    if (gs != 0.f) dist_corner_grads(R, p, edge, tseg, gs, gx, gy);
     for (int i = 0; i < 3; ++i) {
         g[3 * i] = gx[i];
         g[3 * i + 1] = gy[i];

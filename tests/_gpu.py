@@ -42,7 +42,8 @@ def np_frags(fr):
 
 def compare_frags(gpu, orc, amb, atol=1e-5):
     """pix_to_face bit-exact on unambiguous pixels; zbuf, bary, dists within atol
-    wherever the face ids agree.  Returns (#ambiguous, #mismatched unambiguous)."""
+    wherever the face ids agree (except the flag-128 slots, which are counted
+    and printed).  Returns (#ambiguous, #mismatched unambiguous)."""
     gp, gz, gb, gd = [np.asarray(x) for x in gpu]
     op, oz, ob, od = orc
     P, K = op.shape
@@ -52,6 +53,9 @@ def compare_frags(gpu, orc, amb, atol=1e-5):
     gd = gd.reshape(P, K)
     ok = amb == 0
     bad = np.nonzero(np.any(gp[ok] != op[ok], axis=1))[0]
+    # slots whose values are not compared: the unclipped extrapolations the
+    # oracle marks as ill-conditioned for fp32 (flag 128), counted and shown
+    n128 = int((((amb & 128) != 0)[:, None] & (gp == op) & (op >= 0)).sum())
     same = gp == op
     # empty slots carry exactly -1
     empty = op < 0
@@ -73,7 +77,70 @@ def compare_frags(gpu, orc, amb, atol=1e-5):
         assert ez <= atol, ("zbuf", ez, where(np.abs(gz - oz)))
         assert eb <= atol, ("bary", eb, where(np.max(np.abs(gb - ob), axis=-1)))
         assert ed <= atol, ("dists", ed, where(np.abs(gd - od)))
+    print("compare_frags: %d of %d pixels ambiguous (ids not compared), %d slots' values not compared "
+          "(ill-conditioned unclipped extrapolation), %d id mismatches" % (int((~ok).sum()), P, n128, int(bad.size)))
     return int((~ok).sum()), int(bad.size)
+
+
+# ---------------------------------------------------------------------------
+# the oracle over a pixel sample, split across spawned processes (one per host
+# core; spawned, because this process holds a CUDA context)
+# ---------------------------------------------------------------------------
+_POOL_MESH = None
+
+
+def _pool_init(arrs):
+    global _POOL_MESH
+    _POOL_MESH = oracle.Mesh(*arrs)
+
+
+def _pool_job(job):
+    kind, args, kw, px = job
+    fn = {"rasterize": oracle.rasterize, "margins": oracle.margins, "rast_bwd": oracle.rast_bwd}[kind]
+    return fn(_POOL_MESH, *args, pixels=px, **kw)
+
+
+class OraclePool:
+    """``rasterize`` / ``margins`` / ``rast_bwd`` of the oracle on a pixel sample,
+    the sample cut into one slice per worker (results concatenated; vertex
+    gradients summed)."""
+
+    def __init__(self, m, workers=None):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        import os
+        self.workers = workers or os.cpu_count() or 1
+        arrs = (m.verts, m.faces, m.first_face, m.num_faces, m.cams)
+        self.ex = cf.ProcessPoolExecutor(max_workers=self.workers, mp_context=mp.get_context("spawn"),
+                                         initializer=_pool_init, initargs=(arrs,))
+
+    def _map(self, kind, args, kw, px, extra=None):
+        cuts = np.array_split(np.arange(px.shape[0]), self.workers)
+        jobs = []
+        for c in cuts:
+            if c.size == 0:
+                continue
+            kwc = dict(kw)
+            if extra is not None:
+                kwc.update({k: (None if v is None else v[c]) for k, v in extra.items()})
+            jobs.append((kind, args, kwc, px[c]))
+        return list(self.ex.map(_pool_job, jobs))
+
+    def rasterize(self, S, K, blur, persp, clip, px):
+        parts = self._map("rasterize", (S, K, blur, persp, clip), {}, px)
+        return tuple(np.concatenate([p[i] for p in parts]) for i in range(4))
+
+    def margins(self, S, K, blur, persp, clip, px):
+        return np.concatenate(self._map("margins", (S, K, blur, persp, clip), {}, px))
+
+    def rast_bwd(self, S, K, p2f, grad_zbuf, grad_bary, grad_dists, blur, persp, clip, px):
+        parts = self._map("rast_bwd", (S, K), dict(blur=blur, persp=persp, clip=clip, with_abs=True), px,
+                          extra=dict(pix_to_face=p2f, grad_zbuf=grad_zbuf, grad_bary=grad_bary,
+                                     grad_dists=grad_dists))
+        return sum(p[0] for p in parts), sum(p[1] for p in parts)
+
+    def close(self):
+        self.ex.shutdown()
 
 
 def pick(fr, pixels, S):
@@ -108,13 +175,12 @@ def grad_close(g, ref, rel=1e-4, scale=None, return_count=False):
 
 
 def assert_grad_close(g, ref, scale, label=""):
-    """Vertex-gradient criterion: global relative error <= 1e-4; every component
-    within 1e-3 of its own term scale; at least 99% of the components with a
-    non-zero scale within 1e-4 of it.  (Components fed by a few fragments
-    lying within ~1e-5 NDC of an edge carry fp32 rounding of that order.)"""
+    """Vertex-gradient criterion: global relative error <= 1e-4, and every
+    component within 1e-4 of max(|ref|, its own term scale).  Prints the
+    worst ratio and how many components were compared."""
     worst, glob, n_over = grad_close(g, ref, scale=scale, return_count=True)
     n_live = int((np.asarray(scale) > 0).sum())
+    print("%s: %d live components, worst %.3f of the 1e-4 bound, global %.2e" % (label, n_live, worst, glob))
     assert glob <= 1e-4, (label, "global", glob)
-    assert worst <= 10, (label, "worst", worst, glob)
-    assert n_over <= max(3, 1e-2 * n_live), (label, "over 1e-4", n_over, n_live, worst)
+    assert n_over == 0, (label, "over 1e-4", n_over, n_live, worst)
     return worst, glob, n_over

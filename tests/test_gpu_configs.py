@@ -10,14 +10,16 @@ autotuner picks, against the FP64 oracle on a seeded pixel sample:
 Each runs forward, silhouette blend, blend adjoint and rasterizer adjoint over
 the whole batch on the GPU; the upstream gradient is non-zero only at the
 sampled, unambiguous pixels, so the vertex gradient can be checked against the
-oracle adjoint evaluated at those pixels alone.
+oracle adjoint evaluated at those pixels alone.  The sample is 256 pixels per
+image (half of them in the central region the meshes cover); the oracle runs
+over it in one spawned process per host core.
 """
 import numpy as np
 import pytest
 import torch
 
 import oracle
-from _gpu import assert_grad_close, compare_frags, np_frags, oracle_mesh, pick, to_dev
+from _gpu import OraclePool, assert_grad_close, compare_frags, np_frags, oracle_mesh, pick, to_dev
 from paper_2007_08501_gb300 import ops, tune, workloads
 
 pytestmark = pytest.mark.gpu
@@ -52,8 +54,16 @@ def _run(w, per_image, seed, check_grad=True):
     assert ops.rast_query_status(ws) == 0
     px = _sample(b.N, S, per_image, seed)
     m = oracle_mesh(b)
-    orc = oracle.rasterize(m, S, K, blur, persp, clip, pixels=px)
-    flags = oracle.margins(m, S, K, blur, persp, clip, pixels=px)
+    pool = OraclePool(m)
+    try:
+        _check(w, b, d, p, ws, frags, px, pool, S, K, blur, persp, clip, seed, check_grad)
+    finally:
+        pool.close()
+
+
+def _check(w, b, d, p, ws, frags, px, pool, S, K, blur, persp, clip, seed, check_grad):
+    orc = pool.rasterize(S, K, blur, persp, clip, px)
+    flags = pool.margins(S, K, blur, persp, clip, px)
     got = pick(np_frags(frags), px, S)
     n_amb, n_bad = compare_frags(got, orc, flags & oracle.FWD_AMBIGUOUS)
     assert n_bad == 0
@@ -86,21 +96,27 @@ def _run(w, per_image, seed, check_grad=True):
     _, _, rd, _ = oracle.blend_bwd(gfr[0], gfr[1], gfr[2], gfr[3], None, None, gsel, float(np.float32(w.sigma)),
                                    float(np.float32(w.gamma)), float(np.float32(w.znear)),
                                    float(np.float32(w.zfar)), mode=0, V=1)
-    ref, ref_abs = oracle.rast_bwd(m, S, K, gfr[0], None, None, rd, blur, persp, clip, pixels=px, with_abs=True)
+    ref, ref_abs = pool.rast_bwd(S, K, gfr[0], None, None, rd, blur, persp, clip, px)
     assert np.abs(ref).max() > 0
     worst, glob, n_over = assert_grad_close(gv.cpu().numpy(), ref, ref_abs, w.name)
     print("%s: ambiguous %d / %d pixels, grad worst %.2f, global %.2e, over 1e-4: %d"
           % (w.name, n_amb, px.shape[0], worst, glob, n_over))
+    # the fused backward the benchmark step runs (blend adjoint pulled straight
+    # through the rasterizer adjoint), against the same oracle adjoint
+    gv2 = torch.empty_like(d["verts"])
+    ops.blend_rast_bwd(p, bp, d["verts"], d["faces"], d["first_face"], d["num_faces"], d["cams"], p2f, None, None,
+                       di, None, gimg, gv2, None, ws)
+    assert_grad_close(gv2.cpu().numpy(), ref, ref_abs, w.name + " fused")
 
 
 def test_heterogeneous_batch_of_32_meshes_512():
-    _run(workloads.workload(2), per_image=8, seed=20)
+    _run(workloads.workload(2), per_image=256, seed=20)
 
 
 @pytest.mark.parametrize("variant", ["hard", "soft"])
 def test_large_mesh_1024(variant):
-    _run(workloads.workload(3, variant), per_image=12, seed=30)
+    _run(workloads.workload(3, variant), per_image=256, seed=30)
 
 
 def test_twenty_views_shared_vertices_k50():
-    _run(workloads.workload(4), per_image=4, seed=40)
+    _run(workloads.workload(4), per_image=256, seed=40)
