@@ -2,13 +2,17 @@
 """Throughput of the differentiable packed-mesh rasterizer + soft blends on GB300.
 
 One step = the whole differentiable path over one batch, through the C ABI:
-  rast_mesh_fwd (stage, bin count/scan/fill, fine top-K) -> blend_fwd (softmax
-  rgb + silhouette alpha) -> blend_bwd (upstream grad N(0,1)) -> rast_mesh_bwd
-  (grad to the packed vertices).
-Workload: 8 displaced icospheres of 5,120 faces (level 4), random cameras,
-256x256, K = 8, blur_radius = ln(1/1e-4 - 1) 1e-4, sigma = gamma = 1e-4.
+  rast_blend_fwd (stage, bin count/scan/fill, fine top-K, blend) ->
+  blend_rast_bwd (blend adjoint pulled through the rasterizer adjoint, upstream
+  grad N(0,1), grad to the packed vertices).
+Default workload (the largest configuration): 1 displaced icosphere of 81,920
+faces (level 6) seen by 20 cameras, 512x512, K = 50, blur_radius =
+ln(1/1e-4 - 1) 1e-4, soft silhouette (sigma = 1e-4); the same step as four
+separate calls and the plain per-mesh form (one unbinned launch per image) are
+timed beside it.  --workload 1 is the 8 x 5,120-face batch at 256x256, K = 8,
+softmax RGB + silhouette.
 
-Each C-ABI call is captured in its own CUDA graph; a step replays the four
+Each C-ABI call is captured in its own CUDA graph; a step replays the
 graphs with CUDA events between them, so every stage's device time is
 measured live on the launching stream inside the timed region.  L2 is
 flushed (256 MiB write) between steps, outside the events.
@@ -99,9 +103,12 @@ def _args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="1", choices=sorted(WORKLOADS),
-                    help="1 (default, the headline line) or one of the larger parity workloads")
+    ap.add_argument("--workload", default="4", choices=sorted(WORKLOADS),
+                    help="4 (default: the largest configuration, 20 views x 81,920 faces, 512^2, K = 50) or "
+                         "another workload")
     ap.add_argument("--no-plain", action="store_true", help="skip timing the plain per-mesh form")
+    ap.add_argument("--plain", action="store_true",
+                    help="also time the plain per-mesh form on workloads other than 1 and 4 (slow)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-fit", action="store_true", help="workload 4: skip timing the fitting loop")
     ap.add_argument("--bin-size", type=int, default=0, choices=[0, 8, 16],
@@ -136,6 +143,36 @@ def _peaks():
         return float(pk["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def measure_fp32_peak(device, target_ms=40.0, reps=5):
+    """FP32 FMA throughput of this GPU (``meshrast_fma_probe``: 8 blocks of 256
+    threads per SM, 8 independent FMA chains per thread), CUDA events on the
+    launching stream, best of ``reps`` after a warm-up.  Returns FMA lane
+    operations per second (one FMA per lane per clock at peak; 2 FLOPs each)."""
+    import torch
+    from paper_2007_08501_gb300 import ops
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    blocks = sms * 8
+    out = torch.empty(blocks * 256, dtype=torch.float32, device=device)
+    iters = 64
+    ops.fma_probe(out, blocks, iters)
+    torch.cuda.synchronize(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ops.fma_probe(out, blocks, iters)
+    e1.record()
+    e1.synchronize()
+    iters = max(64, int(iters * target_ms / max(e0.elapsed_time(e1), 1e-3)))
+    best = None
+    for _ in range(reps):
+        e0.record()
+        flops = ops.fma_probe(out, blocks, iters)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    return flops / 2 / (best / 1e3)
 
 
 # ---------------------------------------------------------------------------
@@ -614,15 +651,24 @@ def run_ours(args):
         del g, img2
 
     plain = None
-    if not args.no_plain and args.workload == "1":
+    if not args.no_plain and (args.workload in ("1", "4") or args.plain):
+        # the plain per-mesh form: one unbinned launch per image (no graph);
+        # a few steps, each of them seconds long at the larger workloads
         pp = Pipeline(w, bin_size=0, max_faces_per_bin=1, device=dev)
         pp.run_eager()
-        ps = timed_steps(pp, max(3, args.steps // 2), 2, flush, use_graph=False)
+        small = args.workload == "1"
+        ps = timed_steps(pp, max(3, args.steps // 2) if small else 2, 2 if small else 1, flush, use_graph=False)
         pms = statistics.mean(sum(s.values()) for s in ps)
         pstages = {k: round(statistics.mean(s[k] for s in ps), 4) for k in ps[0]}
         plain = {"ms_per_step": round(pms, 4), "value": round(slots / (pms / 1e3) / 1e6, 1),
                  "fwd_ms": pstages["fwd"], "launches_per_step": b.N + 1 + 1 + 2,
                  "speedup_of_binned": round(pms / ms, 3)}
+
+    # the FP32 FMA peak of this GPU (the ALU ceiling of the fine pass's face tests)
+    fp32_fma = measure_fp32_peak(dev)
+    fp32 = {"fma_lane_ops_per_s": round(fp32_fma, 1), "tflops": round(2 * fp32_fma / 1e12, 2),
+            "probe": "meshrast_fma_probe: 8 blocks x 256 threads per SM, 8 FMA chains per thread, best of 5",
+            "derived_at_max_clock_tflops": round(2 * FP32_LANE_OPS_PEAK / 1e12, 2)}
 
     fit_loop = None
     if args.workload == "4" and not args.no_fit:
@@ -663,7 +709,8 @@ def run_ours(args):
             "fine_pass": {"face_pixel_tests": fine_tests,
                           "tests_per_s": round(fine_tests / (stages.get("fwd", stages.get("rast_fwd")) / 1e3), 1),
                           "note": "sum over bins of (pixels in bin x faces in bin)"},
-            "clocks": clk, "unfused": separate, "silhouette_without_fragments": sil_only, "plain_form": plain,
+            "clocks": clk, "fp32_peak": fp32, "unfused": separate, "silhouette_without_fragments": sil_only,
+            "plain_form": plain,
             "fit_loop": fit_loop,
             "status": st,
             "wall_s_timed_region": round(wall, 3),
@@ -1105,11 +1152,13 @@ def run_knn(args):
     stages = {k: statistics.mean(s[k] for s in per_step) for k in per_step[0]}
     dom = "chamfer_fwd" if w.chamfer else "knn"
     achieved = pairs * KNN_OPS_PER_PAIR / (stages[dom] / 1e3)
-    roofline = {"bound": "alu", "achieved": round(achieved / 1e12, 3), "peak": round(FP32_LANE_OPS_PEAK / 1e12, 2),
-                "unit": "T FP32 lane-op/s", "frac": round(achieved / FP32_LANE_OPS_PEAK, 4), "traffic": None,
+    peak_ops = measure_fp32_peak(dev)
+    roofline = {"bound": "alu", "achieved": round(achieved / 1e12, 3), "peak": round(peak_ops / 1e12, 2),
+                "unit": "T FP32 lane-op/s", "frac": round(achieved / peak_ops, 4), "traffic": None,
                 "kernel": "k_knn (%s call)" % dom,
                 "ops_per_pair": KNN_OPS_PER_PAIR, "pairs_per_launch": pairs,
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz (one lane-op per lane per clock)"}
+                "peak_source": "measured in this run: meshrast_fma_probe (FMA lane operations per second)",
+                "derived_peak": round(FP32_LANE_OPS_PEAK / 1e12, 2)}
     # end to end with host buffers: inputs in, results out, every step
     pin = lambda t: t.cpu().pin_memory()
     h_in = [(d_, pin(d_)) for d_ in pipe.inputs()]

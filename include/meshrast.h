@@ -77,7 +77,8 @@ extern "C" {
 #define MESHRAST_OK                 0
 #define MESHRAST_ERR_INVALID_ARG   (-1)   /* bad size, NULL pointer, bad flag */
 #define MESHRAST_ERR_WORKSPACE     (-2)   /* workspace too small or not 256-byte aligned */
-#define MESHRAST_ERR_UNSUPPORTED   (-3)   /* e.g. K > 64, bin_size not in {0, 8, 16} */
+#define MESHRAST_ERR_UNSUPPORTED   (-3)   /* K > 64, bin_size not in {0, 8, 16}, or a binned layout
+                                             with N * nb^2 >= 2^31 - 1 bins or > 2^31 - 1 list entries */
 #define MESHRAST_ERR_CUDA          (-4)   /* a kernel launch or memset failed */
 #define MESHRAST_ERR_STATIC_TOO_LARGE (-5) /* rast_mesh_fwd_static: the call needs more workspace
                                               than MESHRAST_STATIC_WORKSPACE_BYTES */
@@ -103,7 +104,9 @@ typedef struct {
     float   blur_radius;          /* >= 0, squared NDC units (same units as dists) */
     float   reserved_f;           /* must be 0 */
     int64_t max_bin_entries;      /* binned mode: capacity of all bin lists together;
-                                     0 means N * nb * nb * max_faces_per_bin, nb = ceil(S / bin_size) */
+                                     0 means N * nb * nb * max_faces_per_bin, nb = ceil(S / bin_size).
+                                     Bins (N * nb * nb) and this capacity must stay below 2^31 - 1
+                                     (32-bit device counters), else MESHRAST_ERR_UNSUPPORTED */
 } rast_params;
 
 /* Blend parameters (Algorithms 1 and 2; zfar, znear, sigma, gamma are the
@@ -300,6 +303,29 @@ MESHRAST_API int rast_query_status(const void *workspace, uint32_t *status, void
 MESHRAST_API int rast_bin_occupancy(const rast_params *p, int64_t V, int64_t F, const void *workspace,
                        int32_t *max_count, int64_t *total_entries, void *stream);
 
+/* Where a forward leaves its coarse-binning result in the workspace, for
+ * callers that inspect the bin assignment (the first pass of Section 3.2's
+ * two-pass rasterizer).  Pure host computation; byte offsets from the start of
+ * the workspace, valid for binned parameters (bin_size 8 or 16):
+ *   counts   int32[NB]    faces whose inflated bbox meets bin b (before any clamp)
+ *   eff      int32[NB]    entries stored for bin b (counts clamped to the capacities)
+ *   offsets  int32[NB+1]  first list entry of bin b
+ *   lists    uint64[capacity]  entries of bin b at lists[offsets[b] .. offsets[b] + eff[b]):
+ *            (float bits of the face's nearest-corner view depth << 32) | face id
+ *            (order within a bin unspecified)
+ * Bin b = (n * nb + by) * nb + bx for image n, bin row by, bin column bx;
+ * bin (by, bx) holds the pixel rows by*bin_size .. and columns bx*bin_size ...
+ * Returns MESHRAST_ERR_INVALID_ARG / _UNSUPPORTED as rast_workspace_bytes
+ * would return 0, or when out is NULL or the parameters are not binned. */
+typedef struct {
+    int64_t counts, eff, offsets, lists;   /* byte offsets */
+    int64_t nb;                            /* bins per image side, ceil(S / bin_size) */
+    int64_t NB;                            /* N * nb * nb */
+    int64_t capacity;                      /* entries lists can hold */
+    int64_t bytes;                         /* = rast_workspace_bytes */
+} rast_bin_layout;
+MESHRAST_API int rast_workspace_bin_layout(const rast_params *p, int64_t V, int64_t F, rast_bin_layout *out);
+
 /* ---- forward without a caller-supplied workspace -------------------------
  * Not part of the paper's method; it exists for callers that cannot allocate
  * device memory at all -- for example a plugin inside a host application
@@ -318,13 +344,16 @@ MESHRAST_API int rast_bin_occupancy(const rast_params *p, int64_t V, int64_t F, 
  *     max_faces_per_bin = 256 needs about 8 MiB.
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before capturing any stream on that device.
+ *     before capturing any stream on that device.  A failed lookup is not
+ *     remembered (the next call tries again); a successful one is kept for
+ *     the life of the context, so after cudaDeviceReset() the process must
+ *     not call this entry point again (the kept address would be stale).
  *   - All calls share the one array, and each call starts by resetting what
  *     it needs.  Calls that overlap on the GPU (two streams, or several host
  *     threads) race on it: order them on one stream.
- *   - The status word it leaves is not readable through this API (there is
- *     no workspace pointer to pass to rast_query_status); outputs follow the
- *     same rules as rast_mesh_fwd. */
+ *   - Outputs follow the same rules as rast_mesh_fwd; the status word the
+ *     call leaves in the array (MESHRAST_ST_* bits, e.g. a bin overflow) is
+ *     read with rast_query_static_status. */
 #define MESHRAST_STATIC_WORKSPACE_BYTES (16u << 20)
 MESHRAST_API int rast_mesh_fwd_static(const rast_params *p,
                                       const float *verts, int64_t V,
@@ -333,6 +362,24 @@ MESHRAST_API int rast_mesh_fwd_static(const rast_params *p,
                                       const float *cams,
                                       int64_t *pix_to_face, float *zbuf, float *bary, float *dists,
                                       void *stream);
+
+/* Status word (MESHRAST_ST_* bits) of the last rast_mesh_fwd_static call on
+ * the current device, like rast_query_status for a caller-owned workspace:
+ * synchronises `stream` (the one the call ran on), then copies the word to
+ * *status.  The word belongs to the shared array, so a later static call
+ * resets it.  Returns MESHRAST_ERR_INVALID_ARG for a NULL status pointer and
+ * MESHRAST_ERR_CUDA when the stream or the copy fails. */
+MESHRAST_API int rast_query_static_status(uint32_t *status, void *stream);
+
+/* ---- measurement -----------------------------------------------------
+ * FP32 FMA throughput probe (no counterpart in the paper: it measures the
+ * denominator of the ALU rooflines).  Enqueues `blocks` blocks of 256 threads;
+ * each thread runs 8 independent chains of iters * 16 fused multiply-adds
+ * and writes one float to out[block * 256 + thread] (out holds blocks * 256
+ * floats).  FLOPs per launch = blocks * 256 * 8 * 16 * iters * 2; time it
+ * with CUDA events on `stream`.  MESHRAST_ERR_INVALID_ARG for a NULL out,
+ * blocks outside 1 .. 2^20 or iters < 1. */
+MESHRAST_API int meshrast_fma_probe(float *out, int64_t blocks, int32_t iters, void *stream);
 
 /* Static text for a MESHRAST_ERR_* code. */
 MESHRAST_API const char *rast_strerror(int code);

@@ -30,8 +30,7 @@ bool ws_layout(const rast_params *p, int64_t V, int64_t F, mr::WsLayout *L) {
     if (p->bin_size > 0) {
         const int64_t nb = (p->image_size + p->bin_size - 1) / p->bin_size;
         const int64_t NB = (int64_t)p->N * nb * nb;
-        int64_t cap = p->max_bin_entries > 0 ? p->max_bin_entries : NB * (int64_t)p->max_faces_per_bin;
-        if (cap > 0x7fffffffLL) cap = 0x7fffffffLL;
+        const int64_t cap = p->max_bin_entries > 0 ? p->max_bin_entries : NB * (int64_t)p->max_faces_per_bin;
         L->nb = nb;
         L->NB = NB;
         L->capacity = cap;
@@ -81,6 +80,15 @@ static bool check_params(const rast_params *p, int64_t V, int64_t F) {
 static int unsupported(const rast_params *p) {
     if (p->faces_per_pixel > mr::kMaxK) return 1;
     if (p->bin_size != 0 && p->bin_size != 8 && p->bin_size != 16) return 1;
+    if (p->bin_size > 0) {
+        // bin keys, counts, offsets and list positions are 32-bit on the device:
+        // refuse layouts that would not fit instead of clamping them
+        const int64_t nb = (p->image_size + p->bin_size - 1) / p->bin_size;
+        const int64_t NB = (int64_t)p->N * nb * nb;
+        if (NB >= 0x7fffffffLL) return 1;
+        const int64_t cap = p->max_bin_entries > 0 ? p->max_bin_entries : NB * (int64_t)p->max_faces_per_bin;
+        if (cap > 0x7fffffffLL) return 1;
+    }
     return 0;
 }
 
@@ -510,12 +518,31 @@ int rast_bin_occupancy(const rast_params *p, int64_t V, int64_t F, const void *w
     return MESHRAST_OK;
 }
 
+int rast_workspace_bin_layout(const rast_params *p, int64_t V, int64_t F, rast_bin_layout *out) {
+    if (!out || !mr_host::check_params(p, V, F)) return MESHRAST_ERR_INVALID_ARG;
+    if (mr_host::unsupported(p)) return MESHRAST_ERR_UNSUPPORTED;
+    if (p->bin_size <= 0) return MESHRAST_ERR_INVALID_ARG;
+    WsLayout L;
+    mr_host::ws_layout(p, V, F, &L);
+    out->counts = (int64_t)L.counts;
+    out->eff = (int64_t)L.eff;
+    out->offsets = (int64_t)L.offsets;
+    out->lists = (int64_t)L.lists;
+    out->nb = L.nb;
+    out->NB = L.NB;
+    out->capacity = L.capacity;
+    out->bytes = (int64_t)L.bytes;
+    return MESHRAST_OK;
+}
+
 const char *rast_strerror(int code) {
     switch (code) {
         case MESHRAST_OK: return "ok";
         case MESHRAST_ERR_INVALID_ARG: return "invalid argument";
         case MESHRAST_ERR_WORKSPACE: return "workspace too small or not 256-byte aligned";
-        case MESHRAST_ERR_UNSUPPORTED: return "unsupported parameters (K > 64 or bin_size not in {0, 8, 16})";
+        case MESHRAST_ERR_UNSUPPORTED:
+            return "unsupported parameters (K > 64, bin_size not in {0, 8, 16}, or 2^31 - 1 or more bins or bin-list "
+                   "entries)";
         case MESHRAST_ERR_CUDA: return "CUDA launch failed";
         case MESHRAST_ERR_STATIC_TOO_LARGE:
             return "the call needs more workspace than the library's built-in 16 MiB array (use rast_mesh_fwd)";

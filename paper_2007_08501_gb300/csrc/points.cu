@@ -632,7 +632,16 @@ static bool pt_params_ok(const pts_params *p, int64_t P) {
 }
 
 static bool pt_unsupported(const pts_params *p) {
-    return p->points_per_pixel > kMaxK || (p->bin_size != 0 && p->bin_size != 8 && p->bin_size != 16);
+    if (p->points_per_pixel > kMaxK || (p->bin_size != 0 && p->bin_size != 8 && p->bin_size != 16)) return true;
+    if (p->bin_size > 0) {
+        // bin keys, counts, offsets and list positions are 32-bit on the device
+        const int64_t nb = (p->image_size + p->bin_size - 1) / p->bin_size;
+        const int64_t NB = (int64_t)p->N * nb * nb;
+        if (NB >= 0x7fffffffLL) return true;
+        const int64_t cap = p->max_bin_entries > 0 ? p->max_bin_entries : NB * (int64_t)p->max_points_per_bin;
+        if (cap > 0x7fffffffLL) return true;
+    }
+    return false;
 }
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -647,8 +656,7 @@ static void pt_layout(const pts_params *p, int64_t P, PtLayout *L) {
     if (p->bin_size > 0) {
         const int64_t nb = (p->image_size + p->bin_size - 1) / p->bin_size;
         const int64_t NB = (int64_t)p->N * nb * nb;
-        int64_t cap = p->max_bin_entries > 0 ? p->max_bin_entries : NB * (int64_t)p->max_points_per_bin;
-        if (cap > 0x7fffffffLL) cap = 0x7fffffffLL;
+        const int64_t cap = p->max_bin_entries > 0 ? p->max_bin_entries : NB * (int64_t)p->max_points_per_bin;
         L->nb = nb;
         L->NB = NB;
         L->capacity = cap;

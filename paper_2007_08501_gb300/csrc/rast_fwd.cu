@@ -120,8 +120,8 @@ __global__ void __launch_bounds__(256) k_stage(StageArgs a) {
 // scan: one block; clamps counts, exclusive scan, resets cursors and queue
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(1024) k_scan(ScanArgs a) {
-    __shared__ int warp_sums[32];
-    __shared__ int carry_s;
+    __shared__ long long warp_sums[32];
+    __shared__ long long carry_s;   // running sum of the clamped counts (may exceed the capacity)
     __shared__ int maxc_s;
     __shared__ unsigned long long tot_s;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -151,36 +151,37 @@ __global__ void __launch_bounds__(1024) k_scan(ScanArgs a) {
         local_tot += (unsigned long long)c;
         int e = c;
         if (e > a.max_per_bin) { e = a.max_per_bin; overflow = true; }
-        // block exclusive scan of e
-        int x = e;
+        // block exclusive scan of e (64-bit: 1024 counts may sum past 2^31)
+        long long x = e;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, x, o);
+            long long y = __shfl_up_sync(0xffffffffu, x, o);
             if (lane >= o) x += y;
         }
         if (lane == 31) warp_sums[wid] = x;
         __syncthreads();
         if (wid == 0) {
-            int s = warp_sums[lane];
+            long long s = warp_sums[lane];
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, s, o);
+                long long y = __shfl_up_sync(0xffffffffu, s, o);
                 if (lane >= o) s += y;
             }
             warp_sums[lane] = s;
         }
         __syncthreads();
-        const int carry = carry_s;
-        int excl = carry + (wid ? warp_sums[wid - 1] : 0) + x - e;
+        const long long carry = carry_s;
+        // 64-bit position; entries past the capacity are dropped (overflow bit)
+        const long long excl = carry + (wid ? warp_sums[wid - 1] : 0ll) + x - e;
         if (b < a.NB) {
-            int64_t room = a.capacity - (int64_t)excl;
-            if ((int64_t)e > room) { e = (int)max((int64_t)0, room); overflow = true; }
-            a.offsets[b] = excl;
+            const long long room = (long long)a.capacity - excl;
+            if ((long long)e > room) { e = (int)max(0ll, room); overflow = true; }
+            a.offsets[b] = (int)min(excl, (long long)a.capacity);  // capacity < 2^31 (checked on the host)
             a.eff[b] = e;
             a.cursor[b] = 0;
         }
         __syncthreads();
-        if (tid == 1023) carry_s = (int)min((int64_t)carry + warp_sums[31], (int64_t)0x7fffffff);
+        if (tid == 1023) carry_s = carry + warp_sums[31];
         __syncthreads();
     }
     // block totals: warp reductions first, then one shared atomic per warp
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(1024) k_scan(ScanArgs a) {
     if (__any_sync(0xffffffffu, overflow) && lane == 0) set_status(a.status, MESHRAST_ST_BIN_OVERFLOW);
     __syncthreads();
     if (tid == 0) {
-        a.offsets[a.NB] = carry_s;
+        a.offsets[a.NB] = (int)min(carry_s, (long long)a.capacity);
         *a.maxcount = maxc_s;
         *a.total = (long long)tot_s;
     }

@@ -23,23 +23,25 @@ namespace {
 
 constexpr int kMaxDevices = 64;
 void *g_ws_ptr[kMaxDevices];
-cudaError_t g_ws_err[kMaxDevices];
-std::once_flag g_ws_once[kMaxDevices];
+std::mutex g_ws_mutex;
 
 // The array's name in host code is only a host-side stand-in; its device
-// address is looked up once per device, with that device current.
+// address is looked up with the device current, on the first call on that
+// device, and kept.  A failed lookup is not kept: the next call tries again.
 cudaError_t device_workspace(void **ptr) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::call_once(g_ws_once[dev], [dev]() {
+    std::lock_guard<std::mutex> lock(g_ws_mutex);
+    if (g_ws_ptr[dev] == nullptr) {
         void *p = nullptr;
-        g_ws_err[dev] = cudaGetSymbolAddress(&p, g_static_workspace);
-        g_ws_ptr[dev] = (g_ws_err[dev] == cudaSuccess) ? p : nullptr;
-    });
+        e = cudaGetSymbolAddress(&p, g_static_workspace);
+        if (e != cudaSuccess) return e;
+        g_ws_ptr[dev] = p;
+    }
     *ptr = g_ws_ptr[dev];
-    return g_ws_err[dev];
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -58,4 +60,12 @@ extern "C" MESHRAST_API int rast_mesh_fwd_static(const rast_params *p, const flo
     // shared array does not matter.
     return rast_mesh_fwd(p, verts, V, faces, F, first_face, num_faces, cams, pix_to_face, zbuf, bary, dists,
                          ws, (size_t)MESHRAST_STATIC_WORKSPACE_BYTES, stream);
+}
+
+// The status word sits at the start of the array, as in any workspace.
+extern "C" MESHRAST_API int rast_query_static_status(uint32_t *status, void *stream) {
+    if (!status) return MESHRAST_ERR_INVALID_ARG;
+    void *ws = nullptr;
+    if (device_workspace(&ws) != cudaSuccess || ws == nullptr) return MESHRAST_ERR_CUDA;
+    return rast_query_status(ws, status, stream);
 }

@@ -33,6 +33,7 @@ BLEND_RGB = 1
 
 EXPORTED = ("rast_workspace_bytes", "rast_mesh_fwd", "rast_mesh_bwd", "blend_fwd", "blend_bwd",
             "rast_query_status", "rast_bin_occupancy", "rast_strerror", "rast_mesh_fwd_static",
+            "rast_query_static_status", "rast_workspace_bin_layout", "meshrast_fma_probe",
             "blend_rast_bwd", "rast_blend_fwd",
             "pts_workspace_bytes", "pts_rasterize_fwd", "pts_rasterize_bwd", "pts_composite_fwd",
             "pts_composite_bwd", "pts_bin_occupancy", "shade_fwd", "shade_bwd",
@@ -57,6 +58,12 @@ class blend_params(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_float), ("gamma", ctypes.c_float), ("znear", ctypes.c_float),
                 ("zfar", ctypes.c_float), ("bg", ctypes.c_float * 3), ("eps", ctypes.c_float),
                 ("mode", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class rast_bin_layout(ctypes.Structure):
+    _fields_ = [("counts", ctypes.c_int64), ("eff", ctypes.c_int64), ("offsets", ctypes.c_int64),
+                ("lists", ctypes.c_int64), ("nb", ctypes.c_int64), ("NB", ctypes.c_int64),
+                ("capacity", ctypes.c_int64), ("bytes", ctypes.c_int64)]
 
 
 class MeshRastError(RuntimeError):
@@ -118,6 +125,12 @@ def load(build_if_missing: bool = False):
     L.rast_bin_occupancy.restype = ctypes.c_int
     L.rast_mesh_fwd_static.argtypes = [P, vp, i64, vp, i64, vp, vp, vp, vp, vp, vp, vp, vp]
     L.rast_mesh_fwd_static.restype = ctypes.c_int
+    L.rast_query_static_status.argtypes = [ctypes.POINTER(ctypes.c_uint32), vp]
+    L.rast_query_static_status.restype = ctypes.c_int
+    L.rast_workspace_bin_layout.argtypes = [P, i64, i64, ctypes.POINTER(rast_bin_layout)]
+    L.rast_workspace_bin_layout.restype = ctypes.c_int
+    L.meshrast_fma_probe.argtypes = [vp, i64, ctypes.c_int32, vp]
+    L.meshrast_fma_probe.restype = ctypes.c_int
     H = ctypes.POINTER(shade_params)
     L.shade_fwd.argtypes = [B, H, i64, i64, i64, vp, vp, vp, vp, vp, i64, vp, vp, vp, i64, vp, vp, vp]
     L.shade_fwd.restype = ctypes.c_int
@@ -281,6 +294,30 @@ def rast_mesh_fwd_static(p, verts, faces, first_face, num_faces, cams, pix_to_fa
     if check:
         _check(rc, "rast_mesh_fwd_static")
     return rc
+
+
+def rast_query_static_status(stream=None) -> int:
+    """Status bits left by the last rast_mesh_fwd_static call on this device (syncs the stream)."""
+    v = ctypes.c_uint32(0)
+    _check(load().rast_query_static_status(ctypes.byref(v), _stream(stream)), "rast_query_static_status")
+    return int(v.value)
+
+
+def fma_probe(out, blocks, iters, stream=None):
+    """Enqueue the FP32 FMA throughput probe; returns the FLOPs it performs."""
+    _atleast(out, blocks * 256, "out")
+    _check(load().meshrast_fma_probe(_ptr(out, torch.float32, "out"), int(blocks), int(iters), _stream(stream)),
+           "meshrast_fma_probe")
+    return blocks * 256 * 8 * 16 * iters * 2
+
+
+def rast_workspace_bin_layout(p, V, F) -> dict:
+    """Byte offsets of the bin counts, clamped counts, offsets and lists in the workspace
+    (binned parameters), with nb, NB, capacity and the workspace size."""
+    out = rast_bin_layout()
+    _check(load().rast_workspace_bin_layout(ctypes.byref(p), int(V), int(F), ctypes.byref(out)),
+           "rast_workspace_bin_layout")
+    return {k: int(getattr(out, k)) for k, _ in rast_bin_layout._fields_}
 
 
 def rast_mesh_bwd(p, verts, faces, first_face, num_faces, cams, pix_to_face, grad_zbuf, grad_bary, grad_dists,

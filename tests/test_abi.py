@@ -65,6 +65,30 @@ def test_pure_host_entry_points(lib):
                        None) == ops.MESHRAST_ERR_INVALID_ARG
 
 
+def test_bin_layouts_past_32_bits_are_refused(lib):
+    # bin keys, counts, offsets and list positions are 32-bit on the device: a
+    # layout with 2^31 - 1 or more bins, or more bin-list entries, is refused
+    # (workspace size 0, UNSUPPORTED from the calls) instead of being clamped
+    from paper_2007_08501_gb300 import ops
+    ops._lib = None
+    L = ops.load()
+    ok = ops.make_rast_params(16, 8192, 4, 1e-3, 16, 256)           # 2^22 bins x 256 entries
+    assert L.rast_workspace_bytes(ctypes.byref(ok), 100, 200) > 0
+    many_bins = ops.make_rast_params(65535, 8192, 4, 1e-3, 8, 1)    # 65535 x 1024^2 bins
+    assert L.rast_workspace_bytes(ctypes.byref(many_bins), 100, 200) == 0
+    big_cap = ops.make_rast_params(16, 8192, 4, 1e-3, 16, 1 << 20)  # 2^22 bins x 2^20 entries
+    assert L.rast_workspace_bytes(ctypes.byref(big_cap), 100, 200) == 0
+    big_entries = ops.make_rast_params(1, 64, 4, 1e-3, 16, 128, max_bin_entries=1 << 31)
+    assert L.rast_workspace_bytes(ctypes.byref(big_entries), 100, 200) == 0
+    for p in (many_bins, big_cap, big_entries):
+        assert L.rast_mesh_fwd(ctypes.byref(p), None, 0, None, 0, None, None, None, None, None, None, None,
+                               None, 0, None) == ops.MESHRAST_ERR_UNSUPPORTED
+    pp = ops.make_pts_params(16, 8192, 4, 0.01, 16, 1 << 20)
+    assert L.pts_workspace_bytes(ctypes.byref(pp), 100) == 0
+    pp = ops.make_pts_params(16, 8192, 4, 0.01, 16, 256)
+    assert L.pts_workspace_bytes(ctypes.byref(pp), 100) > 0
+
+
 def test_fragment_free_forward_is_refused_outside_the_fine_pass_blend(lib):
     from paper_2007_08501_gb300 import ops
     ops._lib = None

@@ -3,8 +3,12 @@ memory (the library's built-in 16 MiB array stands in for the workspace).
 
 Checked through the C ABI against rast_mesh_fwd on the same inputs, on two
 calls in a row with different batches, so that contents left in the shared
-array by the first call cannot leak into the second.  This file sorts last so
-that a run stopping at the first failure has already run every other test.
+array by the first call cannot leak into the second.  The same kernels run on
+the same inputs, so the outputs must be identical bit for bit.  A warmed-up
+call must not change the device's free memory, and its status word (read
+with rast_query_static_status) must report a forced bin overflow.  This file
+sorts last so that a run stopping at the first failure has already run every
+other test.
 """
 import numpy as np
 import pytest
@@ -34,15 +38,14 @@ def _both(b, S, K, bin_size, max_per_bin, clip=True):
         t.fill_(7)          # anything the call fails to write shows up
     ops.rast_mesh_fwd_static(p, v, f, ff, nf, cams, *got)
     torch.cuda.synchronize()
+    assert ops.rast_query_static_status() == 0
     return ref, got
 
 
 def _same(ref, got):
-    # the same kernels run on the same inputs: identical ids, and values
-    # within the fragment tolerance of the parity tests
-    np.testing.assert_array_equal(ref[0].cpu().numpy(), got[0].cpu().numpy())
-    for a, b in zip(ref[1:], got[1:]):
-        assert np.max(np.abs(a.cpu().numpy() - b.cpu().numpy())) <= 1e-5
+    # the same kernels run on the same inputs: every output identical
+    for a, b in zip(ref, got):
+        assert torch.equal(a, b)
 
 
 def test_static_workspace_forward_matches_rast_mesh_fwd_twice():
@@ -54,6 +57,27 @@ def test_static_workspace_forward_matches_rast_mesh_fwd_twice():
     ref2, got2 = _both(b2, 100, 3, 8, 512, clip=False)
     _same(ref2, got2)
     assert (ref2[0] >= 0).any()
+
+
+def test_static_call_allocates_nothing_and_reports_its_status():
+    b = workloads.sphere_batch([2, 2], 0.05, seed_base=17)
+    v, f, ff, nf, cams = _dev(b)
+    fr = ops.alloc_fragments(b.N, 64, 4)
+    p = ops.make_rast_params(b.N, 64, 4, BLUR, 16, 512, True, True)
+    ops.rast_mesh_fwd_static(p, v, f, ff, nf, cams, *fr)      # warm-up: address lookup, lazy loading
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    ops.rast_mesh_fwd_static(p, v, f, ff, nf, cams, *fr)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert ops.rast_query_static_status() == 0
+    # a bin capacity of 1 face overflows: the status word says so
+    tiny = ops.make_rast_params(b.N, 64, 4, BLUR, 16, 1, True, True)
+    ops.rast_mesh_fwd_static(tiny, v, f, ff, nf, cams, *fr)
+    assert ops.rast_query_static_status() & ops.ST_BIN_OVERFLOW
+    # the next call starts from a clean status word
+    ops.rast_mesh_fwd_static(p, v, f, ff, nf, cams, *fr)
+    assert ops.rast_query_static_status() == 0
 
 
 def test_static_workspace_rejects_requests_beyond_its_size():
