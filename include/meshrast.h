@@ -323,6 +323,9 @@ typedef struct {
     int64_t NB;                            /* N * nb * nb */
     int64_t capacity;                      /* entries lists can hold */
     int64_t bytes;                         /* = rast_workspace_bytes */
+    int64_t redo;                          /* uint32 at this byte offset: pixels the large-K (K > 16)
+                                              fine pass handed to a whole warp (their unsettled
+                                              candidates outgrew the per-pixel ring) */
 } rast_bin_layout;
 MESHRAST_API int rast_workspace_bin_layout(const rast_params *p, int64_t V, int64_t F, rast_bin_layout *out);
 

@@ -22,6 +22,7 @@ bool ws_layout(const rast_params *p, int64_t V, int64_t F, mr::WsLayout *L) {
     L->queue = 4;
     L->total = 8;
     L->maxcount = 16;
+    L->redo = 20;
     off = 256;
     L->records = off;
     off = align256(off + (size_t)F * sizeof(mr::FaceRec));
@@ -221,14 +222,39 @@ static int forward(const rast_params *p, const float *verts, int64_t V, const in
     ka.eff = reinterpret_cast<const int *>(ws + L.eff);
     ka.offsets = reinterpret_cast<const int *>(ws + L.offsets);
     ka.queue = reinterpret_cast<unsigned *>(ws + L.queue);
+    ka.redo_count = reinterpret_cast<unsigned *>(ws + L.redo);
     ka.items = (int)L.NB;
     ka.nb = (int)L.nb;
     ka.S = (int)S;
     ka.K = (int)K;
     ka.fl = fl;
     ka.out = out;
-    ka.sort_cap = mr::fine_sort_cap(p->max_faces_per_bin, (int)K, p->bin_size * p->bin_size);
     std::memset(&ka.blend, 0, sizeof(ka.blend));
+    // Large K: the front-to-back streaming fine pass, when every bin's list is
+    // sorted as one piece (capacity <= 8192) and a candidate's depth is never
+    // below its face's nearest corner (clipped barycentrics, or no blur);
+    // Fragment attributes (and the silhouette blend) in a pass of their own.
+    const bool zcull = p->clip_barycentric_coords || !(p->blur_radius > 0.f);
+    if (K > 16 && zcull && p->max_faces_per_bin <= 8192 && pix_to_face && zbuf && bary && dists) {
+        int cap = 256;
+        while (cap < p->max_faces_per_bin) cap <<= 1;
+        ka.sort_cap = cap;
+        if (mr::launch_fine_stream(ka, p->bin_size, st) != cudaSuccess) return MESHRAST_ERR_CUDA;
+        mr::FragAttrArgs fa2;
+        fa2.rec = ka.rec;
+        fa2.out = out;
+        fa2.F = F;
+        fa2.status = reinterpret_cast<unsigned *>(ws + L.status);
+        fa2.P = (int64_t)p->N * S * S;
+        fa2.S = (int)S;
+        fa2.K = (int)K;
+        fa2.fl = fl;
+        fa2.sigma = blend ? blend->sigma : 1.f;
+        fa2.image = (blend && !blend->rgb) ? blend->image : nullptr;
+        if (fa2.image && blended) *blended = true;
+        return mr::launch_frag_attr(fa2, st) == cudaSuccess ? MESHRAST_OK : MESHRAST_ERR_CUDA;
+    }
+    ka.sort_cap = mr::fine_sort_cap(p->max_faces_per_bin, (int)K, p->bin_size * p->bin_size);
     if (fine_blend) {
         ka.blend = *blend;
         ka.blend.frag = no_frag ? 0 : 1;
@@ -532,6 +558,7 @@ int rast_workspace_bin_layout(const rast_params *p, int64_t V, int64_t F, rast_b
     out->NB = L.NB;
     out->capacity = L.capacity;
     out->bytes = (int64_t)L.bytes;
+    out->redo = (int64_t)L.redo;
     return MESHRAST_OK;
 }
 

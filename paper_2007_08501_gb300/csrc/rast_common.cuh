@@ -406,6 +406,7 @@ struct WsLayout {
     size_t queue;       // uint32 work-queue head of the fine pass
     size_t total;       // int64 sum of raw bin counts
     size_t maxcount;    // int32 largest raw bin count
+    size_t redo;        // uint32 pixels the large-K streaming fine pass redid with a whole warp
     size_t records;     // F x FaceRec
     size_t face_mesh;   // F x int32
     size_t counts;      // NB x int32 raw counts

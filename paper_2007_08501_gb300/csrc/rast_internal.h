@@ -73,11 +73,26 @@ struct FineArgs {
     unsigned long long *lists;  // K > 16: each block sorts its bins' lists in place
     const int *eff, *offsets;
     unsigned *queue;
+    unsigned *redo_count;       // large-K streaming pass: pixels redone by a whole warp
     int items, nb, S, K;
     int sort_cap;  // bin entries sorted at a time (power of two)
     EvalFlags fl;
     FineOut out;
     FineBlend blend;
+};
+
+// Fragment attributes after the large-K streaming fine pass: pix_to_face holds
+// (depth bits << 32) | face id per slot (-1: empty) on entry.
+struct FragAttrArgs {
+    const FaceRec *rec;
+    FineOut out;
+    int64_t F;        // faces in the batch (a key's face id must be below)
+    unsigned *status;
+    int64_t P;        // pixels
+    int S, K;
+    EvalFlags fl;
+    float sigma;
+    float *image;     // non-NULL: silhouette blend (Algorithm 1) into (P, 4)
 };
 
 struct NaiveArgs {
@@ -128,6 +143,10 @@ cudaError_t launch_fill(const FillArgs &a, cudaStream_t st);
 cudaError_t launch_fine(const FineArgs &a, int bin, cudaStream_t st);
 bool fine_blends(int K, bool rgb);  // whether launch_fine applies FineArgs::blend
 cudaError_t launch_naive(const NaiveArgs &a, int N, cudaStream_t st);
+// large K: front-to-back streaming fine pass + attribute pass (fine_stream.cu)
+size_t fine_stream_smem(int sort_cap, int bin);
+cudaError_t launch_fine_stream(const FineArgs &a, int bin, cudaStream_t st);
+cudaError_t launch_frag_attr(const FragAttrArgs &a, cudaStream_t st);
 cudaError_t launch_rast_bwd(const RastBwdArgs &a, int N, cudaStream_t st);
 cudaError_t launch_blend_fwd(const BlendArgs &a, cudaStream_t st);
 cudaError_t launch_blend_bwd(const BlendArgs &a, cudaStream_t st);

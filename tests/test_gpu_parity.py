@@ -62,6 +62,39 @@ def test_large_k_shared_memory_path():
         _full_check(b, 48, 50, BLUR, bs, True, True)
 
 
+@pytest.mark.parametrize("S,K,bin_size", [(48, 50, 16), (70, 50, 16), (70, 20, 8), (40, 64, 16), (33, 17, 8)])
+def test_large_k_streaming_path(S, K, bin_size):
+    # clipped barycentrics, K > 16: the front-to-back streaming fine pass and
+    # the attribute pass (ragged images, K up to the 64 maximum)
+    b = workloads.sphere_batch([3, 3], 0.05, seed_base=91)
+    _full_check(b, S, K, BLUR, bin_size, True, True)
+
+
+def test_large_k_ring_overflow_is_redone_by_a_warp():
+    """30 faces tilted away from the camera: each has one corner at depth 1 (its
+    sort key), while at the pixels near its far edge its depth is ~5.  No
+    candidate settles before the bin's list ends, so more than the 16 a pixel
+    keeps on chip are unsettled at once: those pixels are redone by a warp."""
+    from _scenes import ndc_triangle, scene
+    tris = [ndc_triangle((-0.6 + 0.002 * i, -0.6), (0.6, -0.6 + 0.001 * i), (0.0, 0.9), (5.0 + 0.01 * i, 5.0, 1.0))
+            for i in range(30)]
+    sc = scene(tris)
+    S, K = 32, 40
+    d = to_dev(sc)
+    fr, status, p, ws = gpu_fwd(d, S, K, BLUR, 16, True, True)
+    assert status == 0
+    L = ops.rast_workspace_bin_layout(p, d["verts"].shape[0], d["faces"].shape[0])
+    redo = int(ws[L["redo"]:L["redo"] + 4].cpu().numpy().view(np.uint32)[0])
+    print("pixels redone by a warp: %d" % redo)
+    assert redo > 0
+    m = oracle_mesh(sc)
+    orc = oracle.rasterize(m, S, K, BLUR, True, True)
+    amb = oracle.margins(m, S, K, BLUR, True, True) & oracle.FWD_AMBIGUOUS
+    n_amb, n_bad = compare_frags(np_frags(fr), orc, amb)
+    assert n_bad == 0 and n_amb < 0.5 * amb.size
+    assert (orc[0][:, 20] >= 0).any()   # some pixels hold more than 20 faces
+
+
 @pytest.mark.parametrize("level,S,K,bin_size,clip", [
     (6, 32, 4, 16, True),     # ~20k faces per bin: sorted in segments of 8192
     (6, 32, 4, 16, False),    # unclipped blur: no depth cull, every segment walked
