@@ -189,7 +189,7 @@ __device__ __forceinline__ void bary_adjoint(const T (&b)[3], const T (&iz)[3], 
 // sphere seen edge-on near its silhouette).  Every input is taken at full
 // accuracy: the corners and the pixel as double-float sums, the barycentrics
 // from edge functions of those.
-__device__ __noinline__ void bary_adjoint_f64(const FaceRec &R, const PixC &p, int persp, int clip, bool inside,
+static __device__ __noinline__ void bary_adjoint_f64(const FaceRec &R, const PixC &p, int persp, int clip, bool inside,
                                               float gbp0, float gbp1, float gbp2, float gz, float (&gx)[3],
                                               float (&gy)[3], float (&gZ)[3]) {
     const double qx = ((double)p.xh - (double)R.a.x) + ((double)p.xl - (double)R.a.z);
