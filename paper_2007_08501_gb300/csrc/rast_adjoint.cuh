@@ -22,13 +22,13 @@ __device__ __forceinline__ void corner_df(const FaceRec &R, int i, df &x, df &y)
 
 __device__ __forceinline__ void edge_residual(const FaceRec &R, const PixC &p, int edge, float t, float &rx,
                                               float &ry) {
-    const df qx = df_add(two_sum(p.xh, -R.a.x), two_sum(p.xl, -R.a.z));
-    const df qy = df_add(two_sum(p.yh, -R.a.y), two_sum(p.yl, -R.a.w));
+    df qx, qy;
+    local_q_df(R, p, qx, qy);
     const int ia = edge, ib = (edge == 2) ? 0 : edge + 1;
     if (t <= 0.f || t >= 1.f) {
         df cx, cy;
         corner_df(R, (t <= 0.f) ? ia : ib, cx, cy);
-        const df dx = df_sub(qx, cx), dy = df_sub(qy, cy);
+        const df dx = df_sub_fast(qx, cx), dy = df_sub_fast(qy, cy);
         rx = __fadd_rn(dx.hi, dx.lo);
         ry = __fadd_rn(dy.hi, dy.lo);
         return;
@@ -36,11 +36,10 @@ __device__ __forceinline__ void edge_residual(const FaceRec &R, const PixC &p, i
     df axd, ayd, bxd, byd;
     corner_df(R, ia, axd, ayd);
     corner_df(R, ib, bxd, byd);
-    const df ex = df_sub(bxd, axd), ey = df_sub(byd, ayd);
-    const df cr = df_cross(ex, ey, df_sub(qx, axd), df_sub(qy, ayd));
-    const float c = __fadd_rn(cr.hi, cr.lo);
+    const df ex = df_sub_fast(bxd, axd), ey = df_sub_fast(byd, ayd);
+    const float c = df_cross_f(ex, ey, df_sub_fast(qx, axd), df_sub_fast(qy, ayd));
     const float exf = __fadd_rn(ex.hi, ex.lo), eyf = __fadd_rn(ey.hi, ey.lo);
-    const float s = __fdiv_rn(c, __fmaf_rn(exf, exf, __fmul_rn(eyf, eyf)));
+    const float s = __fdividef(c, __fmaf_rn(exf, exf, __fmul_rn(eyf, eyf)));
     rx = -eyf * s;
     ry = exf * s;
 }

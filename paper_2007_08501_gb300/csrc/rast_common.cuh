@@ -163,21 +163,45 @@ __device__ __forceinline__ void screen_bary(const FaceRec &r, float qx, float qy
     b2 = __fmul_rn(e2, r.d.x);
 }
 
-// Screen barycentrics in double-float: q = p - v0, u, w and the three edge
-// functions carried as hi + lo, then scaled by 1/A.
-__device__ __forceinline__ df df_cross(df ax, df ay, df bx, df by) {
-    return df_sub(df_mul(ax, by), df_mul(ay, bx));
+// Double-float difference a - b with the rounding error of the high parts
+// kept exactly (two-sum) and the low parts added to it: not renormalised, good
+// to ~1e-14 relative, which is all the cross products below need.
+__device__ __forceinline__ df df_sub_fast(df a, df b) {
+    const df s = two_sum(a.hi, -b.hi);
+    return {s.hi, __fadd_rn(s.lo, __fsub_rn(a.lo, b.lo))};
 }
+
+// cross(a, b) = ax by - ay bx of double-float vectors, rounded once: the
+// products of the high parts and their difference are exact (fma, two-sum),
+// the low parts enter to first order.  ~17 instructions.
+__device__ __forceinline__ float df_cross_f(df ax, df ay, df bx, df by) {
+    const float p = __fmul_rn(ax.hi, by.hi), pe = __fmaf_rn(ax.hi, by.hi, -p);
+    const float r = __fmul_rn(ay.hi, bx.hi), re = __fmaf_rn(ay.hi, bx.hi, -r);
+    const df d = two_sum(p, -r);
+    const float lo = __fmaf_rn(ax.hi, by.lo, __fmaf_rn(ax.lo, by.hi, -__fmaf_rn(ay.hi, bx.lo, __fmul_rn(ay.lo, bx.hi))));
+    return __fadd_rn(d.hi, __fadd_rn(d.lo, __fadd_rn(__fsub_rn(pe, re), lo)));
+}
+
+// pixel minus corner 0, as a double-float
+__device__ __forceinline__ void local_q_df(const FaceRec &r, const PixC &p, df &qx, df &qy) {
+    qx = df_sub_fast({p.xh, p.xl}, {r.a.x, r.a.z});
+    qy = df_sub_fast({p.yh, p.yl}, {r.a.y, r.a.w});
+}
+
+// Screen barycentrics from edge functions of the double-float corners and
+// pixel (q = p - v0, u, w), each edge function rounded once, then scaled by
+// 1/A: every component keeps ~1e-7 relative accuracy, even near zero and on
+// slivers seen edge-on.
 __device__ __forceinline__ void screen_bary_df(const FaceRec &r, const PixC &p, float &b0, float &b1, float &b2) {
-    const df qx = df_add(two_sum(p.xh, -r.a.x), two_sum(p.xl, -r.a.z));
-    const df qy = df_add(two_sum(p.yh, -r.a.y), two_sum(p.yl, -r.a.w));
+    df qx, qy;
+    local_q_df(r, p, qx, qy);
     const df ux = {r.b.x, r.e.x}, uy = {r.b.y, r.e.y}, wx = {r.b.z, r.e.z}, wy = {r.b.w, r.e.w};
-    const df e2 = df_cross(ux, uy, qx, qy);
-    const df e1 = df_cross(qx, qy, wx, wy);
-    const df e0 = df_cross(df_sub(wx, ux), df_sub(wy, uy), df_sub(qx, ux), df_sub(qy, uy));
-    b0 = __fmul_rn(__fadd_rn(e0.hi, e0.lo), r.d.x);
-    b1 = __fmul_rn(__fadd_rn(e1.hi, e1.lo), r.d.x);
-    b2 = __fmul_rn(__fadd_rn(e2.hi, e2.lo), r.d.x);
+    const float e2 = df_cross_f(ux, uy, qx, qy);
+    const float e1 = df_cross_f(qx, qy, wx, wy);
+    const float e0 = df_cross_f(df_sub_fast(wx, ux), df_sub_fast(wy, uy), df_sub_fast(qx, ux), df_sub_fast(qy, uy));
+    b0 = __fmul_rn(e0, r.d.x);
+    b1 = __fmul_rn(e1, r.d.x);
+    b2 = __fmul_rn(e2, r.d.x);
 }
 
 // squared distance from (qx,qy) to segment a + t e, t in [0,1]; returns s, t
@@ -334,7 +358,8 @@ __device__ __forceinline__ void face_fragment(const FaceRec &r, const PixC &p, c
     float t;
     float s = nearest_edge(r, qx, qy, e, t);
     dist = inside ? -s : s;
-    (void)face_depth<true>(r, fl.persp, fl.clip, inside, b0, b1, b2, bp);
+    // approximate (~2 ulp) reciprocals: the barycentrics keep ~3e-7 relative
+    (void)face_depth<true, true>(r, fl.persp, fl.clip, inside, b0, b1, b2, bp);
 }
 
 // strict total order on (depth, face id)
