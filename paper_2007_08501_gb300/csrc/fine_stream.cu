@@ -141,6 +141,16 @@ __device__ void redo_pixel(const FineArgs &a, const unsigned long long *ent, int
 // ---------------------------------------------------------------------------
 // the streaming fine pass
 // ---------------------------------------------------------------------------
+// Pixel of thread t in a BS x BS bin: each warp covers an 8 x 4 block (8
+// columns, 4 rows) rather than two full rows, so that the warp's footprint is
+// about as wide as tall, like the inflated face bboxes it is culled against.
+template <int BS>
+__device__ __forceinline__ void tile_pixel_of(int t, int &ty, int &tx) {
+    const int lane = t & 31, warp = t >> 5;
+    ty = (warp / (BS / 8)) * 4 + (lane >> 3);
+    tx = (warp % (BS / 8)) * 8 + (lane & 7);
+}
+
 template <int BS>
 __global__ void __launch_bounds__(BS *BS, BS == 16 ? 3 : 8) k_fine_stream(FineArgs a) {
     constexpr int BD = BS * BS;
@@ -154,7 +164,8 @@ __global__ void __launch_bounds__(BS *BS, BS == 16 ? 3 : 8) k_fine_stream(FineAr
     float *ring_z = reinterpret_cast<float *>(s_sort + a.sort_cap);
     int *ring_f = reinterpret_cast<int *>(ring_z + kRing * BD);
     const int tid = threadIdx.x;
-    const int ty = tid / BS, tx = tid % BS;
+    int ty, tx;
+    tile_pixel_of<BS>(tid, ty, tx);
     const int lane = tid & 31, warp = tid >> 5;
     float *rz = ring_z + tid;  // ring entry j at rz[j * BD]
     int *rf = ring_f + tid;
@@ -310,8 +321,9 @@ __global__ void __launch_bounds__(BS *BS, BS == 16 ? 3 : 8) k_fine_stream(FineAr
         __syncthreads();
         const int nredo = s_nredo;
         for (int i = warp; i < nredo; i += BD / 32) {
-            const int t = s_redo[i];
-            redo_pixel(a, s_sort, cnt, n, by * BS + t / BS, bx * BS + t % BS, fl);
+            int rty, rtx;
+            tile_pixel_of<BS>(s_redo[i], rty, rtx);
+            redo_pixel(a, s_sort, cnt, n, by * BS + rty, bx * BS + rtx, fl);
         }
         if (nredo > 0 && lane == 0 && warp == 0) atomicAdd(a.redo_count, (unsigned)nredo);
         __syncthreads();  // s_sort, s_item and s_nredo are reused by the next item
@@ -333,17 +345,36 @@ __global__ void __launch_bounds__(256) k_frag_attr(FragAttrArgs a) {
     const PixC p = pixel_centre(r, c, S);
     const int64_t s0 = pix * K;
     float keep = 1.f;
+    // both of the lane's slots: keys and face records are loaded before either
+    // is evaluated (two gathers in flight per lane)
+    long long v[2];
+    FaceRec R[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int k = lane + 32 * h;
+        v[h] = (k < K) ? a.out.pix_to_face[s0 + k] : -1ll;
+        // a key names a face of the batch; anything else (never written by the
+        // fine pass) is reported and treated as an empty slot
+        if (v[h] >= 0 && (long long)(unsigned)(v[h] & 0xffffffffll) >= a.F) {
+            set_status(a.status, MESHRAST_ST_BAD_INDEX);
+            v[h] = -1ll;
+        }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (v[h] < 0) continue;
+        const float4 *src = reinterpret_cast<const float4 *>(a.rec + (int)(unsigned)(v[h] & 0xffffffffll));
+        R[h].a = __ldg(src);
+        R[h].b = __ldg(src + 1);
+        R[h].d = __ldg(src + 3);
+        R[h].e = __ldg(src + 4);
+    }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int k = lane + 32 * h;
         if (k >= K) break;
         const int64_t s = s0 + k;
-        const long long v = a.out.pix_to_face[s];
-        // a key names a face of the batch; anything else (never written by the
-        // fine pass) is reported and treated as an empty slot
-        const bool bad = v >= 0 && (long long)(unsigned)(v & 0xffffffffll) >= a.F;
-        if (bad) set_status(a.status, MESHRAST_ST_BAD_INDEX);
-        if (v < 0 || bad) {
+        if (v[h] < 0) {
             a.out.pix_to_face[s] = -1ll;
             a.out.zbuf[s] = -1.f;
             a.out.bary[3 * s] = -1.f;
@@ -352,16 +383,10 @@ __global__ void __launch_bounds__(256) k_frag_attr(FragAttrArgs a) {
             a.out.dists[s] = -1.f;
             continue;
         }
-        const int f = (int)(unsigned)(v & 0xffffffffll);
-        const float z = __uint_as_float((unsigned)((unsigned long long)v >> 32));
-        FaceRec R;
-        const float4 *src = reinterpret_cast<const float4 *>(a.rec + f);
-        R.a = __ldg(src);
-        R.b = __ldg(src + 1);
-        R.d = __ldg(src + 3);
-        R.e = __ldg(src + 4);
+        const int f = (int)(unsigned)(v[h] & 0xffffffffll);
+        const float z = __uint_as_float((unsigned)((unsigned long long)v[h] >> 32));
         float bp[3], d;
-        face_fragment(R, p, a.fl, bp, d);
+        face_fragment(R[h], p, a.fl, bp, d);
         a.out.pix_to_face[s] = f;
         a.out.zbuf[s] = z;
         a.out.bary[3 * s] = bp[0];
