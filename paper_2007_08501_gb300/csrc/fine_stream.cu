@@ -107,13 +107,13 @@ __device__ void redo_pixel(const FineArgs &a, const unsigned long long *ent, int
             fid = (int)(unsigned)(v & 0xffffffffull);
             const float4 *src = reinterpret_cast<const float4 *>(a.rec + fid);
             FaceRec R;
-            R.c = __ldg(src + 2);
+            R.c = __ldg(src + kRecC);
             if (in_bbox(R, p)) {
-                R.a = __ldg(src);
-                R.b = __ldg(src + 1);
-                R.d = __ldg(src + 3);
-                R.e = __ldg(src + 4);
-                R.h = __ldg(src + 5);
+                R.a = __ldg(src + kRecA);
+                R.b = __ldg(src + kRecB);
+                R.d = __ldg(src + kRecD);
+                R.e = __ldg(src + kRecE);
+                R.h = __ldg(src + kRecH);
                 hit = face_key_nobbox(R, p, fl, z);
             }
         }
@@ -218,12 +218,12 @@ __global__ void __launch_bounds__(BS *BS, BS == 16 ? 3 : 8) k_fine_stream(FineAr
                 s_key[tid] = __uint_as_float((unsigned)(v >> 32));
                 const float4 *src = reinterpret_cast<const float4 *>(a.rec + fid);
                 FaceRec R;
-                R.a = __ldg(src);
-                R.b = __ldg(src + 1);
-                R.c = __ldg(src + 2);
-                R.d = __ldg(src + 3);
-                R.e = __ldg(src + 4);
-                R.h = __ldg(src + 5);
+                R.a = __ldg(src + kRecA);
+                R.b = __ldg(src + kRecB);
+                R.c = __ldg(src + kRecC);
+                R.d = __ldg(src + kRecD);
+                R.e = __ldg(src + kRecE);
+                R.h = __ldg(src + kRecH);
                 s_rec[tid] = R;
             }
             __syncthreads();
@@ -331,75 +331,74 @@ __global__ void __launch_bounds__(BS *BS, BS == 16 ? 3 : 8) k_fine_stream(FineAr
 }
 
 // ---------------------------------------------------------------------------
-// Fragment attributes: one warp per pixel, lane k (and k + 32) per slot
+// Fragment attributes: a block takes PB = 256 / K whole pixels, one thread per
+// slot in output order (consecutive threads, consecutive slots: coalesced)
 // ---------------------------------------------------------------------------
 template <bool BL>
 __global__ void __launch_bounds__(256) k_frag_attr(FragAttrArgs a) {
-    const int lane = threadIdx.x & 31;
-    const int64_t pix = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (pix >= a.P) return;  // warp-uniform
-    const int S = a.S, K = a.K;
-    const int64_t n = pix / ((int64_t)S * S);
-    const int rem = (int)(pix - n * S * S);
-    const int r = rem / S, c = rem - r * S;
-    const PixC p = pixel_centre(r, c, S);
-    const int64_t s0 = pix * K;
+    __shared__ float s_keep[256];
+    const int K = a.K, S = a.S;
+    const int PB = 256 / K;
+    const int t = threadIdx.x;
+    const int64_t pix0 = (int64_t)blockIdx.x * PB;
+    const int lp = t / K, k = t - lp * K;
+    const int64_t pix = pix0 + lp;
+    const bool active = lp < PB && pix < a.P;
     float keep = 1.f;
-    // both of the lane's slots: keys and face records are loaded before either
-    // is evaluated (two gathers in flight per lane)
-    long long v[2];
-    FaceRec R[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int k = lane + 32 * h;
-        v[h] = (k < K) ? a.out.pix_to_face[s0 + k] : -1ll;
+    if (active) {
+        const int64_t s = pix * K + k;
+        long long v = a.out.pix_to_face[s];
         // a key names a face of the batch; anything else (never written by the
         // fine pass) is reported and treated as an empty slot
-        if (v[h] >= 0 && (long long)(unsigned)(v[h] & 0xffffffffll) >= a.F) {
+        if (v >= 0 && (long long)(unsigned)(v & 0xffffffffll) >= a.F) {
             set_status(a.status, MESHRAST_ST_BAD_INDEX);
-            v[h] = -1ll;
+            v = -1ll;
         }
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        if (v[h] < 0) continue;
-        const float4 *src = reinterpret_cast<const float4 *>(a.rec + (int)(unsigned)(v[h] & 0xffffffffll));
-        R[h].a = __ldg(src);
-        R[h].b = __ldg(src + 1);
-        R[h].d = __ldg(src + 3);
-        R[h].e = __ldg(src + 4);
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int k = lane + 32 * h;
-        if (k >= K) break;
-        const int64_t s = s0 + k;
-        if (v[h] < 0) {
+        if (v < 0) {
             a.out.pix_to_face[s] = -1ll;
             a.out.zbuf[s] = -1.f;
             a.out.bary[3 * s] = -1.f;
             a.out.bary[3 * s + 1] = -1.f;
             a.out.bary[3 * s + 2] = -1.f;
             a.out.dists[s] = -1.f;
-            continue;
+        } else {
+            const int f = (int)(unsigned)(v & 0xffffffffll);
+            const float z = __uint_as_float((unsigned)((unsigned long long)v >> 32));
+            const float4 *src = reinterpret_cast<const float4 *>(a.rec + f);
+            FaceRec R;
+            R.a = __ldg(src + kRecA);
+            R.b = __ldg(src + kRecB);
+            R.d = __ldg(src + kRecD);
+            R.e = __ldg(src + kRecE);
+            const int64_t n = pix / ((int64_t)S * S);
+            const int rem = (int)(pix - n * S * S);
+            const int r = rem / S, c = rem - r * S;
+            float bp[3], d;
+            face_fragment(R, pixel_centre(r, c, S), a.fl, bp, d);
+            a.out.pix_to_face[s] = f;
+            a.out.zbuf[s] = z;
+            a.out.bary[3 * s] = bp[0];
+            a.out.bary[3 * s + 1] = bp[1];
+            a.out.bary[3 * s + 2] = bp[2];
+            a.out.dists[s] = d;
+            if constexpr (BL) keep = sigmoidf_(d / a.sigma);
         }
-        const int f = (int)(unsigned)(v[h] & 0xffffffffll);
-        const float z = __uint_as_float((unsigned)((unsigned long long)v[h] >> 32));
-        float bp[3], d;
-        face_fragment(R[h], p, a.fl, bp, d);
-        a.out.pix_to_face[s] = f;
-        a.out.zbuf[s] = z;
-        a.out.bary[3 * s] = bp[0];
-        a.out.bary[3 * s + 1] = bp[1];
-        a.out.bary[3 * s + 2] = bp[2];
-        a.out.dists[s] = d;
-        if constexpr (BL) keep *= sigmoidf_(d / a.sigma);
     }
     if constexpr (BL) {
-        // Algorithm 1: alpha = 1 - prod_k (1 - prob_k); fixed tree order over the lanes
+        // Algorithm 1: alpha = 1 - prod_k (1 - prob_k); one warp per pixel
+        // multiplies its K factors in a fixed tree order
+        s_keep[t] = keep;
+        __syncthreads();
+        const int lane = t & 31;
+        for (int q = t >> 5; q < PB; q += 8) {
+            const int64_t qp = pix0 + q;
+            float m = 1.f;
+            if (lane < K) m = s_keep[q * K + lane];
+            if (lane + 32 < K) m *= s_keep[q * K + lane + 32];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) keep *= __shfl_xor_sync(0xffffffffu, keep, o);
-        if (lane == 0) reinterpret_cast<float4 *>(a.image)[pix] = make_float4(0.f, 0.f, 0.f, 1.f - keep);
+            for (int o = 16; o > 0; o >>= 1) m *= __shfl_xor_sync(0xffffffffu, m, o);
+            if (lane == 0 && qp < a.P) reinterpret_cast<float4 *>(a.image)[qp] = make_float4(0.f, 0.f, 0.f, 1.f - m);
+        }
     }
 }
 
@@ -431,7 +430,9 @@ cudaError_t launch_fine_stream(const FineArgs &a, int bin, cudaStream_t st) {
 
 cudaError_t launch_frag_attr(const FragAttrArgs &a, cudaStream_t st) {
     if (a.P <= 0) return cudaSuccess;
-    const int64_t blocks = (a.P + 7) / 8;
+    if (a.K < 1 || a.K > 64) return cudaErrorInvalidValue;
+    const int PB = 256 / a.K;
+    const int64_t blocks = (a.P + PB - 1) / PB;
     if (a.image) k_frag_attr<true><<<(unsigned)blocks, 256, 0, st>>>(a);
     else k_frag_attr<false><<<(unsigned)blocks, 256, 0, st>>>(a);
     return cudaGetLastError();

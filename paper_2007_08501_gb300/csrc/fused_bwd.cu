@@ -34,10 +34,10 @@ __device__ __forceinline__ void slot_vertices(const BlendArgs &a, int64_t s, int
 
 __device__ __forceinline__ void load_adjoint_rec(const FaceRec *rec, int f, FaceRec &R) {
     const float4 *src = reinterpret_cast<const float4 *>(rec + f);
-    R.a = __ldg(src);
-    R.b = __ldg(src + 1);
-    R.d = __ldg(src + 3);
-    R.e = __ldg(src + 4);
+    R.a = __ldg(src + kRecA);
+    R.b = __ldg(src + kRecB);
+    R.d = __ldg(src + kRecD);
+    R.e = __ldg(src + kRecE);
 }
 
 // one lane per face: colour atomics (softmax blend) and vertex atomics

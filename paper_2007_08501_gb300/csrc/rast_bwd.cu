@@ -38,11 +38,11 @@ __global__ void __launch_bounds__(256) k_rast_bwd(RastBwdArgs a) {
         FaceRec R;
         if (f >= 0) {
             const float4 *src = reinterpret_cast<const float4 *>(a.rec + f);
-            R.a = __ldg(src);
-            R.b = __ldg(src + 1);
-            R.c = __ldg(src + 2);
-            R.d = __ldg(src + 3);
-            R.e = __ldg(src + 4);
+            R.a = __ldg(src + kRecA);
+            R.b = __ldg(src + kRecB);
+            R.c = __ldg(src + kRecC);
+            R.d = __ldg(src + kRecD);
+            R.e = __ldg(src + kRecE);
             const float gz = a.grad_zbuf ? a.grad_zbuf[s] : 0.f;
             const float gd = a.grad_dists ? a.grad_dists[s] : 0.f;
             float gb0 = 0.f, gb1 = 0.f, gb2 = 0.f;

@@ -37,7 +37,10 @@ inline int fine_sort_cap(int max_per_bin, int K, int BD) {
 
 // ---------------------------------------------------------------------------
 // Staged face record: 96 bytes, six float4, written once per face by the
-// staging kernel and read by the fine, plain and backward kernels.
+// staging kernel and read by the fine, plain and backward kernels.  In memory
+// the float4s are stored in the order a, b, d, e, c, h (indices kRec*): the
+// four the per-slot passes read (attributes, adjoints) fill the first 64 bytes,
+// two 32-byte sectors, of the record.
 //   a = (v0x_hi, v0y_hi, v0x_lo, v0y_lo)   corner 0 in NDC as a double-float
 //   b = (ux, uy, wx, wy)                   u = v1 - v0, w = v2 - v0 (NDC), high parts
 //   c = (xmin, xmax, ymin, ymax)           bbox inflated by sqrt(blur), rounded outward;
@@ -57,6 +60,8 @@ struct __align__(16) FaceRec {
     float4 a, b, c, d, e, h;
 };
 static_assert(sizeof(FaceRec) == 96, "face record is 96 bytes");
+// float4 index of each field in a record in global memory
+constexpr int kRecA = 0, kRecB = 1, kRecD = 2, kRecE = 3, kRecC = 4, kRecH = 5;
 
 // ---------------------------------------------------------------------------
 // double-float (unevaluated sum hi + lo) arithmetic, error-free transforms

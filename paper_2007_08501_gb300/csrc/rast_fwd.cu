@@ -92,12 +92,12 @@ __global__ void __launch_bounds__(256) k_stage(StageArgs a) {
     if (f < a.F) {
         n = stage_face(a, f, n, R);
         float4 *dst = reinterpret_cast<float4 *>(a.rec + f);
-        dst[0] = R.a;
-        dst[1] = R.b;
-        dst[2] = R.c;
-        dst[3] = R.d;
-        dst[4] = R.e;
-        dst[5] = R.h;
+        dst[kRecA] = R.a;
+        dst[kRecB] = R.b;
+        dst[kRecC] = R.c;
+        dst[kRecD] = R.d;
+        dst[kRecE] = R.e;
+        dst[kRecH] = R.h;
         if (a.face_mesh) a.face_mesh[f] = n;
     }
     if (!a.do_count) return;
@@ -228,8 +228,8 @@ __global__ void __launch_bounds__(256) k_fill(FillArgs a) {
         n = a.face_mesh[f];
         if (n >= 0) {
             const float4 *src = reinterpret_cast<const float4 *>(a.rec + f);
-            R.c = src[2];
-            R.d = src[3];
+            R.c = src[kRecC];
+            R.d = src[kRecD];
         }
     }
     int bx0 = 1, bx1 = 0, by0 = 1, by1 = 0;
@@ -283,11 +283,11 @@ __device__ __forceinline__ void write_pixel(const FineOut &o, int64_t pix, int K
         } else {
             FaceRec R;
             const float4 *src = reinterpret_cast<const float4 *>(rec + f);
-            R.a = __ldg(src);
-            R.b = __ldg(src + 1);
-            R.c = __ldg(src + 2);
-            R.d = __ldg(src + 3);
-            R.e = __ldg(src + 4);
+            R.a = __ldg(src + kRecA);
+            R.b = __ldg(src + kRecB);
+            R.c = __ldg(src + kRecC);
+            R.d = __ldg(src + kRecD);
+            R.e = __ldg(src + kRecE);
             float bp[3], d;
             face_fragment(R, p, fl, bp, d);
             if (store) {
@@ -345,11 +345,11 @@ __device__ __forceinline__ void write_pixel_vec(const FineOut &o, int64_t pix, i
             if (tk.f[k] == 0x7fffffff) continue;
             FaceRec R;
             const float4 *src = reinterpret_cast<const float4 *>(rec + tk.f[k]);
-            R.a = __ldg(src);
-            R.b = __ldg(src + 1);
-            R.c = __ldg(src + 2);
-            R.d = __ldg(src + 3);
-            R.e = __ldg(src + 4);
+            R.a = __ldg(src + kRecA);
+            R.b = __ldg(src + kRecB);
+            R.c = __ldg(src + kRecC);
+            R.d = __ldg(src + kRecD);
+            R.e = __ldg(src + kRecE);
             face_fragment(R, p, fl, bb[i], dd[i]);
             zz[i] = tk.z[k];
             if constexpr (BL) fb.slot(bl, tk.f[k], zz[i], dd[i], bb[i]);
@@ -380,11 +380,11 @@ __device__ __forceinline__ void write_pixel_smem(const FineOut &o, int64_t pix, 
         } else {
             FaceRec R;
             const float4 *src = reinterpret_cast<const float4 *>(rec + f);
-            R.a = __ldg(src);
-            R.b = __ldg(src + 1);
-            R.c = __ldg(src + 2);
-            R.d = __ldg(src + 3);
-            R.e = __ldg(src + 4);
+            R.a = __ldg(src + kRecA);
+            R.b = __ldg(src + kRecB);
+            R.c = __ldg(src + kRecC);
+            R.d = __ldg(src + kRecD);
+            R.e = __ldg(src + kRecE);
             float bp[3], d;
             face_fragment(R, p, fl, bp, d);
             o.pix_to_face[s] = f;
@@ -490,12 +490,12 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
                     s_key[tid] = __uint_as_float((unsigned)(v >> 32));
                     const float4 *src = reinterpret_cast<const float4 *>(a.rec + fid);
                     FaceRec R;
-                    R.a = __ldg(src);
-                    R.b = __ldg(src + 1);
-                    R.c = __ldg(src + 2);
-                    R.d = __ldg(src + 3);
-                    R.e = __ldg(src + 4);
-                    R.h = __ldg(src + 5);
+                    R.a = __ldg(src + kRecA);
+                    R.b = __ldg(src + kRecB);
+                    R.c = __ldg(src + kRecC);
+                    R.d = __ldg(src + kRecD);
+                    R.e = __ldg(src + kRecE);
+                    R.h = __ldg(src + kRecH);
                     s_rec[tid] = R;
                 }
                 __syncthreads();
@@ -579,11 +579,11 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
                     const int f = lf[t * K + k];
                     FaceRec R;
                     const float4 *src = reinterpret_cast<const float4 *>(a.rec + f);
-                    R.a = __ldg(src);
-                    R.b = __ldg(src + 1);
-                    R.c = __ldg(src + 2);
-                    R.d = __ldg(src + 3);
-                    R.e = __ldg(src + 4);
+                    R.a = __ldg(src + kRecA);
+                    R.b = __ldg(src + kRecB);
+                    R.c = __ldg(src + kRecC);
+                    R.d = __ldg(src + kRecD);
+                    R.e = __ldg(src + kRecE);
                     float bp[3], d;
                     face_fragment(R, pixel_centre(rr, cc, a.S), fl, bp, d);
                     a.out.pix_to_face[sl] = f;
@@ -636,12 +636,12 @@ __global__ void __launch_bounds__(256) k_naive(NaiveArgs a, int n) {
     for (int64_t f = lo; f < hi; ++f) {
         FaceRec R;
         const float4 *src = reinterpret_cast<const float4 *>(a.rec + f);
-        R.a = __ldg(src);
-        R.b = __ldg(src + 1);
-        R.c = __ldg(src + 2);
-        R.d = __ldg(src + 3);
-        R.e = __ldg(src + 4);
-        R.h = __ldg(src + 5);
+        R.a = __ldg(src + kRecA);
+        R.b = __ldg(src + kRecB);
+        R.c = __ldg(src + kRecC);
+        R.d = __ldg(src + kRecD);
+        R.e = __ldg(src + kRecE);
+        R.h = __ldg(src + kRecH);
         float z;
         if (face_key(R, p, fl, z)) {
             if constexpr (KM > 0) {
