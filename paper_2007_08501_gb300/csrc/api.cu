@@ -235,7 +235,9 @@ static int forward(const rast_params *p, const float *verts, int64_t V, const in
     // below its face's nearest corner (clipped barycentrics, or no blur);
     // Fragment attributes (and the silhouette blend) in a pass of their own.
     const bool zcull = p->clip_barycentric_coords || !(p->blur_radius > 0.f);
-    if (K > 16 && zcull && p->max_faces_per_bin <= 8192 && pix_to_face && zbuf && bary && dists) {
+    // (work items: 32-pixel blocks of every bin, counted by a 32-bit queue)
+    const bool items_fit = L.NB * (int64_t)(p->bin_size * p->bin_size / 32) < 0x7fffffffLL;
+    if (K > 16 && zcull && p->max_faces_per_bin <= 8192 && items_fit && pix_to_face && zbuf && bary && dists) {
         int cap = 256;
         while (cap < p->max_faces_per_bin) cap <<= 1;
         ka.sort_cap = cap;

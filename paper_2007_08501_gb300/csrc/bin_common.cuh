@@ -97,12 +97,80 @@ __device__ __forceinline__ void bin_rect(const FaceRec &R, int S, int bin, int &
     bin_rect_box(R.c, S, bin, bx0, bx1, by0, by1);
 }
 
+// Bitonic sort of N2 = BD * E entries, E consecutive entries per thread in
+// registers: stages whose partner is in the same thread (distance < E) run in
+// registers, stages whose partner is in the same warp (distance < 32 E) go
+// through lane shuffles, and only the few wider ones through shared memory
+// (two barriers each).  Padding entries (all ones) sort last.
+template <int E, int J>
+__device__ __forceinline__ void sort_stage_local(unsigned long long (&v)[E], int k2, int tid) {
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        if (e & J) continue;
+        const int i = tid * E + e;
+        const unsigned long long x = v[e], y = v[e + J];
+        const bool asc = (i & k2) == 0;
+        const unsigned long long lo = x < y ? x : y, hi = x < y ? y : x;
+        v[e] = asc ? lo : hi;
+        v[e + J] = asc ? hi : lo;
+    }
+}
+
+template <int BD, int E>
+__device__ __forceinline__ void sort_entries_regs(unsigned long long *s_sort, const unsigned long long *src, int m) {
+    constexpr int N2 = BD * E;
+    const int tid = threadIdx.x;
+    unsigned long long v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = tid * E + e;
+        v[e] = i < m ? src[i] : ~0ull;
+    }
+#pragma unroll 1
+    for (int k2 = 2; k2 <= N2; k2 <<= 1) {
+#pragma unroll 1
+        for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
+            if (j2 < E) {
+                if constexpr (E > 4) { if (j2 == 4) { sort_stage_local<E, (E > 4 ? 4 : 1)>(v, k2, tid); continue; } }
+                if constexpr (E > 2) { if (j2 == 2) { sort_stage_local<E, (E > 2 ? 2 : 1)>(v, k2, tid); continue; } }
+                sort_stage_local<E, 1>(v, k2, tid);
+                continue;
+            }
+            if (j2 < 32 * E) {
+                const int lm = j2 / E;  // partner lane distance
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    const int i = tid * E + e;
+                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, v[e], lm);
+                    const bool keep_min = ((i & j2) == 0) == ((i & k2) == 0);
+                    v[e] = keep_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
+                }
+                continue;
+            }
+#pragma unroll
+            for (int e = 0; e < E; ++e) s_sort[tid * E + e] = v[e];
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int i = tid * E + e;
+                const unsigned long long o = s_sort[i ^ j2];
+                const bool keep_min = ((i & j2) == 0) == ((i & k2) == 0);
+                v[e] = keep_min ? (o < v[e] ? o : v[e]) : (o > v[e] ? o : v[e]);
+            }
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < E; ++e) s_sort[tid * E + e] = v[e];
+    __syncthreads();
+}
+
 // Sorts m <= sort-buffer bin entries (64-bit keys) from src into s_sort,
 // ascending; every thread of the block (BD threads) must call it.  A segment
 // that fits one entry per thread sorts in registers: partners closer than 32
 // trade through shuffles, farther ones through shared memory.  Larger ones
 // run a bitonic sort in shared memory.  Padding entries (all ones) sort last.
-template <int BD>
+template <int BD, bool REGS = false>
 __device__ __forceinline__ void sort_entries(unsigned long long *s_sort, const unsigned long long *src, int m) {
     const int tid = threadIdx.x;
     int n2 = 32;
@@ -131,6 +199,13 @@ __device__ __forceinline__ void sort_entries(unsigned long long *s_sort, const u
         s_sort[tid] = v;
         __syncthreads();
         return;
+    }
+    // REGS: two to eight entries per thread in registers and shuffles (more
+    // registers, far fewer barriers)
+    if constexpr (REGS) {
+        if (n2 == 2 * BD) { sort_entries_regs<BD, 2>(s_sort, src, m); return; }
+        if (n2 == 4 * BD) { sort_entries_regs<BD, 4>(s_sort, src, m); return; }
+        if (n2 == 8 * BD) { sort_entries_regs<BD, 8>(s_sort, src, m); return; }
     }
     for (int i = tid; i < n2; i += BD) s_sort[i] = i < m ? src[i] : ~0ull;
     __syncthreads();

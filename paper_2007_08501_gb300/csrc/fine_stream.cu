@@ -139,51 +139,54 @@ __device__ void redo_pixel(const FineArgs &a, const unsigned long long *ent, int
 }
 
 // ---------------------------------------------------------------------------
-// the streaming fine pass
+// front-to-back order of every bin's list, sorted in place before the fine
+// pass (one block per bin; small shared memory, many blocks per SM)
 // ---------------------------------------------------------------------------
-// Pixel of thread t in a BS x BS bin: each warp covers an 8 x 4 block (8
-// columns, 4 rows) rather than two full rows, so that the warp's footprint is
-// about as wide as tall, like the inflated face bboxes it is culled against.
-template <int BS>
-__device__ __forceinline__ void tile_pixel_of(int t, int &ty, int &tx) {
-    const int lane = t & 31, warp = t >> 5;
-    ty = (warp / (BS / 8)) * 4 + (lane >> 3);
-    tx = (warp % (BS / 8)) * 8 + (lane & 7);
+__global__ void __launch_bounds__(256) k_sort_bins(FineArgs a) {
+    extern __shared__ unsigned long long s_sort[];
+    for (int item = blockIdx.x; item < a.items; item += gridDim.x) {
+        const int cnt = a.eff[item];  // <= sort_cap (checked on the host); uniform over the block
+        if (cnt <= 1) continue;
+        unsigned long long *list = a.lists + a.offsets[item];
+        sort_entries<256, true>(s_sort, list, cnt);
+        for (int i = threadIdx.x; i < cnt; i += 256) list[i] = s_sort[i];
+        __syncthreads();
+    }
 }
 
+// ---------------------------------------------------------------------------
+// the streaming fine pass: every warp works on its own, with no block
+// barrier.  A work item is an 8 x 4 block of pixels of one bin (8 columns, 4
+// rows: about as wide as tall, like the inflated face bboxes the warp culls
+// against); the warp walks the bin's sorted list from L2 32 entries at a
+// time, each lane keeping its pixel's unsettled candidates in its own ring.
+// ---------------------------------------------------------------------------
+constexpr int kWarpsPerBlock = 8;
+
 template <int BS>
-__global__ void __launch_bounds__(BS *BS, BS == 16 ? 3 : 8) k_fine_stream(FineArgs a) {
-    constexpr int BD = BS * BS;
-    __shared__ FaceRec s_rec[BD];
-    __shared__ int s_id[BD];
-    __shared__ float s_key[BD];
-    __shared__ int s_item, s_nredo;
-    int *s_redo = s_id;  // after the walk: the pixels left for the warp redo
-    // dynamic: the bin's sorted entries (sort_cap), then the rings ([slot][thread])
-    extern __shared__ unsigned long long s_sort[];
-    float *ring_z = reinterpret_cast<float *>(s_sort + a.sort_cap);
-    int *ring_f = reinterpret_cast<int *>(ring_z + kRing * BD);
-    const int tid = threadIdx.x;
-    int ty, tx;
-    tile_pixel_of<BS>(tid, ty, tx);
-    const int lane = tid & 31, warp = tid >> 5;
-    float *rz = ring_z + tid;  // ring entry j at rz[j * BD]
-    int *rf = ring_f + tid;
+__global__ void __launch_bounds__(256, 3) k_fine_stream(FineArgs a) {
+    constexpr int SUB = BS * BS / 32;  // 8 x 4 pixel blocks per bin
+    // per warp: the rings ([slot][lane])
+    __shared__ float s_rz[kWarpsPerBlock][kRing][32];
+    __shared__ int s_rf[kWarpsPerBlock][kRing][32];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    float (*rz)[32] = s_rz[wib];
+    int (*rf)[32] = s_rf[wib];
     EvalFlags fl = a.fl;
     const int nb2 = a.nb * a.nb;
     const int K = a.K;
+    const long long total = (long long)a.items * SUB;
     const float kInf = __int_as_float(0x7f800000);
     while (true) {
-        if (tid == 0) {
-            s_item = (int)atomicAdd(a.queue, 1u);
-            s_nredo = 0;
-        }
-        __syncthreads();
-        const int item = s_item;
-        if (item >= a.items) break;
-        const int n = item / nb2, rem = item - n * nb2;
+        long long item = 0;
+        if (lane == 0) item = (long long)atomicAdd(a.queue, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= total) break;
+        const int bin = (int)(item / SUB), sub = (int)(item - (long long)bin * SUB);
+        const int n = bin / nb2, rem = bin - n * nb2;
         const int by = rem / a.nb, bx = rem - by * a.nb;
-        const int r = by * BS + ty, c = bx * BS + tx;
+        const int r = by * BS + (sub / (BS / 8)) * 4 + (lane >> 3);
+        const int c = bx * BS + (sub % (BS / 8)) * 8 + (lane & 7);
         fl.znear = __ldg(a.cams + 16 * n + 13);
         const bool valid = (r < a.S) && (c < a.S);
         const PixC p = pixel_centre(r, c, a.S);
@@ -193,140 +196,118 @@ __global__ void __launch_bounds__(BS *BS, BS == 16 ? 3 : 8) k_fine_stream(FineAr
             const unsigned cmax = __reduce_max_sync(0xffffffffu, valid ? (unsigned)c : 0u);
             const unsigned rmin = __reduce_min_sync(0xffffffffu, valid ? (unsigned)r : 0xffffffffu);
             const unsigned rmax = __reduce_max_sync(0xffffffffu, valid ? (unsigned)r : 0u);
-            if (cmin <= cmax) {
-                wx1 = pc_hi((int)cmin, a.S);
-                wx0 = pc_hi((int)cmax, a.S);
-                wy1 = pc_hi((int)rmin, a.S);
-                wy0 = pc_hi((int)rmax, a.S);
-            }
+            if (cmin > cmax) continue;  // no pixel of this block lies in the image (warp-uniform)
+            wx1 = pc_hi((int)cmin, a.S);
+            wx0 = pc_hi((int)cmax, a.S);
+            wy1 = pc_hi((int)rmin, a.S);
+            wy0 = pc_hi((int)rmax, a.S);
         }
-        const int cnt = a.eff[item];  // <= max_faces_per_bin <= sort_cap (checked on the host)
-        const int off = a.offsets[item];
-        sort_entries<BD>(s_sort, a.lists + off, cnt);
+        const int cnt = a.eff[bin];
+        // the bin's list, sorted front to back by k_sort_bins
+        const unsigned long long *ent = a.lists + a.offsets[bin];
         const int64_t s0 = (((int64_t)n * a.S + r) * a.S + c) * K;
         int head = 0, nr = 0, nfin = 0;           // ring head, unsettled entries, settled slots
         float kth_z = kInf;                       // K-th entry while the list is full
         int kth_f = 0x7fffffff;
         bool redo = false;
         auto settle = [&](float z, int f) { a.out.pix_to_face[s0 + nfin] = pack_key(z, f); ++nfin; };
-        for (int base = 0; base < cnt; base += BD) {
-            const int mc = min(BD, cnt - base);
-            if (tid < mc) {
-                const unsigned long long v = s_sort[base + tid];
-                const int fid = (int)(unsigned)(v & 0xffffffffull);
-                s_id[tid] = fid;
-                s_key[tid] = __uint_as_float((unsigned)(v >> 32));
-                const float4 *src = reinterpret_cast<const float4 *>(a.rec + fid);
+        for (int jb = 0; jb < cnt; jb += 32) {
+            // a lane that is done (or invalid, or left for the redo) needs no more faces
+            const bool live = valid && !redo && nfin < K;
+            const float thr = !live ? 0.f : (nfin + nr >= K ? kth_z : kInf);
+            const float wthr = __int_as_float(__reduce_max_sync(0xffffffffu, __float_as_int(thr)));
+            const int jl = jb + lane;
+            int fid = 0;
+            float key = kInf;
+            float4 bb = make_float4(1.f, -1.f, 1.f, -1.f);
+            if (jl < cnt) {
+                const unsigned long long v = __ldg(ent + jl);
+                fid = (int)(unsigned)(v & 0xffffffffull);
+                key = __uint_as_float((unsigned)(v >> 32));
+                bb = __ldg(reinterpret_cast<const float4 *>(a.rec + fid) + kRecC);
+            }
+            // keys ascend along the list: once the first is behind every lane, the rest is too
+            if (__shfl_sync(0xffffffffu, key, 0) > wthr) break;
+            const bool hit = bb.x <= wx1 && bb.y >= wx0 && bb.z <= wy1 && bb.w >= wy0 && !(key > wthr);
+            unsigned mask = __ballot_sync(0xffffffffu, hit);
+            while (mask) {
+                const int src = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int f = __shfl_sync(0xffffffffu, fid, src);
+                const float fkey = __shfl_sync(0xffffffffu, key, src);
                 FaceRec R;
-                R.a = __ldg(src + kRecA);
-                R.b = __ldg(src + kRecB);
-                R.c = __ldg(src + kRecC);
-                R.d = __ldg(src + kRecD);
-                R.e = __ldg(src + kRecE);
-                R.h = __ldg(src + kRecH);
-                s_rec[tid] = R;
-            }
-            __syncthreads();
-            bool warp_done = false;
-            for (int jb = 0; jb < mc; jb += 32) {
-                // a lane that is done (or invalid, or left for the redo) needs no more faces
-                const bool live = valid && !redo && nfin < K;
-                const float thr = !live ? 0.f : (nfin + nr >= K ? kth_z : kInf);
-                const float wthr = __int_as_float(__reduce_max_sync(0xffffffffu, __float_as_int(thr)));
-                if (s_key[jb] > wthr) {
-                    warp_done = true;
-                    break;
+                R.c.x = __shfl_sync(0xffffffffu, bb.x, src);
+                R.c.y = __shfl_sync(0xffffffffu, bb.y, src);
+                R.c.z = __shfl_sync(0xffffffffu, bb.z, src);
+                R.c.w = __shfl_sync(0xffffffffu, bb.w, src);
+                if (!valid || redo || nfin >= K) continue;
+                if (!in_bbox(R, p)) continue;
+                const bool full = nfin + nr >= K;
+                if (full && fkey > kth_z) continue;  // its depth is at least its key
+                const float4 *rs = reinterpret_cast<const float4 *>(a.rec + f);
+                R.a = __ldg(rs + kRecA);
+                R.b = __ldg(rs + kRecB);
+                R.d = __ldg(rs + kRecD);
+                R.e = __ldg(rs + kRecE);
+                R.h = __ldg(rs + kRecH);
+                float z;
+                if (!face_key_nobbox(R, p, fl, z)) continue;
+                if (full && !key_less(z, f, kth_z, kth_f)) continue;
+                // entries in front of this face's key are settled: no later face precedes them
+                while (nr > 0) {
+                    const int h = head & (kRing - 1);
+                    const float fz = rz[h][lane];
+                    if (!(fz < fkey)) break;
+                    settle(fz, rf[h][lane]);
+                    ++head;
+                    --nr;
                 }
-                const int jl = jb + lane;
-                bool hit = false;
-                if (jl < mc) {
-                    const float4 bb = s_rec[jl].c;
-                    hit = bb.x <= wx1 && bb.y >= wx0 && bb.z <= wy1 && bb.w >= wy0 && !(s_key[jl] > wthr);
+                if (full) --nr;             // the K-th entry is displaced (nr >= 1: not done)
+                if (nr == kRing) {          // no room: this pixel is redone by the warp
+                    redo = true;
+                    continue;
                 }
-                unsigned mask = __ballot_sync(0xffffffffu, hit);
-                while (mask) {
-                    const int jj = jb + __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    if (!valid || redo || nfin >= K) continue;
-                    FaceRec R;
-                    R.c = s_rec[jj].c;
-                    if (!in_bbox(R, p)) continue;
-                    const float key = s_key[jj];
-                    const bool full = nfin + nr >= K;
-                    if (full && key > kth_z) continue;  // its depth is at least its key
-                    R.a = s_rec[jj].a;
-                    R.b = s_rec[jj].b;
-                    R.d = s_rec[jj].d;
-                    R.e = s_rec[jj].e;
-                    R.h = s_rec[jj].h;
-                    float z;
-                    if (!face_key_nobbox(R, p, fl, z)) continue;
-                    const int fid = s_id[jj];
-                    if (full && !key_less(z, fid, kth_z, kth_f)) continue;
-                    // entries in front of this face's key are settled: no later face precedes them
-                    while (nr > 0) {
-                        const int h = head & (kRing - 1);
-                        const float fz = rz[h * BD];
-                        if (!(fz < key)) break;
-                        settle(fz, rf[h * BD]);
-                        ++head;
-                        --nr;
-                    }
-                    if (full) --nr;             // the K-th entry is displaced (nr >= 1: not done)
-                    if (nr == kRing) {          // no room: this pixel is redone by a warp
-                        redo = true;
-                        continue;
-                    }
-                    int pos = nr;               // insertion from the tail (arrivals are nearly sorted)
-                    while (pos > 0) {
-                        const int hp = (head + pos - 1) & (kRing - 1);
-                        const float pz = rz[hp * BD];
-                        const int pf = rf[hp * BD];
-                        if (!key_less(z, fid, pz, pf)) break;
-                        const int hq = (head + pos) & (kRing - 1);
-                        rz[hq * BD] = pz;
-                        rf[hq * BD] = pf;
-                        --pos;
-                    }
+                int pos = nr;               // insertion from the tail (arrivals are nearly sorted)
+                while (pos > 0) {
+                    const int hp = (head + pos - 1) & (kRing - 1);
+                    const float pz = rz[hp][lane];
+                    const int pf = rf[hp][lane];
+                    if (!key_less(z, f, pz, pf)) break;
                     const int hq = (head + pos) & (kRing - 1);
-                    rz[hq * BD] = z;
-                    rf[hq * BD] = fid;
-                    ++nr;
-                    if (nfin + nr >= K) {
-                        const int hl = (head + nr - 1) & (kRing - 1);
-                        kth_z = rz[hl * BD];
-                        kth_f = rf[hl * BD];
-                    }
+                    rz[hq][lane] = pz;
+                    rf[hq][lane] = pf;
+                    --pos;
+                }
+                const int hq = (head + pos) & (kRing - 1);
+                rz[hq][lane] = z;
+                rf[hq][lane] = f;
+                ++nr;
+                if (nfin + nr >= K) {
+                    const int hl = (head + nr - 1) & (kRing - 1);
+                    kth_z = rz[hl][lane];
+                    kth_f = rf[hl][lane];
                 }
             }
-            if (!warp_done && base + BD < cnt) {
-                const bool live = valid && !redo && nfin < K;
-                const float thr = !live ? 0.f : (nfin + nr >= K ? kth_z : kInf);
-                const float wthr = __int_as_float(__reduce_max_sync(0xffffffffu, __float_as_int(thr)));
-                warp_done = __uint_as_float((unsigned)(s_sort[base + BD] >> 32)) > wthr;
-            }
-            if (__syncthreads_and(warp_done)) break;
         }
         // everything left in the ring is settled; empty slots get -1
         if (valid && !redo) {
             while (nr > 0) {
                 const int h = head & (kRing - 1);
-                settle(rz[h * BD], rf[h * BD]);
+                settle(rz[h][lane], rf[h][lane]);
                 ++head;
                 --nr;
             }
             for (int k = nfin; k < K; ++k) a.out.pix_to_face[s0 + k] = -1ll;
         }
-        if (valid && redo) s_redo[atomicAdd(&s_nredo, 1)] = tid;
-        __syncthreads();
-        const int nredo = s_nredo;
-        for (int i = warp; i < nredo; i += BD / 32) {
-            int rty, rtx;
-            tile_pixel_of<BS>(s_redo[i], rty, rtx);
-            redo_pixel(a, s_sort, cnt, n, by * BS + rty, bx * BS + rtx, fl);
+        // pixels whose unsettled candidates outgrew the ring: the whole warp redoes each
+        unsigned todo = __ballot_sync(0xffffffffu, valid && redo);
+        if (todo && lane == 0) atomicAdd(a.redo_count, (unsigned)__popc(todo));
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int rr = __shfl_sync(0xffffffffu, r, src), cc = __shfl_sync(0xffffffffu, c, src);
+            redo_pixel(a, ent, cnt, n, rr, cc, fl);
         }
-        if (nredo > 0 && lane == 0 && warp == 0) atomicAdd(a.redo_count, (unsigned)nredo);
-        __syncthreads();  // s_sort, s_item and s_nredo are reused by the next item
     }
 }
 
@@ -334,16 +315,29 @@ __global__ void __launch_bounds__(BS *BS, BS == 16 ? 3 : 8) k_fine_stream(FineAr
 // Fragment attributes: a block takes PB = 256 / K whole pixels, one thread per
 // slot in output order (consecutive threads, consecutive slots: coalesced)
 // ---------------------------------------------------------------------------
+// q = n / d for n < 2^26 and 1 <= d <= 8192 from a 32-bit reciprocal, corrected to exact
+__device__ __forceinline__ unsigned div_small(unsigned n, unsigned d, unsigned magic) {
+    unsigned q = __umulhi(n, magic);
+    if ((q + 1) * d <= n) ++q;
+    if (q * d > n) --q;
+    return q;
+}
+
 template <bool BL>
 __global__ void __launch_bounds__(256) k_frag_attr(FragAttrArgs a) {
     __shared__ float s_keep[256];
     const int K = a.K, S = a.S;
     const int PB = 256 / K;
     const int t = threadIdx.x;
-    const int64_t pix0 = (int64_t)blockIdx.x * PB;
-    const int lp = t / K, k = t - lp * K;
+    // grid: x = chunk of PB pixels of one image, y = image
+    const unsigned SS = (unsigned)S * (unsigned)S;
+    const unsigned q0 = blockIdx.x * (unsigned)PB;            // first pixel of the chunk in its image
+    const int lp = (int)__fdividef((float)t + 0.5f, (float)K); // t / K (t < 256: exact)
+    const int k = t - lp * K;
+    const unsigned qi = q0 + (unsigned)lp;
+    const int64_t pix0 = (int64_t)blockIdx.y * SS + q0;
     const int64_t pix = pix0 + lp;
-    const bool active = lp < PB && pix < a.P;
+    const bool active = lp < PB && qi < SS;
     float keep = 1.f;
     if (active) {
         const int64_t s = pix * K + k;
@@ -370,9 +364,7 @@ __global__ void __launch_bounds__(256) k_frag_attr(FragAttrArgs a) {
             R.b = __ldg(src + kRecB);
             R.d = __ldg(src + kRecD);
             R.e = __ldg(src + kRecE);
-            const int64_t n = pix / ((int64_t)S * S);
-            const int rem = (int)(pix - n * S * S);
-            const int r = rem / S, c = rem - r * S;
+            const int r = (int)div_small(qi, (unsigned)S, a.magic_S), c = (int)qi - r * S;
             float bp[3], d;
             face_fragment(R, pixel_centre(r, c, S), a.fl, bp, d);
             a.out.pix_to_face[s] = f;
@@ -391,13 +383,13 @@ __global__ void __launch_bounds__(256) k_frag_attr(FragAttrArgs a) {
         __syncthreads();
         const int lane = t & 31;
         for (int q = t >> 5; q < PB; q += 8) {
-            const int64_t qp = pix0 + q;
             float m = 1.f;
             if (lane < K) m = s_keep[q * K + lane];
             if (lane + 32 < K) m *= s_keep[q * K + lane + 32];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) m *= __shfl_xor_sync(0xffffffffu, m, o);
-            if (lane == 0 && qp < a.P) reinterpret_cast<float4 *>(a.image)[qp] = make_float4(0.f, 0.f, 0.f, 1.f - m);
+            if (lane == 0 && q0 + (unsigned)q < SS)
+                reinterpret_cast<float4 *>(a.image)[pix0 + q] = make_float4(0.f, 0.f, 0.f, 1.f - m);
         }
     }
 }
@@ -405,24 +397,34 @@ __global__ void __launch_bounds__(256) k_frag_attr(FragAttrArgs a) {
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-size_t fine_stream_smem(int sort_cap, int bin) { return (size_t)sort_cap * 8 + (size_t)kRing * bin * bin * 8; }
+static cudaError_t launch_sort_bins(const FineArgs &a, cudaStream_t st) {
+    const size_t dyn = (size_t)a.sort_cap * 8;
+    cudaError_t e = cudaFuncSetAttribute(k_sort_bins, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    int bps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_sort_bins, 256, dyn);
+    if (e != cudaSuccess) return e;
+    const int grid = std::max(1, std::min<int>(a.items, mr_host::num_sms() * std::max(1, bps)));
+    k_sort_bins<<<grid, 256, dyn, st>>>(a);
+    return cudaGetLastError();
+}
 
 template <int BS>
 static cudaError_t launch_fine_stream_t(const FineArgs &a, cudaStream_t st) {
-    constexpr int BD = BS * BS;
-    const size_t dyn = fine_stream_smem(a.sort_cap, BS);
     auto kern = k_fine_stream<BS>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (e != cudaSuccess) return e;
     int bps = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, BD, dyn);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, 256, 0);
     if (e != cudaSuccess) return e;
-    const int grid = std::max(1, std::min<int>(a.items, mr_host::num_sms() * std::max(1, bps)));
-    kern<<<grid, BD, dyn, st>>>(a);
+    const long long warps = (long long)a.items * (BS * BS / 32);
+    const long long need = (warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int grid = (int)std::max(1LL, std::min<long long>(need, (long long)mr_host::num_sms() * std::max(1, bps)));
+    kern<<<grid, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_fine_stream(const FineArgs &a, int bin, cudaStream_t st) {
+    cudaError_t e = launch_sort_bins(a, st);
+    if (e != cudaSuccess) return e;
     if (bin == 8) return launch_fine_stream_t<8>(a, st);
     if (bin == 16) return launch_fine_stream_t<16>(a, st);
     return cudaErrorInvalidValue;
@@ -431,10 +433,15 @@ cudaError_t launch_fine_stream(const FineArgs &a, int bin, cudaStream_t st) {
 cudaError_t launch_frag_attr(const FragAttrArgs &a, cudaStream_t st) {
     if (a.P <= 0) return cudaSuccess;
     if (a.K < 1 || a.K > 64) return cudaErrorInvalidValue;
+    if (a.S < 1 || a.S > 8192 || a.P % ((int64_t)a.S * a.S) != 0) return cudaErrorInvalidValue;
     const int PB = 256 / a.K;
-    const int64_t blocks = (a.P + PB - 1) / PB;
-    if (a.image) k_frag_attr<true><<<(unsigned)blocks, 256, 0, st>>>(a);
-    else k_frag_attr<false><<<(unsigned)blocks, 256, 0, st>>>(a);
+    const int64_t N = a.P / ((int64_t)a.S * a.S);
+    if (N > 65535) return cudaErrorInvalidValue;
+    FragAttrArgs b = a;
+    b.magic_S = (unsigned)((0x100000000ull + (unsigned)a.S - 1) / (unsigned)a.S);
+    const dim3 grid((unsigned)(((int64_t)a.S * a.S + PB - 1) / PB), (unsigned)N);
+    if (a.image) k_frag_attr<true><<<grid, 256, 0, st>>>(b);
+    else k_frag_attr<false><<<grid, 256, 0, st>>>(b);
     return cudaGetLastError();
 }
 

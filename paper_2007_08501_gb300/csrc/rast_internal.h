@@ -93,6 +93,7 @@ struct FragAttrArgs {
     EvalFlags fl;
     float sigma;
     float *image;     // non-NULL: silhouette blend (Algorithm 1) into (P, 4)
+    unsigned magic_S; // ceil(2^32 / S), set by the launcher
 };
 
 struct NaiveArgs {
@@ -144,7 +145,6 @@ cudaError_t launch_fine(const FineArgs &a, int bin, cudaStream_t st);
 bool fine_blends(int K, bool rgb);  // whether launch_fine applies FineArgs::blend
 cudaError_t launch_naive(const NaiveArgs &a, int N, cudaStream_t st);
 // large K: front-to-back streaming fine pass + attribute pass (fine_stream.cu)
-size_t fine_stream_smem(int sort_cap, int bin);
 cudaError_t launch_fine_stream(const FineArgs &a, int bin, cudaStream_t st);
 cudaError_t launch_frag_attr(const FragAttrArgs &a, cudaStream_t st);
 cudaError_t launch_rast_bwd(const RastBwdArgs &a, int N, cudaStream_t st);
