@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256) k_sort_bins(FineArgs a) {
 constexpr int kWarpsPerBlock = 8;
 
 template <int BS>
-__global__ void __launch_bounds__(256, 3) k_fine_stream(FineArgs a) {
+__global__ void __launch_bounds__(256, 4) k_fine_stream(FineArgs a) {
     constexpr int SUB = BS * BS / 32;  // 8 x 4 pixel blocks per bin
     // per warp: the rings ([slot][lane])
     __shared__ float s_rz[kWarpsPerBlock][kRing][32];
@@ -373,7 +373,7 @@ __global__ void __launch_bounds__(256) k_frag_attr(FragAttrArgs a) {
             a.out.bary[3 * s + 1] = bp[1];
             a.out.bary[3 * s + 2] = bp[2];
             a.out.dists[s] = d;
-            if constexpr (BL) keep = sigmoidf_(d / a.sigma);
+            if constexpr (BL) keep = __frcp_rn(1.f + expf(-d * a.inv_sigma));  // 1 - prob = sigmoid(d / sigma)
         }
     }
     if constexpr (BL) {
@@ -438,6 +438,7 @@ cudaError_t launch_frag_attr(const FragAttrArgs &a, cudaStream_t st) {
     const int64_t N = a.P / ((int64_t)a.S * a.S);
     if (N > 65535) return cudaErrorInvalidValue;
     FragAttrArgs b = a;
+    b.inv_sigma = 1.f / a.sigma;
     b.magic_S = (unsigned)((0x100000000ull + (unsigned)a.S - 1) / (unsigned)a.S);
     const dim3 grid((unsigned)(((int64_t)a.S * a.S + PB - 1) / PB), (unsigned)N);
     if (a.image) k_frag_attr<true><<<grid, 256, 0, st>>>(b);

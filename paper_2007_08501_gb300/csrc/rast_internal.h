@@ -94,6 +94,7 @@ struct FragAttrArgs {
     float sigma;
     float *image;     // non-NULL: silhouette blend (Algorithm 1) into (P, 4)
     unsigned magic_S; // ceil(2^32 / S), set by the launcher
+    float inv_sigma;  // 1 / sigma, set by the launcher
 };
 
 struct NaiveArgs {

@@ -188,6 +188,8 @@ def test_render_meshes_autograd_equals_separate_functions(rgb):
     (ops.BLEND_RGB, 5, 16, True),     # fine pass blends (scalar write path, K < 8)
     (ops.BLEND_RGB, 16, 16, False),
     (ops.BLEND_RGB, 20, 8, True),     # K > 16: separate blend kernel inside the call
+    (ops.BLEND_SIL, 20, 16, True),    # K > 16: the attribute pass blends the silhouette
+    (ops.BLEND_SIL, 50, 8, True),
     (ops.BLEND_SIL, 4, 0, True),      # plain form: separate blend kernel
 ])
 def test_fused_forward_equals_rasterize_then_blend(mode, K, bin_size, clip):
