@@ -108,7 +108,7 @@ __device__ __forceinline__ void scatter_face_dist(const RastBwdArgs &r, int key,
 template <bool RGB, int NA>
 __device__ __forceinline__ void slot_tail(const BlendArgs &a, const RastBwdArgs &r, const PixC &p, int f, float gz,
                                           float gd, float gb0, float gb1, float gb2, const int64_t vi[3],
-                                          float (&acc)[NA]) {
+                                          float (&acc)[NA], RareQueue rq = RareQueue{nullptr, nullptr}) {
     const int fr = (f >= 0 && (int64_t)f < r.F) ? f : -1;  // an id outside the batch contributes nothing
     const int nf = fr >= 0 ? __ldg(r.face_mesh + fr) : -1;
     const bool live = nf >= 0 && (gz != 0.f || gd != 0.f || gb0 != 0.f || gb1 != 0.f || gb2 != 0.f);
@@ -131,7 +131,7 @@ __device__ __forceinline__ void slot_tail(const BlendArgs &a, const RastBwdArgs 
         for (int j = 0; j < 9; ++j) g9[j] = 0.f;
         if (live) {
             load_adjoint_rec(r.rec, fr, R);
-            slot_corner_grads(R, p, r.fl, gz, gd, gb0, gb1, gb2, g9);
+            slot_corner_grads(R, p, r.fl, gz, gd, gb0, gb1, gb2, g9, rq, fr, nf);
         }
 #pragma unroll
         for (int j = 0; j < 9; ++j) acc[j] = g9[j];
@@ -164,6 +164,13 @@ __global__ void __launch_bounds__(256, fused_min_blocks(KM, RGB)) k_blend_rast_b
     const bool valid = row < a.S && col < a.S;
     const int64_t pix = ((int64_t)blockIdx.z * a.S + row) * a.S + col;
     const PixC p = pixel_centre(row, col, a.S);
+    // softmax blend: slots whose barycentric adjoint needs double-float are
+    // queued and done at the end of the block
+    __shared__ RareSlot s_rare[RGB ? kRareCap : 1];
+    __shared__ int s_nrare;
+    if (RGB && threadIdx.x == 0) s_nrare = 0;
+    if (RGB) __syncthreads();
+    const RareQueue rq{RGB ? s_rare : nullptr, &s_nrare};
     SlotData<KM> S;
     float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
     if (valid) {
@@ -279,8 +286,9 @@ __global__ void __launch_bounds__(256, fused_min_blocks(KM, RGB)) k_blend_rast_b
                 }
             }
         }
-        slot_tail<RGB, NA>(a, r, p, f, gz, gd, gb[0], gb[1], gb[2], vi, acc);
+        slot_tail<RGB, NA>(a, r, p, f, gz, gd, gb[0], gb[1], gb[2], vi, acc, rq);
     }
+    if constexpr (RGB) flush_rare_slots(rq, r.rec, r.cams, r.faces, r.grad_verts, a.S, r.fl);
 }
 
 // ---------------------------------------------------------------------------
@@ -296,6 +304,11 @@ __global__ void __launch_bounds__(256) k_blend_rast_bwd_any(BlendArgs a, RastBwd
     const PixC p = pixel_centre(row, col, a.S);
     const int K = a.K;
     const int64_t s0 = pix * K;
+    __shared__ RareSlot s_rare[RGB ? kRareCap : 1];
+    __shared__ int s_nrare;
+    if (RGB && threadIdx.x == 0) s_nrare = 0;
+    if (RGB) __syncthreads();
+    const RareQueue rq{RGB ? s_rare : nullptr, &s_nrare};
     const float4 g = valid ? reinterpret_cast<const float4 *>(a.grad_image)[pix] : make_float4(0.f, 0.f, 0.f, 0.f);
     float keep = 1.f, zmin = __int_as_float(0x7f800000);
     bool any = false;
@@ -393,15 +406,18 @@ __global__ void __launch_bounds__(256) k_blend_rast_bwd_any(BlendArgs a, RastBwd
                 }
             }
         }
-        slot_tail<RGB, NA>(a, r, p, f, gz, gd, gb[0], gb[1], gb[2], vi, acc);
+        slot_tail<RGB, NA>(a, r, p, f, gz, gd, gb[0], gb[1], gb[2], vi, acc, rq);
     }
+    if constexpr (RGB) flush_rare_slots(rq, r.rec, r.cams, r.faces, r.grad_verts, a.S, r.fl);
 }
 
 // ---------------------------------------------------------------------------
 template <int KM, bool RGB>
 static void launch_fused_t(const BlendArgs &a, const RastBwdArgs &r, dim3 grid, cudaStream_t st) {
     constexpr size_t smem = fused_smem(KM, RGB);
-    if constexpr (smem > 48 * 1024) {
+    // dynamic plus static shared memory may exceed the 48 KB a launch gets
+    // without the opt-in
+    if constexpr (smem > 32 * 1024) {
         static bool set = false;  // one attribute call per process and instantiation
         if (!set) {
             cudaFuncSetAttribute(k_blend_rast_bwd<KM, RGB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -82,11 +82,30 @@ __device__ __forceinline__ void slot_corner_grads_dist(const FaceRec &R, const P
     }
 }
 
-template <typename T>
-__device__ __forceinline__ T rcp_t(T x) {
-    if constexpr (sizeof(T) == 4) return __fdividef(1.f, x);
-    else return 1.0 / x;
+// A double-float number (~44-bit significand) for the few slots whose
+// barycentric adjoint is ill-conditioned in fp32: GB300's FP64 rate is a
+// small fraction of its FP32 rate, fp32 pairs are several times cheaper.
+struct dfv {
+    df v;
+    dfv() = default;
+    __device__ __forceinline__ dfv(df x) : v(x) {}
+    __device__ __forceinline__ dfv(float x) : v{x, 0.f} {}
+    __device__ __forceinline__ dfv(int x) : v{(float)x, 0.f} {}
+    __device__ __forceinline__ float f() const { return __fadd_rn(v.hi, v.lo); }
+};
+__device__ __forceinline__ dfv operator+(dfv a, dfv b) { return dfv(df_add(a.v, b.v)); }
+__device__ __forceinline__ dfv operator-(dfv a, dfv b) { return dfv(df_sub(a.v, b.v)); }
+__device__ __forceinline__ dfv operator-(dfv a) { return dfv(df_neg(a.v)); }
+__device__ __forceinline__ dfv operator*(dfv a, dfv b) { return dfv(df_mul(a.v, b.v)); }
+__device__ __forceinline__ dfv &operator+=(dfv &a, dfv b) { return a = a + b; }
+__device__ __forceinline__ dfv &operator-=(dfv &a, dfv b) { return a = a - b; }
+__device__ __forceinline__ bool operator>(dfv a, dfv b) {
+    const df d = df_sub(a.v, b.v);
+    return d.hi > 0.f || (d.hi == 0.f && d.lo > 0.f);
 }
+
+__device__ __forceinline__ float rcp_t(float x) { return __fdividef(1.f, x); }
+__device__ __forceinline__ dfv rcp_t(dfv x) { return dfv(df_div({1.f, 0.f}, x.v)); }
 
 // Barycentric part of one slot's adjoint: dL/d(bary', zbuf) -> dL/d(x, y, z) of
 // the three corners (corner-0-relative: P0 = 0, P1 = u, P2 = w), in the
@@ -125,30 +144,34 @@ __device__ __forceinline__ void bary_adjoint(const T (&b)[3], const T (&iz)[3], 
     // z_i - z_j = (1/z_j - 1/z_i) z_i z_j
     auto zdiff = [&](int i, int j) { return (iz[j] - iz[i]) * zc[i] * zc[j]; };
     if (clip && !inside) {
-        // clipped barycentrics, z = sum_i b'_i z_i
-        T gbt[3], gb[3];
+        // clipped barycentrics: b'_i = t_i / U over the unclipped set (b~_i > 0),
+        // U = sum of t_j there, t_i = b_i / z_i (b_i when affine): T cancels in
+        // the renormalisation, so the adjoint is taken through t directly;
+        // z = sum_i b'_i z_i
+        T t[3], Ut = T(0);
+        for (int i = 0; i < 3; ++i) {
+            t[i] = persp ? b[i] * iz[i] : b[i];
+            if (bt[i] > T(0)) Ut += t[i];   // the t of the unclipped set share T's sign
+        }
+        const T iU = rcp_t(Ut);
+        T gb[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             gZ[i] = gz * bp[i];
-            T acc = T(0);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) acc += bp[j] * ((gbp[i] - gbp[j]) + gz * zdiff(i, j));
-            gbt[i] = (bt[i] > T(0)) ? acc * ics : T(0);
-        }
-        if (persp) {
-            // b~_i = t_i / T, t_i = b_i / z_i
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
+            T gt = T(0);
+            if (bt[i] > T(0)) {
                 T acc = T(0);
 #pragma unroll
-                for (int j = 0; j < 3; ++j) acc += bt[j] * (gbt[i] - gbt[j]);
-                const T gt = acc * iT;
+                for (int j = 0; j < 3; ++j)
+                    if (bt[j] > T(0)) acc += bp[j] * ((gbp[i] - gbp[j]) + gz * zdiff(i, j));
+                gt = acc * iU;
+            }
+            if (persp) {
                 gb[i] = gt * iz[i];
                 gZ[i] -= gt * b[i] * iz[i] * iz[i];
+            } else {
+                gb[i] = gt;
             }
-        } else {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) gb[i] = gbt[i];
         }
         d1 = gb[1] - gb[0];
         d2 = gb[2] - gb[0];
@@ -183,37 +206,113 @@ __device__ __forceinline__ void bary_adjoint(const T (&b)[3], const T (&iz)[3], 
     }
 }
 
-// The same in FP64 for the slots whose barycentric gradient is ill-conditioned
-// in fp32 (slivers, far-extrapolated barycentrics: ~1 % of the slots of a
-// sphere seen edge-on near its silhouette).  Every input is taken at full
-// accuracy: the corners and the pixel as double-float sums, the barycentrics
-// from edge functions of those.
-static __device__ __noinline__ void bary_adjoint_f64(const FaceRec &R, const PixC &p, int persp, int clip, bool inside,
-                                              float gbp0, float gbp1, float gbp2, float gz, float (&gx)[3],
-                                              float (&gy)[3], float (&gZ)[3]) {
-    const double qx = ((double)p.xh - (double)R.a.x) + ((double)p.xl - (double)R.a.z);
-    const double qy = ((double)p.yh - (double)R.a.y) + ((double)p.yl - (double)R.a.w);
-    const double ux = (double)R.b.x + (double)R.e.x, uy = (double)R.b.y + (double)R.e.y;
-    const double wx = (double)R.b.z + (double)R.e.z, wy = (double)R.b.w + (double)R.e.w;
-    const double A = ux * wy - uy * wx, invA = 1.0 / A;
-    const double e2 = ux * qy - uy * qx, e1 = qx * wy - qy * wx;
-    const double e0 = (wx - ux) * (qy - uy) - (wy - uy) * (qx - ux);
-    const double b[3] = {e0 * invA, e1 * invA, e2 * invA};
-    const double iz[3] = {(double)R.d.y, (double)R.d.z, (double)R.d.w};
-    const double gbp[3] = {(double)gbp0, (double)gbp1, (double)gbp2};
-    double dx[3], dy[3], dZ[3];
-    bary_adjoint<double>(b, iz, ux, uy, wx, wy, invA, persp, clip, inside, gbp, (double)gz, dx, dy, dZ);
+// The same in double-float for the slots whose barycentric gradient is
+// ill-conditioned in fp32 (slivers seen far outside: ~1 % of the slots of a
+// sphere near its silhouette).  Every input is taken at full accuracy: the
+// corners and the pixel as double-float sums, the barycentrics from
+// double-float edge functions of those.
+static __device__ __noinline__ void bary_adjoint_df(const FaceRec &R, const PixC &p, int persp, int clip, bool inside,
+                                                    float gbp0, float gbp1, float gbp2, float gz, float (&gx)[3],
+                                                    float (&gy)[3], float (&gZ)[3]) {
+    const df qx = df_add(two_sum(p.xh, -R.a.x), two_sum(p.xl, -R.a.z));
+    const df qy = df_add(two_sum(p.yh, -R.a.y), two_sum(p.yl, -R.a.w));
+    const df ux = {R.b.x, R.e.x}, uy = {R.b.y, R.e.y}, wx = {R.b.z, R.e.z}, wy = {R.b.w, R.e.w};
+    const df A = df_cross(ux, uy, wx, wy);
+    const df invA = df_div({1.f, 0.f}, A);
+    const df e2 = df_cross(ux, uy, qx, qy);
+    const df e1 = df_cross(qx, qy, wx, wy);
+    const df e0 = df_cross(df_sub(wx, ux), df_sub(wy, uy), df_sub(qx, ux), df_sub(qy, uy));
+    const dfv b[3] = {dfv(df_mul(e0, invA)), dfv(df_mul(e1, invA)), dfv(df_mul(e2, invA))};
+    const dfv iz[3] = {dfv(R.d.y), dfv(R.d.z), dfv(R.d.w)};
+    const dfv gbp[3] = {dfv(gbp0), dfv(gbp1), dfv(gbp2)};
+    dfv dx[3], dy[3], dZ[3];
+    bary_adjoint<dfv>(b, iz, dfv(ux), dfv(uy), dfv(wx), dfv(wy), dfv(invA), persp, clip, inside, gbp, dfv(gz), dx,
+                      dy, dZ);
     for (int i = 0; i < 3; ++i) {
-        gx[i] = (float)dx[i];
-        gy[i] = (float)dy[i];
-        gZ[i] = (float)dZ[i];
+        gx[i] = dx[i].f();
+        gy[i] = dy[i].f();
+        gZ[i] = dZ[i].f();
+    }
+}
+
+// Slots whose barycentric adjoint needs double-float are put aside in a
+// per-block queue in shared memory and done at the end of the block, one
+// thread per slot: done in line, one such lane would hold up the other 31 of
+// its warp for the whole double-float evaluation.
+constexpr int kRareCap = 256;   // ~1 % of a 16 x 16 tile's slots need it at K = 8
+struct RareSlot {
+    int f, nf, tid;        // face, its image, the thread (pixel of the block's tile) of the slot
+    float gz, gb0, gb1, gb2;
+};
+struct RareQueue {
+    RareSlot *e;
+    int *n;
+};
+
+// NDC corner gradients g[9] of face R (corner-0-relative record) through the
+// projection Jacobian and R^T of camera cam to world space: atomics into
+// grad_verts at the face's three vertices.
+__device__ __forceinline__ void scatter_corner_grads(const FaceRec &R, const float *cam, const int64_t *faces,
+                                                     int64_t f, const float (&g)[9], float *grad_verts) {
+    const float fo = cam[12];
+    const float v0x = R.a.x + R.a.z, v0y = R.a.y + R.a.w;
+    const float Px[3] = {0.f, R.b.x, R.b.z}, Py[3] = {0.f, R.b.y, R.b.w};
+    const float iz[3] = {R.d.y, R.d.z, R.d.w};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        // x = f x_v / z_v, y = f y_v / z_v: d/dx_v = f/z, d/dz_v = -(x dL/dx + y dL/dy)/z
+        const float xn = v0x + Px[i], yn = v0y + Py[i];
+        const float gxv = g[3 * i] * fo * iz[i];
+        const float gyv = g[3 * i + 1] * fo * iz[i];
+        const float gzv = g[3 * i + 2] - (g[3 * i] * xn + g[3 * i + 1] * yn) * iz[i];
+        const int64_t vi = __ldg(faces + 3 * f + i);
+        float *gv = grad_verts + 3 * vi;
+        atomicAdd(gv + 0, cam[0] * gxv + cam[3] * gyv + cam[6] * gzv);
+        atomicAdd(gv + 1, cam[1] * gxv + cam[4] * gyv + cam[7] * gzv);
+        atomicAdd(gv + 2, cam[2] * gxv + cam[5] * gyv + cam[8] * gzv);
+    }
+}
+
+// The queued slots of a block whose threads own the pixels of a 16 x 16 tile
+// (thread t: row blockIdx.y * 16 + t / 16, column blockIdx.x * 16 + t % 16).
+// Every thread of the block must call it, after its last slot.
+__device__ __forceinline__ void flush_rare_slots(const RareQueue &q, const FaceRec *rec, const float *cams,
+                                                 const int64_t *faces, float *grad_verts, int S, const EvalFlags &fl) {
+    __syncthreads();
+    const int cnt = min(*q.n, kRareCap);
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const RareSlot e = q.e[i];
+        const int r = blockIdx.y * 16 + (e.tid >> 4), c = blockIdx.x * 16 + (e.tid & 15);
+        const PixC p = pixel_centre(r, c, S);
+        FaceRec R;
+        const float4 *src = reinterpret_cast<const float4 *>(rec + e.f);
+        R.a = __ldg(src + kRecA);
+        R.b = __ldg(src + kRecB);
+        R.d = __ldg(src + kRecD);
+        R.e = __ldg(src + kRecE);
+        float qx, qy, b[3];
+        local_q(R, p, qx, qy);
+        screen_bary(R, qx, qy, b[0], b[1], b[2]);
+        const bool inside = (b[0] >= 0.f) && (b[1] >= 0.f) && (b[2] >= 0.f);
+        float gx[3], gy[3], gZ[3], g[9];
+        bary_adjoint_df(R, p, fl.persp, fl.clip, inside, e.gb0, e.gb1, e.gb2, e.gz, gx, gy, gZ);
+        for (int j = 0; j < 3; ++j) {
+            g[3 * j] = gx[j];
+            g[3 * j + 1] = gy[j];
+            g[3 * j + 2] = gZ[j];
+        }
+        scatter_corner_grads(R, cams + 16 * e.nf, faces, e.f, g, grad_verts);
     }
 }
 
 // NDC-space corner gradients of one slot: g[3*i + {0,1,2}] = dL/d(x_i, y_i, z_i)
 // of corner i (NDC x, NDC y, view depth).  Uses the record's a, b, d and e.
+// With a queue (q.e non-NULL), a slot whose barycentric part needs
+// double-float leaves that part to flush_rare_slots (face f of image nf) while
+// there is room; without one it is evaluated in fp32.
 __device__ __forceinline__ void slot_corner_grads(const FaceRec &R, const PixC &p, const EvalFlags &fl, float gz,
-                                                  float gd, float gbp0, float gbp1, float gbp2, float (&g)[9]) {
+                                                  float gd, float gbp0, float gbp1, float gbp2, float (&g)[9],
+                                                  RareQueue q = RareQueue{nullptr, nullptr}, int f = 0, int nf = 0) {
     float qx, qy;
     local_q(R, p, qx, qy);
     float b[3];
@@ -225,13 +324,17 @@ __device__ __forceinline__ void slot_corner_grads(const FaceRec &R, const PixC &
     (void)nearest_edge(R, qx, qy, edge, tseg);
     float gx[3] = {0.f, 0.f, 0.f}, gy[3] = {0.f, 0.f, 0.f}, gZ[3] = {0.f, 0.f, 0.f};
     if (gz != 0.f || gbp0 != 0.f || gbp1 != 0.f || gbp2 != 0.f) {
-        // fp32 unless the face is a sliver (edge^2 / area large) or the pixel
-        // lies far outside it (|b| large): there the barycentric gradient
-        // is a near-cancellation of large terms, and FP64 keeps it to ~1e-7
+        // fp32 unless the face is a sliver (edge^2 / area large) and the pixel
+        // lies far outside it (|b| large): there the barycentric gradient is a
+        // near-cancellation of large terms, and double-float keeps it to
+        // ~1e-7 (about 1 % of the slots of a sphere seen near its silhouette)
         const float sliver = (R.b.x * R.b.x + R.b.y * R.b.y + R.b.z * R.b.z + R.b.w * R.b.w) * fabsf(R.d.x);
         const float bmax = fmaxf(fabsf(b[0]), fmaxf(fabsf(b[1]), fabsf(b[2])));
-        if (sliver > 64.f || bmax > 4.f) {
-            bary_adjoint_f64(R, p, fl.persp, fl.clip, inside, gbp0, gbp1, gbp2, gz, gx, gy, gZ);
+        // (a full queue leaves the slot to the fp32 evaluation below: the same
+        // formula, at fp32 accuracy)
+        const int i = (sliver > 64.f && bmax > 8.f && q.e) ? atomicAdd(q.n, 1) : kRareCap;
+        if (i < kRareCap) {
+            q.e[i] = RareSlot{f, nf, (int)threadIdx.x, gz, gbp0, gbp1, gbp2};
         } else {
             // near a clip kink the forward's clamped component has the sign of
             // the double-float barycentrics: take those

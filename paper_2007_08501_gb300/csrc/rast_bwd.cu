@@ -26,6 +26,11 @@ __global__ void __launch_bounds__(256) k_rast_bwd(RastBwdArgs a) {
     const bool valid = (r < a.S) && (c < a.S);
     const PixC p = pixel_centre(r, c, a.S);
     const int64_t pix = ((int64_t)n * a.S + r) * a.S + c;
+    __shared__ RareSlot s_rare[kRareCap];
+    __shared__ int s_nrare;
+    if (threadIdx.x == 0) s_nrare = 0;
+    __syncthreads();
+    const RareQueue rq{s_rare, &s_nrare};
     for (int k = 0; k < a.K; ++k) {
         const int64_t s = pix * a.K + k;
         int64_t f = valid ? a.pix_to_face[s] : -1;
@@ -52,35 +57,17 @@ __global__ void __launch_bounds__(256) k_rast_bwd(RastBwdArgs a) {
                 gb2 = a.grad_bary[3 * s + 2];
             }
             if (gz != 0.f || gd != 0.f || gb0 != 0.f || gb1 != 0.f || gb2 != 0.f)
-                slot_corner_grads(R, p, a.fl, gz, gd, gb0, gb1, gb2, g);
+                slot_corner_grads(R, p, a.fl, gz, gd, gb0, gb1, gb2, g, rq, (int)f, nf);
             else
                 f = -1;
         }
         const int key = (int)f;
         const unsigned peers = __match_any_sync(0xffffffffu, key);
         group_sum<9>(peers, g);
-        if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) {
-            // NDC -> view -> world, once per face and warp
-            const float *cam = a.cams + 16 * nf;
-            const float fo = cam[12];
-            const float v0x = R.a.x + R.a.z, v0y = R.a.y + R.a.w;
-            const float Px[3] = {0.f, R.b.x, R.b.z}, Py[3] = {0.f, R.b.y, R.b.w};
-            const float iz[3] = {R.d.y, R.d.z, R.d.w};
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                // x = f x_v / z_v, y = f y_v / z_v: d/dx_v = f/z, d/dz_v = -(x dL/dx + y dL/dy)/z
-                const float xn = v0x + Px[i], yn = v0y + Py[i];
-                const float gxv = g[3 * i] * fo * iz[i];
-                const float gyv = g[3 * i + 1] * fo * iz[i];
-                const float gzv = g[3 * i + 2] - (g[3 * i] * xn + g[3 * i + 1] * yn) * iz[i];
-                const int64_t vi = a.faces[3 * f + i];
-                float *gv = a.grad_verts + 3 * vi;
-                atomicAdd(gv + 0, cam[0] * gxv + cam[3] * gyv + cam[6] * gzv);
-                atomicAdd(gv + 1, cam[1] * gxv + cam[4] * gyv + cam[7] * gzv);
-                atomicAdd(gv + 2, cam[2] * gxv + cam[5] * gyv + cam[8] * gzv);
-            }
-        }
+        if (key >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1)
+            scatter_corner_grads(R, a.cams + 16 * nf, a.faces, f, g, a.grad_verts);  // once per face and warp
     }
+    flush_rare_slots(rq, a.rec, a.cams, a.faces, a.grad_verts, a.S, a.fl);
 }
 
 cudaError_t launch_rast_bwd(const RastBwdArgs &a, int N, cudaStream_t st) {

@@ -168,6 +168,11 @@ __device__ __forceinline__ void screen_bary(const FaceRec &r, float qx, float qy
     b2 = __fmul_rn(e2, r.d.x);
 }
 
+// cross(a, b) = ax by - ay bx in full double-float arithmetic
+__device__ __forceinline__ df df_cross(df ax, df ay, df bx, df by) {
+    return df_sub(df_mul(ax, by), df_mul(ay, bx));
+}
+
 // Double-float difference a - b with the rounding error of the high parts
 // kept exactly (two-sum) and the low parts added to it: not renormalised, good
 // to ~1e-14 relative, which is all the cross products below need.

@@ -410,7 +410,11 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
     // dynamic: sort_cap bin entries; K > 16: afterwards the per-thread lists
     extern __shared__ unsigned long long s_sort[];
     const int tid = threadIdx.x;
-    const int ty = tid / BS, tx = tid % BS;
+    // K <= 16: each warp covers an 8 x 4 block of the bin (about as wide as
+    // tall, like the inflated face bboxes it is culled against); K > 16: two
+    // rows (the tile writer below walks slots in row order)
+    const int ty = KM > 0 ? ((tid >> 5) / (BS / 8)) * 4 + ((tid & 31) >> 3) : tid / BS;
+    const int tx = KM > 0 ? ((tid >> 5) % (BS / 8)) * 8 + (tid & 7) : tid % BS;
     EvalFlags fl = a.fl;
     const bool zcull = fl.clip || !(fl.blur > 0.f);
     const int nb2 = a.nb * a.nb;

@@ -10,9 +10,9 @@ kink of the loss (its margin flags at that width: edge-distance ties, clip
 kinks, blur boundaries, depth ties; the perturbation moves corners by ~3e-4),
 carry upstream gradient, so the loss is smooth in the perturbation.  The
 comparison is loose (fp32 forward: its rounding divided by 2h), and stands
-beside the strict comparison with the FP64 oracle adjoint in the other tests.  Both blends: silhouette (Algorithm 1) and softmax RGB
-(Algorithm 2); sigma and gamma are widened so the loss is smooth at the
-scale of h.
+beside the strict comparison with the FP64 oracle adjoint in the other tests.
+Both blends: silhouette (Algorithm 1) and softmax RGB (Algorithm 2); sigma
+and gamma are widened so the loss is smooth at the scale of h.
 """
 import numpy as np
 import pytest
