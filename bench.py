@@ -70,14 +70,22 @@ WORKLOADS = {
                                   "256x256, K=50, splat radius 0.01 NDC, Norm-composited silhouettes, fwd+bwd to "
                                   "points"),
 }
-# kernels one step launches: rast_blend_fwd = k_stage, k_scan, k_fill, k_fine
-# (+ k_blend_fwd unless the fine pass blends: silhouette, K <= 16);
+# kernels one step launches: rast_blend_fwd = k_stage, k_scan, k_fill, then
+#   K <= 16: k_fine (+ k_blend_fwd for the softmax blend);
+#   K > 16 with clipped barycentrics (or no blur): k_sort_bins, k_fine_stream,
+#   k_frag_attr (which blends the silhouette; + k_blend_fwd for softmax);
 # blend_rast_bwd = k_stage, k_blend_rast_bwd
 
 
 def mesh_kernels_per_step(w):
-    fine_blends = w.blend_mode != "rgb" and w.K <= 16
-    return (4 if fine_blends else 5) + 2
+    rgb = w.blend_mode == "rgb"
+    if w.K <= 16:
+        fwd = 4 + (1 if rgb else 0)
+    elif w.clip_barycentric_coords or not w.blur_radius > 0:
+        fwd = 6 + (1 if rgb else 0)
+    else:
+        fwd = 5          # k_fine with shared-memory lists, then k_blend_fwd
+    return fwd + 2
 # DRAM bytes (read + write) per C-ABI call of a stage -- every kernel of the
 # call, one ncu capture (gpu__time_duration, dram__bytes_read/write, default
 # cache control) with the current kernel source -- keyed by (workload, stage,
