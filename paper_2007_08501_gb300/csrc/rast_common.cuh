@@ -123,6 +123,13 @@ struct PixC {
 };
 __device__ __forceinline__ void pix_coord(int i, int S, float &h, float &l) {
     float num = (float)(S - 2 * i - 1);  // exact for S < 2^24
+    if ((S & (S - 1)) == 0) {
+        // S = 2^m: the quotient num * 2^-m is exact, the same value the
+        // correctly rounded division gives, and the remainder is 0
+        h = __fmul_rn(num, __int_as_float((127 - (31 - __clz(S))) << 23));
+        l = 0.f;
+        return;
+    }
     float Sf = (float)S;
     h = __fdiv_rn(num, Sf);
     l = __fdiv_rn(__fmaf_rn(-h, Sf, num), Sf);
