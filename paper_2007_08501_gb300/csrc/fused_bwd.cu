@@ -164,6 +164,7 @@ __global__ void __launch_bounds__(256, fused_min_blocks(KM, RGB)) k_blend_rast_b
     const bool valid = row < a.S && col < a.S;
     const int64_t pix = ((int64_t)blockIdx.z * a.S + row) * a.S + col;
     const PixC p = pixel_centre(row, col, a.S);
+    const float isg = __frcp_rn(a.sigma);  // d / sigma as d * (1 / sigma) in the per-slot terms
     // softmax blend: slots whose barycentric adjoint needs double-float are
     // queued and done at the end of the block
     __shared__ RareSlot s_rare[RGB ? kRareCap : 1];
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(256, fused_min_blocks(KM, RGB)) k_blend_rast_b
 #pragma unroll
     for (int k = 0; k < KM; ++k) {
         if (S.f[k] < 0) continue;
-        keep *= sigmoidf_(S.d[k] / a.sigma);
+        keep *= sigmoidf_(S.d[k] * isg);
         if (RGB) zmin = fminf(zmin, S.z[k]);
         any = true;
     }
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(256, fused_min_blocks(KM, RGB)) k_blend_rast_b
             C[k][0] = C[k][1] = C[k][2] = 0.f;
             if (S.f[k] < 0) continue;
             const float arg = face_max ? (zmin - S.z[k]) / (range * a.gamma) : ((a.zfar - S.z[k]) / range - m) / a.gamma;
-            W[k] = sigmoidf_(-S.d[k] / a.sigma) * expf(arg);
+            W[k] = sigmoidf_(-S.d[k] * isg) * expf(arg);
             float b[3];
             int64_t vi[3];
             slot_colour(a, s0 + k, S.f[k], C[k], vi, b);
@@ -227,7 +228,7 @@ __global__ void __launch_bounds__(256, fused_min_blocks(KM, RGB)) k_blend_rast_b
         const int f = S.f[k];
         float gd = 0.f, gz = 0.f, gc0 = 0.f, gc1 = 0.f, gc2 = 0.f;
         if (f >= 0) {
-            const float prob = sigmoidf_(-S.d[k] / a.sigma);
+            const float prob = sigmoidf_(-S.d[k] * isg);
             gd = sil * prob;
             if constexpr (RGB) {
                 // c_k - rgb = (sum_{j != k} w_j (c_k - c_j) + delta (c_k - bg)) / D
@@ -240,9 +241,9 @@ __global__ void __launch_bounds__(256, fused_min_blocks(KM, RGB)) k_blend_rast_b
                     d2 += W[j] * (C[k][2] - C[j][2]);
                 }
                 const float gw = (g.x * d0 + g.y * d1 + g.z * d2) * iD * iD;
-                const float q = sigmoidf_(S.d[k] / a.sigma);
+                const float q = sigmoidf_(S.d[k] * isg);
                 const float arg = face_max ? (zmin - S.z[k]) / (range * a.gamma) : ((a.zfar - S.z[k]) / range - m) / a.gamma;
-                gd = sil * prob + gw * expf(arg) * (-prob * q / a.sigma);
+                gd = sil * prob + gw * expf(arg) * (-prob * q * isg);
                 gz = gw * W[k] / a.gamma * (-1.f / range);
                 gc0 = g.x * W[k] * iD;
                 gc1 = g.y * W[k] * iD;
@@ -302,6 +303,7 @@ __global__ void __launch_bounds__(256) k_blend_rast_bwd_any(BlendArgs a, RastBwd
     const bool valid = row < a.S && col < a.S;
     const int64_t pix = ((int64_t)blockIdx.z * a.S + row) * a.S + col;
     const PixC p = pixel_centre(row, col, a.S);
+    const float isg = __frcp_rn(a.sigma);  // d / sigma as d * (1 / sigma) in the per-slot terms
     const int K = a.K;
     const int64_t s0 = pix * K;
     __shared__ RareSlot s_rare[RGB ? kRareCap : 1];
@@ -314,7 +316,7 @@ __global__ void __launch_bounds__(256) k_blend_rast_bwd_any(BlendArgs a, RastBwd
     bool any = false;
     auto take = [&](long long f, float d, int k) {
         if (f < 0) return;
-        keep *= sigmoidf_(d / a.sigma);
+        keep *= sigmoidf_(d * isg);
         if (RGB) zmin = fminf(zmin, __ldg(a.zbuf + s0 + k));
         any = true;
     };
@@ -350,7 +352,7 @@ __global__ void __launch_bounds__(256) k_blend_rast_bwd_any(BlendArgs a, RastBwd
             if (f < 0) continue;
             const float z = a.zbuf[s];
             const float arg = face_max ? (zmin - z) / (range * a.gamma) : ((a.zfar - z) / range - m) / a.gamma;
-            Wl[k] = sigmoidf_(-a.dists[s] / a.sigma) * expf(arg);
+            Wl[k] = sigmoidf_(-a.dists[s] * isg) * expf(arg);
             float b[3];
             int64_t vi[3];
             slot_colour(a, s, f, Cl[k], vi, b);
@@ -376,7 +378,7 @@ __global__ void __launch_bounds__(256) k_blend_rast_bwd_any(BlendArgs a, RastBwd
         for (int j = 0; j < NA; ++j) acc[j] = 0.f;
         int64_t vi[3] = {-1, -1, -1};
         if (f >= 0) {
-            const float prob = sigmoidf_(-d / a.sigma);
+            const float prob = sigmoidf_(-d * isg);
             gd = sil * prob;
             if constexpr (RGB) {
                 float b[3] = {0.f, 0.f, 0.f};
@@ -393,7 +395,7 @@ __global__ void __launch_bounds__(256) k_blend_rast_bwd_any(BlendArgs a, RastBwd
                     d2 += Wl[j] * (Cl[k][2] - Cl[j][2]);
                 }
                 const float gw = (g.x * d0 + g.y * d1 + g.z * d2) * iD * iD;
-                gd += gw * E * (-prob * sigmoidf_(d / a.sigma) / a.sigma);
+                gd += gw * E * (-prob * sigmoidf_(d * isg) * isg);
                 gz = gw * Wk / a.gamma * (-1.f / range);
                 const float gc0 = g.x * Wk * iD, gc1 = g.y * Wk * iD, gc2 = g.z * Wk * iD;
 #pragma unroll

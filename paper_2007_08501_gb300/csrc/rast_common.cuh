@@ -221,6 +221,22 @@ __device__ __forceinline__ void screen_bary_df(const FaceRec &r, const PixC &p, 
     b2 = __fmul_rn(e2, r.d.x);
 }
 
+// The same from two edge functions: b1, b2 as above and b0 = 1 - b1 - b2
+// (the three sum to 1).  b0 then carries an absolute error of ~6e-8 (1 + |b1|
+// + |b2|) instead of a relative one, which is all a clipped fragment needs:
+// clipping divides by the sum of the positive (perspective-corrected)
+// barycentrics, which is 1 plus the magnitudes of the negative ones and so at
+// least the largest magnitude among them: every clipped component keeps ~2e-7
+// absolute (times the ratio of the corner depths).
+__device__ __forceinline__ void screen_bary_df2(const FaceRec &r, const PixC &p, float &b0, float &b1, float &b2) {
+    df qx, qy;
+    local_q_df(r, p, qx, qy);
+    const df ux = {r.b.x, r.e.x}, uy = {r.b.y, r.e.y}, wx = {r.b.z, r.e.z}, wy = {r.b.w, r.e.w};
+    b2 = __fmul_rn(df_cross_f(ux, uy, qx, qy), r.d.x);
+    b1 = __fmul_rn(df_cross_f(qx, qy, wx, wy), r.d.x);
+    b0 = __fsub_rn(__fsub_rn(1.f, b1), b2);
+}
+
 // squared distance from (qx,qy) to segment a + t e, t in [0,1]; returns s, t
 __device__ __forceinline__ float seg_dist2(float ax, float ay, float ex, float ey, float qx, float qy,
                                            float &t) {
@@ -370,7 +386,10 @@ __device__ __forceinline__ void face_fragment(const FaceRec &r, const PixC &p, c
     screen_bary(r, qx, qy, b0, b1, b2);
     // coverage from the same fp32 sign test as the face loop
     bool inside = (b0 >= 0.f) && (b1 >= 0.f) && (b2 >= 0.f);
-    screen_bary_df(r, p, b0, b1, b2);
+    // unclipped extrapolation outputs the barycentrics themselves: each keeps
+    // its relative accuracy there
+    if (fl.clip) screen_bary_df2(r, p, b0, b1, b2);
+    else screen_bary_df(r, p, b0, b1, b2);
     int e;
     float t;
     float s = nearest_edge(r, qx, qy, e, t);
