@@ -43,6 +43,8 @@ bool ws_layout(const rast_params *p, int64_t V, int64_t F, mr::WsLayout *L) {
         off = align256(off + (size_t)(NB + 1) * 4);
         L->cursor = off;
         off = align256(off + (size_t)NB * 4);
+        L->order = off;
+        off = align256(off + (size_t)NB * 4);
         L->lists = off;
         off = align256(off + (size_t)cap * 8);
     }
@@ -186,11 +188,25 @@ static int forward(const rast_params *p, const float *verts, int64_t V, const in
         a.out = out;
         return mr::launch_naive(a, p->N, st) == cudaSuccess ? MESHRAST_OK : MESHRAST_ERR_CUDA;
     }
+    // Large K: the front-to-back streaming fine pass, when every bin's list is
+    // sorted as one piece (capacity <= 8192) and a candidate's depth is never
+    // below its face's nearest corner (clipped barycentrics, or no blur);
+    // Fragment attributes (and the silhouette blend) in a pass of their own.
+    const bool zcull = p->clip_barycentric_coords || !(p->blur_radius > 0.f);
+    // (work items: 32-pixel blocks of every bin, counted by a 32-bit queue)
+    const bool items_fit = L.NB * (int64_t)(p->bin_size * p->bin_size / 32) < 0x7fffffffLL;
+    const bool streaming =
+        K > 16 && zcull && p->max_faces_per_bin <= 8192 && items_fit && pix_to_face && zbuf && bary && dists;
+    // The block fine pass takes bins longest first.  The streaming pass keeps
+    // the natural (image, bin) order: its items are small, and consecutive
+    // items of one image keep that image's face records and lists in L2.
+    int *const order = streaming ? nullptr : reinterpret_cast<int *>(ws + L.order);
     mr::ScanArgs sa;
     sa.counts = reinterpret_cast<const int *>(ws + L.counts);
     sa.eff = reinterpret_cast<int *>(ws + L.eff);
     sa.offsets = reinterpret_cast<int *>(ws + L.offsets);
     sa.cursor = reinterpret_cast<int *>(ws + L.cursor);
+    sa.order = order;
     sa.NB = L.NB;
     sa.capacity = L.capacity;
     sa.max_per_bin = p->max_faces_per_bin;
@@ -221,6 +237,7 @@ static int forward(const rast_params *p, const float *verts, int64_t V, const in
     ka.lists = reinterpret_cast<unsigned long long *>(ws + L.lists);
     ka.eff = reinterpret_cast<const int *>(ws + L.eff);
     ka.offsets = reinterpret_cast<const int *>(ws + L.offsets);
+    ka.order = order;
     ka.queue = reinterpret_cast<unsigned *>(ws + L.queue);
     ka.redo_count = reinterpret_cast<unsigned *>(ws + L.redo);
     ka.items = (int)L.NB;
@@ -230,14 +247,7 @@ static int forward(const rast_params *p, const float *verts, int64_t V, const in
     ka.fl = fl;
     ka.out = out;
     std::memset(&ka.blend, 0, sizeof(ka.blend));
-    // Large K: the front-to-back streaming fine pass, when every bin's list is
-    // sorted as one piece (capacity <= 8192) and a candidate's depth is never
-    // below its face's nearest corner (clipped barycentrics, or no blur);
-    // Fragment attributes (and the silhouette blend) in a pass of their own.
-    const bool zcull = p->clip_barycentric_coords || !(p->blur_radius > 0.f);
-    // (work items: 32-pixel blocks of every bin, counted by a 32-bit queue)
-    const bool items_fit = L.NB * (int64_t)(p->bin_size * p->bin_size / 32) < 0x7fffffffLL;
-    if (K > 16 && zcull && p->max_faces_per_bin <= 8192 && items_fit && pix_to_face && zbuf && bary && dists) {
+    if (streaming) {
         int cap = 256;
         while (cap < p->max_faces_per_bin) cap <<= 1;
         ka.sort_cap = cap;

@@ -145,9 +145,10 @@ __device__ void redo_pixel(const FineArgs &a, const unsigned long long *ent, int
 __global__ void __launch_bounds__(256) k_sort_bins(FineArgs a) {
     extern __shared__ unsigned long long s_sort[];
     for (int item = blockIdx.x; item < a.items; item += gridDim.x) {
-        const int cnt = a.eff[item];  // <= sort_cap (checked on the host); uniform over the block
+        const int bin = a.order ? __ldg(a.order + item) : item;  // longest bins first
+        const int cnt = a.eff[bin];  // <= sort_cap (checked on the host); uniform over the block
         if (cnt <= 1) continue;
-        unsigned long long *list = a.lists + a.offsets[item];
+        unsigned long long *list = a.lists + a.offsets[bin];
         sort_entries<256, true>(s_sort, list, cnt);
         for (int i = threadIdx.x; i < cnt; i += 256) list[i] = s_sort[i];
         __syncthreads();
@@ -182,7 +183,8 @@ __global__ void __launch_bounds__(256, 4) k_fine_stream(FineArgs a) {
         if (lane == 0) item = (long long)atomicAdd(a.queue, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= total) break;
-        const int bin = (int)(item / SUB), sub = (int)(item - (long long)bin * SUB);
+        const int qb = (int)(item / SUB), sub = (int)(item - (long long)qb * SUB);
+        const int bin = a.order ? __ldg(a.order + qb) : qb;  // longest bins first
         const int n = bin / nb2, rem = bin - n * nb2;
         const int by = rem / a.nb, bx = rem - by * a.nb;
         const int r = by * BS + (sub / (BS / 8)) * 4 + (lane >> 3);

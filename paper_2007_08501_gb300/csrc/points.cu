@@ -817,6 +817,7 @@ int pts_rasterize_fwd(const pts_params *p, const float *points, int64_t P, const
     sa.eff = reinterpret_cast<int *>(ws + L.eff);
     sa.offsets = reinterpret_cast<int *>(ws + L.offsets);
     sa.cursor = a.cursor;
+    sa.order = nullptr;
     sa.NB = L.NB;
     sa.capacity = L.capacity;
     sa.max_per_bin = p->max_points_per_bin;

@@ -474,6 +474,7 @@ struct WsLayout {
     size_t eff;         // NB x int32 counts clamped to capacity
     size_t offsets;     // (NB + 1) x int32
     size_t cursor;      // NB x int32
+    size_t order;       // NB x int32 bins in the fine pass's queue order
     size_t lists;       // capacity x uint64 entries (depth key << 32 | face id)
     int64_t nb;         // bins per side
     int64_t NB;         // N * nb * nb

@@ -199,6 +199,41 @@ __global__ void __launch_bounds__(1024) k_scan(ScanArgs a) {
         *a.maxcount = maxc_s;
         *a.total = (long long)tot_s;
     }
+    if (!a.order) return;
+    // Queue order of the fine pass: bins by descending work class (the bit
+    // length of the clamped count), a counting sort over 32 classes, so the
+    // longest bins start first and the short ones fill the tail.  The order
+    // within a class is whatever the atomics give: each bin's output depends
+    // on that bin alone.
+    __shared__ int cls_n[32];
+    if (tid < 32) cls_n[tid] = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < a.NB; base += 1024) {  // every lane takes every round
+        const int64_t b = base + tid;
+        const int cls = (b < a.NB) ? 32 - __clz(a.eff[b]) : -1;  // 0: empty bin; eff < 2^31
+        const unsigned grp = __match_any_sync(0xffffffffu, cls);
+        if (cls >= 0 && lane == __ffs(grp) - 1) atomicAdd(&cls_n[cls], __popc(grp));
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int s = 0;
+        for (int c = 31; c >= 0; --c) {
+            const int n = cls_n[c];
+            cls_n[c] = s;  // first position of class c
+            s += n;
+        }
+    }
+    __syncthreads();
+    for (int64_t base = 0; base < a.NB; base += 1024) {
+        const int64_t b = base + tid;
+        const int cls = (b < a.NB) ? 32 - __clz(a.eff[b]) : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, cls);
+        const int leader = __ffs(grp) - 1;
+        int first = 0;
+        if (cls >= 0 && lane == leader) first = atomicAdd(&cls_n[cls], __popc(grp));
+        first = __shfl_sync(0xffffffffu, first, leader);
+        if (cls >= 0) a.order[first + __popc(grp & ((1u << lane) - 1u))] = (int)b;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -424,7 +459,8 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
         const int item = s_item;
         __syncthreads();
         if (item >= a.items) break;
-        const int n = item / nb2, rem = item - n * nb2;
+        const int bin = a.order ? __ldg(a.order + item) : item;  // longest bins first
+        const int n = bin / nb2, rem = bin - n * nb2;
         const int by = rem / a.nb, bx = rem - by * a.nb;
         const int r = by * BS + ty, c = bx * BS + tx;
         fl.znear = __ldg(a.cams + 16 * n + 13);
@@ -446,8 +482,8 @@ __global__ void __launch_bounds__(BS *BS) k_fine(FineArgs a) {
                 wy0 = pc_hi((int)rmax, a.S);
             }
         }
-        const int cnt = a.eff[item];
-        const int off = a.offsets[item];
+        const int cnt = a.eff[bin];
+        const int off = a.offsets[bin];
         TopK<(KM > 0 ? KM : 1)> tk;
         SmemTopK stk;
         // The bin's list is sorted front to back in segments of up to sort_cap

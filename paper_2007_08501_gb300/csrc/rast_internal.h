@@ -29,6 +29,7 @@ struct StageArgs {
 struct ScanArgs {
     const int *counts;
     int *eff, *offsets, *cursor;
+    int *order;  // non-NULL: bins by descending work class, for the fine pass's queue
     int64_t NB, capacity;
     int max_per_bin;
     unsigned *queue, *status;
@@ -72,6 +73,7 @@ struct FineArgs {
     const float *cams;
     unsigned long long *lists;  // K > 16: each block sorts its bins' lists in place
     const int *eff, *offsets;
+    const int *order;           // queue position -> bin (bins by descending work class)
     unsigned *queue;
     unsigned *redo_count;       // large-K streaming pass: pixels redone by a whole warp
     int items, nb, S, K;
