@@ -231,13 +231,9 @@ __global__ void __launch_bounds__(256, 4) k_fine_stream(FineArgs a) {
             // keys ascend along the list: once the first is behind every lane, the rest is too
             if (__shfl_sync(0xffffffffu, key, 0) > wthr) break;
             const bool hit = bb.x <= wx1 && bb.y >= wx0 && bb.z <= wy1 && bb.w >= wy0 && !(key > wthr);
-            if (hit) {
-                // the loop below reads the first 64 bytes of each hit's record
-                // one face after another: start their L2 reads now, together
-                const float4 *rp = reinterpret_cast<const float4 *>(a.rec + fid);
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(rp + kRecA));
-                asm volatile("prefetch.global.L1 [%0];" ::"l"(rp + kRecD));
-            }
+            // the loop below reads the first 64 bytes of each hit's record one
+            // face after another: start their L2 reads now, together
+            if (hit) prefetch_rec(a.rec, fid);
             unsigned mask = __ballot_sync(0xffffffffu, hit);
             while (mask) {
                 const int src = __ffs(mask) - 1;

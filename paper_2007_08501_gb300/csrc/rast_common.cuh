@@ -63,6 +63,14 @@ static_assert(sizeof(FaceRec) == 96, "face record is 96 bytes");
 // float4 index of each field in a record in global memory
 constexpr int kRecA = 0, kRecB = 1, kRecD = 2, kRecE = 3, kRecC = 4, kRecH = 5;
 
+// Start the reads of the first 64 bytes of face f's record (a, b, d, e) into
+// L1 ahead of their use: the loads that follow find them there.
+__device__ __forceinline__ void prefetch_rec(const FaceRec *rec, int f) {
+    const float4 *rp = reinterpret_cast<const float4 *>(rec + f);
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(rp + kRecA));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(rp + kRecD));
+}
+
 // ---------------------------------------------------------------------------
 // double-float (unevaluated sum hi + lo) arithmetic, error-free transforms
 // of Knuth (two-sum) and Dekker (two-product via fma).
