@@ -87,21 +87,28 @@ def mesh_kernels_per_step(w):
         fwd = 5          # k_fine with shared-memory lists, then k_blend_fwd
     return fwd + 2
 # DRAM bytes (read + write) per C-ABI call of a stage -- every kernel of the
-# call, one ncu capture (gpu__time_duration, dram__bytes_read/write, default
-# cache control) with the current kernel source -- keyed by (workload, stage,
-# bin size); a combination without an entry reports null.
+# call, from one ncu capture (gpu__time_duration, dram__bytes_read/write,
+# --clock-control none) of the current kernel source -- keyed by (workload,
+# stage, bin size); a combination without an entry reports null.  Workload 4
+# is captured on its first 2 of 20 views (--max-images 2) and scaled by 10:
+# every view carries the same mesh, so each kernel's traffic grows with the
+# views.
 TRAFFIC_BYTES = {
     ("1", "fwd", 16): {"kernel": "rast_blend_fwd call: k_stage + k_scan + k_fill + k_fine<8,16,0> + k_blend_fwd<8>",
-                       "bytes": 160671143},
-    ("1", "bwd", 16): {"kernel": "blend_rast_bwd call: k_stage + k_blend_rast_bwd<8,1>", "bytes": 105950868},
-    ("1", "fwd", 8): {"kernel": "rast_blend_fwd call: k_stage + k_scan + k_fill + k_fine<8,8,0> + k_blend_fwd<8>",
-                      "bytes": 166800670},
-    ("1", "bwd", 8): {"kernel": "blend_rast_bwd call: k_stage + k_blend_rast_bwd<8,1>", "bytes": 106005435},
+                       "bytes": 164500000, "profile": "profiles/launch_list_8x5120faces_256px_K8.md"},
+    ("1", "bwd", 16): {"kernel": "blend_rast_bwd call: k_stage + k_blend_rast_bwd<8,1>", "bytes": 106200000,
+                       "profile": "profiles/launch_list_8x5120faces_256px_K8.md"},
+    ("4", "fwd", 16): {"kernel": "rast_blend_fwd call: k_stage + k_scan + k_fill + k_sort_bins + "
+                                 "k_fine_stream<16> + k_frag_attr<1>", "bytes": 11540000000,
+                       "profile": "profiles/launch_list_20x81920faces_512px_K50.md (2 views x 10)"},
+    ("4", "bwd", 16): {"kernel": "blend_rast_bwd call: k_stage + k_blend_rast_bwd_any<0>", "bytes": 4233000000,
+                       "profile": "profiles/launch_list_20x81920faces_512px_K50.md (2 views x 10)"},
     ("points", "rast_fwd", 8): {"kernel": "pts_rasterize_fwd call: k_pstage + k_scan + k_pfill + k_pfine<0,8>",
-                                "bytes": 552453578},
+                                "bytes": 552453578, "profile": "profiles/points_8x200000pts_256px_K50.md"},
     # the same rasterizer call (compositing mode does not enter it)
     ("points_norm", "rast_fwd", 8): {"kernel": "pts_rasterize_fwd call: k_pstage + k_scan + k_pfill + "
-                                               "k_pfine<0,8>", "bytes": 552453578},
+                                               "k_pfine<0,8>", "bytes": 552453578,
+                                     "profile": "profiles/points_8x200000pts_256px_K50.md"},
 }
 
 
@@ -550,6 +557,9 @@ def run_ours(args):
         raise RuntimeError("device status %d after the first step" % st)
     mc, tot = ops.rast_bin_occupancy(pipe.p, b.V, b.F, pipe.ws)
     fine_tests = int(tot) * tuned["bin_size"] ** 2
+    # pixels the large-K streaming fine pass handed to a whole warp (ring overflow)
+    lay = ops.rast_workspace_bin_layout(pipe.p, b.V, b.F)
+    redo_pixels = int(pipe.ws[lay["redo"]:lay["redo"] + 4].cpu().numpy().view(np.uint32)[0])
     pipe.capture()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -585,7 +595,9 @@ def run_ours(args):
     tr = TRAFFIC_BYTES.get((args.workload, dom, tuned["bin_size"]))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": tr["bytes"] if tr else None,
-                "traffic_kernel": tr["kernel"] if tr else None, "algorithmic_bytes": alg[dom], "kernel": dom,
+                "traffic_kernel": tr["kernel"] if tr else None,
+                "traffic_source": ("ncu capture, " + tr["profile"]) if tr else None,
+                "algorithmic_bytes": alg[dom], "kernel": dom,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
                 else "fallback 6.8 TB/s"}
     stage_frac = {k: round(alg[k] / (stages[k] / 1e3) / 1e9 / peak, 4) for k in stages}
@@ -707,6 +719,7 @@ def run_ours(args):
                                 "fused with the rasterizer adjoint)",
                        "l2": "flushed between steps (256 MiB write), outside the timed events",
                        "bin_occupancy": {"max_faces_in_a_bin": mc, "total_entries": tot},
+                       "redo_pixels": redo_pixels,
                        "parallelism": "replicas x%d" % world},
             "roofline": roofline,
             "stages_ms": {k: round(v, 4) for k, v in stages.items()},
@@ -882,7 +895,9 @@ def run_points(args):
     tr = TRAFFIC_BYTES.get((args.workload, dom, bin_size))
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": tr["bytes"] if tr else None,
-                "traffic_kernel": tr["kernel"] if tr else None, "algorithmic_bytes": alg[dom], "kernel": dom,
+                "traffic_kernel": tr["kernel"] if tr else None,
+                "traffic_source": ("ncu capture, " + tr["profile"]) if tr else None,
+                "algorithmic_bytes": alg[dom], "kernel": dom,
                 "peak_source": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind if peak_kind == "measured"
                 else "fallback 6.8 TB/s"}
     # end to end with host buffers
