@@ -387,15 +387,18 @@ def algorithmic_bytes(w):
     cams = 64 * N
     mesh_in = 12 * V + 24 * F + cams + 16 * N
     rgb_extra = 24 * F + 12 * V if w.blend_mode == "rgb" else 0   # faces + colours gathered by the rgb blend
+    # fragment bytes a blend reads per slot: the silhouette (Algorithm 1) needs
+    # only the face id and the distance (8 + 4), the softmax blend all 28
+    frag_in = 12 if w.blend_mode == "sil" else 28
     return {
         "rast_fwd": mesh_in + 28 * slots,                                  # write fragments
         "fwd": mesh_in + 28 * slots + 16 * pix + rgb_extra,                # fused: fragments + rgba out
         "shade_fwd": 28 * slots + 16 * pix + 24 * F + 36 * V,              # fragments + faces, verts, normals, colours
         "shade_bwd": 28 * slots + 16 * pix + 20 * slots + 24 * F + 72 * V,
-        "blend_fwd": 28 * slots + 16 * pix + rgb_extra,                    # read fragments, write rgba
-        "blend_bwd": 28 * slots + 16 * pix + 20 * slots + rgb_extra + 12 * V,
+        "blend_fwd": frag_in * slots + 16 * pix + rgb_extra,               # read fragments, write rgba
+        "blend_bwd": frag_in * slots + 16 * pix + 20 * slots + rgb_extra + 12 * V,
         "rast_bwd": mesh_in + 28 * slots + 12 * V,                         # ids + grad fragments
-        "bwd": mesh_in + 28 * slots + 16 * pix + rgb_extra + 24 * V,       # fused: fragments + grad image in,
+        "bwd": mesh_in + frag_in * slots + 16 * pix + rgb_extra + 24 * V,  # fused: fragments + grad image in,
     }                                                                      # vertex + colour grads out
 
 
@@ -715,8 +718,11 @@ def run_ours(args):
                        "bin_size": tuned["bin_size"], "max_faces_per_bin": tuned["max_faces_per_bin"],
                        "max_bin_entries": tuned["max_bin_entries"], "autotuned": True,
                        "graph": "one CUDA graph per C-ABI call",
-                       "calls": "rast_blend_fwd (fine pass blends as it writes) + blend_rast_bwd (blend adjoint "
-                                "fused with the rasterizer adjoint)",
+                       "calls": "rast_blend_fwd (%s) + blend_rast_bwd (blend adjoint fused with the rasterizer "
+                                "adjoint)" % ("the silhouette blend applied as the Fragment data is written: by the "
+                                              "fine pass for K <= 16, by the attribute pass for K > 16"
+                                              if w.blend_mode == "sil" else
+                                              "softmax blend kernel inside the call, after the fine pass"),
                        "l2": "flushed between steps (256 MiB write), outside the timed events",
                        "bin_occupancy": {"max_faces_in_a_bin": mc, "total_entries": tot},
                        "redo_pixels": redo_pixels,
