@@ -93,6 +93,8 @@ def _case(mode, K, persp, clip, blur, bin_size, S=48, levels=(3, 2), seed=0):
     (ops.BLEND_RGB, 16, True, True, BLUR, 16),
     (ops.BLEND_RGB, 5, True, True, BLUR, 16),   # generic K
     (ops.BLEND_SIL, 24, True, False, BLUR, 8),  # generic K
+    (ops.BLEND_SIL, 13, True, True, BLUR, 16),  # generic K, odd: slots one at a time
+    (ops.BLEND_SIL, 64, True, True, BLUR, 16),  # largest K: 64 KB of per-slot probabilities
 ])
 def test_fused_backward_matches_oracle_chain(mode, K, persp, clip, blur, bin_size):
     _case(mode, K, persp, clip, blur, bin_size)
