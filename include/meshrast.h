@@ -326,6 +326,12 @@ typedef struct {
     int64_t redo;                          /* uint32 at this byte offset: pixels the large-K (K > 16)
                                               fine pass handed to a whole warp (their unsettled
                                               candidates outgrew the per-pixel ring) */
+    int64_t order;                         /* int32[NB] at this byte offset: the order in which
+                                              the block fine pass takes the bins, a permutation
+                                              of 0 .. NB-1 with the bit length of eff[b]
+                                              non-increasing (longest bins first); written by
+                                              every binned forward except the large-K streaming
+                                              pass, which takes the bins in index order */
 } rast_bin_layout;
 MESHRAST_API int rast_workspace_bin_layout(const rast_params *p, int64_t V, int64_t F, rast_bin_layout *out);
 

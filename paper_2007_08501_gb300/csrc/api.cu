@@ -571,6 +571,7 @@ int rast_workspace_bin_layout(const rast_params *p, int64_t V, int64_t F, rast_b
     out->capacity = L.capacity;
     out->bytes = (int64_t)L.bytes;
     out->redo = (int64_t)L.redo;
+    out->order = (int64_t)L.order;
     return MESHRAST_OK;
 }
 

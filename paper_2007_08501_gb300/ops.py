@@ -63,7 +63,8 @@ class blend_params(ctypes.Structure):
 class rast_bin_layout(ctypes.Structure):
     _fields_ = [("counts", ctypes.c_int64), ("eff", ctypes.c_int64), ("offsets", ctypes.c_int64),
                 ("lists", ctypes.c_int64), ("nb", ctypes.c_int64), ("NB", ctypes.c_int64),
-                ("capacity", ctypes.c_int64), ("bytes", ctypes.c_int64), ("redo", ctypes.c_int64)]
+                ("capacity", ctypes.c_int64), ("bytes", ctypes.c_int64), ("redo", ctypes.c_int64),
+                ("order", ctypes.c_int64)]
 
 
 class MeshRastError(RuntimeError):

@@ -37,6 +37,11 @@ def _gpu_bins(d, N, S, K, blur, bin_size, max_per_bin, clip=True):
     eff = raw[L["eff"]:L["eff"] + 4 * NB].view(np.int32)
     offs = raw[L["offsets"]:L["offsets"] + 4 * (NB + 1)].view(np.int32)
     lists = raw[L["lists"]:L["lists"] + 8 * L["capacity"]].view(np.uint64)
+    order = raw[L["order"]:L["order"] + 4 * NB].view(np.int32)
+    # the fine pass's queue: every bin once, longest first by the bit length of its count
+    np.testing.assert_array_equal(np.sort(order), np.arange(NB))
+    bits = np.array([int(e).bit_length() for e in eff[order]])
+    assert np.all(np.diff(bits) <= 0)
     return L, counts, eff, offs, lists
 
 
