@@ -57,6 +57,10 @@ def test_static_workspace_forward_matches_rast_mesh_fwd_twice():
     ref2, got2 = _both(b2, 100, 3, 8, 512, clip=False)
     _same(ref2, got2)
     assert (ref2[0] >= 0).any()
+    # third call: K > 16, the streaming fine pass and the attribute pass
+    ref3, got3 = _both(b2, 64, 20, 16, 1024)
+    _same(ref3, got3)
+    assert (ref3[0] >= 0).any()
 
 
 def test_static_call_allocates_nothing_and_reports_its_status():
