@@ -164,6 +164,32 @@ __global__ void __launch_bounds__(256) k_sort_bins(FineArgs a) {
 // ---------------------------------------------------------------------------
 constexpr int kWarpsPerBlock = 8;
 
+// Whether no point of the rectangle [x0, x1] x [y0, y1] can be within
+// sqrt(blur) of the face: the whole rectangle lies beyond the line of one of
+// its edges by more than that.  The barycentric of the opposite corner is
+// affine in the point, so its largest value over the rectangle is taken at a
+// corner; beyond the line it is negative and the squared distance to the line
+// is b^2 H.  A 10 % margin on the squared distance covers the fp32 rounding,
+// and slivers (whose fp32 barycentrics are less accurate) are never rejected:
+// a face this rejects is no candidate for any pixel of the rectangle.
+__device__ __forceinline__ bool rect_beyond_edge(const float4 &ra, const float4 &rb, const float4 &rd,
+                                                 const float4 &rh, float x0, float x1, float y0, float y1,
+                                                 float blur) {
+    const float ux = rb.x, uy = rb.y, wx = rb.z, wy = rb.w, iA = rd.x;
+    const float sliver = (ux * ux + uy * uy + wx * wx + wy * wy) * fabsf(iA);
+    const float qx = x0 - (ra.x + ra.z), qy = y0 - (ra.y + ra.w);
+    const float b2 = (ux * qy - uy * qx) * iA, b1 = (qx * wy - qy * wx) * iA, b0 = 1.f - b1 - b2;
+    const float dx = x1 - x0, dy = y1 - y0;
+    const float g2x = -uy * iA * dx, g2y = ux * iA * dy, g1x = wy * iA * dx, g1y = -wx * iA * dy;
+    const float m2 = b2 + fmaxf(g2x, 0.f) + fmaxf(g2y, 0.f);
+    const float m1 = b1 + fmaxf(g1x, 0.f) + fmaxf(g1y, 0.f);
+    const float m0 = b0 + fmaxf(-g1x - g2x, 0.f) + fmaxf(-g1y - g2y, 0.f);
+    const float lim = blur * 1.1f;
+    const bool out = (m0 < 0.f && m0 * m0 * rh.x > lim) || (m1 < 0.f && m1 * m1 * rh.y > lim) ||
+                     (m2 < 0.f && m2 * m2 * rh.z > lim);
+    return out && sliver <= 64.f;
+}
+
 template <int BS>
 __global__ void __launch_bounds__(256, 4) k_fine_stream(FineArgs a) {
     constexpr int SUB = BS * BS / 32;  // 8 x 4 pixel blocks per bin
@@ -230,10 +256,17 @@ __global__ void __launch_bounds__(256, 4) k_fine_stream(FineArgs a) {
             }
             // keys ascend along the list: once the first is behind every lane, the rest is too
             if (__shfl_sync(0xffffffffu, key, 0) > wthr) break;
-            const bool hit = bb.x <= wx1 && bb.y >= wx0 && bb.z <= wy1 && bb.w >= wy0 && !(key > wthr);
-            // the loop below reads the first 64 bytes of each hit's record one
-            // face after another: start their L2 reads now, together
-            if (hit) prefetch_rec(a.rec, fid);
+            bool hit = bb.x <= wx1 && bb.y >= wx0 && bb.z <= wy1 && bb.w >= wy0 && !(key > wthr);
+            if (hit) {
+                // the first 64 bytes of the record, which the loop below reads
+                // one face after another, come to L1 here for all faces at once
+                const float4 *rp = reinterpret_cast<const float4 *>(a.rec + fid);
+                const float4 ra = __ldg(rp + kRecA), rb = __ldg(rp + kRecB), rd = __ldg(rp + kRecD);
+                const float4 rh = __ldg(rp + kRecH);
+                asm volatile("prefetch.global.L1 [%0];" ::"l"(rp + kRecE));
+                // a face whose bbox meets the block but whose blur region misses it
+                if (fl.blur > 0.f && rect_beyond_edge(ra, rb, rd, rh, wx0, wx1, wy0, wy1, fl.blur)) hit = false;
+            }
             unsigned mask = __ballot_sync(0xffffffffu, hit);
             while (mask) {
                 const int src = __ffs(mask) - 1;
