@@ -95,8 +95,8 @@ def mesh_kernels_per_step(w):
 # views.
 TRAFFIC_BYTES = {
     ("1", "fwd", 16): {"kernel": "rast_blend_fwd call: k_stage + k_scan + k_fill + k_fine<8,16,0> + k_blend_fwd<8>",
-                       "bytes": 164500000, "profile": "profiles/launch_list_8x5120faces_256px_K8.md"},
-    ("1", "bwd", 16): {"kernel": "blend_rast_bwd call: k_stage + k_blend_rast_bwd<8,1>", "bytes": 106200000,
+                       "bytes": 142300000, "profile": "profiles/launch_list_8x5120faces_256px_K8.md"},
+    ("1", "bwd", 16): {"kernel": "blend_rast_bwd call: k_stage + k_blend_rast_bwd<8,1>", "bytes": 106000000,
                        "profile": "profiles/launch_list_8x5120faces_256px_K8.md"},
     ("4", "fwd", 16): {"kernel": "rast_blend_fwd call: k_stage + k_scan + k_fill + k_sort_bins + "
                                  "k_fine_stream<16> + k_frag_attr<1>", "bytes": 11558000000,

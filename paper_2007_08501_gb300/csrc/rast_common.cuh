@@ -63,6 +63,23 @@ static_assert(sizeof(FaceRec) == 96, "face record is 96 bytes");
 // float4 index of each field in a record in global memory
 constexpr int kRecA = 0, kRecB = 1, kRecD = 2, kRecE = 3, kRecC = 4, kRecH = 5;
 
+// Stores that ask L2 to keep their lines ahead of other data (evict_last):
+// Fragment data that the blend and the backward read back right away.
+__device__ __forceinline__ unsigned long long l2_keep_policy() {
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void st_keep(float4 *p, float4 v, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y),
+                 "f"(v.z), "f"(v.w), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void st_keep(longlong2 *p, longlong2 v, unsigned long long pol) {
+    asm volatile("st.global.L2::cache_hint.v2.s64 [%0], {%1, %2}, %3;" ::"l"(p), "l"(v.x), "l"(v.y), "l"(pol)
+                 : "memory");
+}
+
 // Start the reads of the first 64 bytes of face f's record (a, b, d, e) into
 // L1 ahead of their use: the loads that follow find them there.
 __device__ __forceinline__ void prefetch_rec(const FaceRec *rec, int f) {

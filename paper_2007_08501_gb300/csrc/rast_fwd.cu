@@ -355,6 +355,7 @@ __device__ __forceinline__ void write_pixel_vec(const FineOut &o, int64_t pix, i
     if constexpr (BL) fb.begin(bl, tk.f[0] != 0x7fffffff, tk.z[0]);
     const bool store = !BL || bl.frag;
     const int64_t s0 = pix * KM;
+    const unsigned long long pol = l2_keep_policy();
     longlong2 *ip = reinterpret_cast<longlong2 *>(o.pix_to_face + s0);
     float4 *zp = reinterpret_cast<float4 *>(o.zbuf + s0);
     float4 *dp = reinterpret_cast<float4 *>(o.dists + s0);
@@ -365,7 +366,7 @@ __device__ __forceinline__ void write_pixel_vec(const FineOut &o, int64_t pix, i
         longlong2 v;
         v.x = (tk.f[2 * j] == 0x7fffffff) ? -1ll : (long long)tk.f[2 * j];
         v.y = (tk.f[2 * j + 1] == 0x7fffffff) ? -1ll : (long long)tk.f[2 * j + 1];
-        ip[j] = v;
+        st_keep(ip + j, v, pol);
     }
     // four slots at a time: one float4 of depths, of distances, three of barycentrics
 #pragma unroll
@@ -390,11 +391,11 @@ __device__ __forceinline__ void write_pixel_vec(const FineOut &o, int64_t pix, i
             if constexpr (BL) fb.slot(bl, tk.f[k], zz[i], dd[i], bb[i]);
         }
         if (!store) continue;
-        zp[j] = make_float4(zz[0], zz[1], zz[2], zz[3]);
-        dp[j] = make_float4(dd[0], dd[1], dd[2], dd[3]);
-        bp[3 * j] = make_float4(bb[0][0], bb[0][1], bb[0][2], bb[1][0]);
-        bp[3 * j + 1] = make_float4(bb[1][1], bb[1][2], bb[2][0], bb[2][1]);
-        bp[3 * j + 2] = make_float4(bb[2][2], bb[3][0], bb[3][1], bb[3][2]);
+        st_keep(zp + j, make_float4(zz[0], zz[1], zz[2], zz[3]), pol);
+        st_keep(dp + j, make_float4(dd[0], dd[1], dd[2], dd[3]), pol);
+        st_keep(bp + 3 * j, make_float4(bb[0][0], bb[0][1], bb[0][2], bb[1][0]), pol);
+        st_keep(bp + 3 * j + 1, make_float4(bb[1][1], bb[1][2], bb[2][0], bb[2][1]), pol);
+        st_keep(bp + 3 * j + 2, make_float4(bb[2][2], bb[3][0], bb[3][1], bb[3][2]), pol);
     }
     if constexpr (BL) fb.end(bl, pix);
 }
