@@ -70,6 +70,32 @@ def test_large_k_streaming_path(S, K, bin_size):
     _full_check(b, S, K, BLUR, bin_size, True, True)
 
 
+def test_streaming_pass_equals_the_block_fine_pass_at_full_size():
+    # The first 2 of the 20 views of the K = 50 benchmark batch (512 x 512),
+    # rendered twice through rast_mesh_fwd: a bin capacity of 8192 takes the
+    # streaming fine pass (bins sorted front to back, warps settling slots as
+    # they go, the block-wide edge-line cull, the warp redo) and the attribute
+    # pass; 8200 (above the streaming pass's limit) takes the block fine pass
+    # with per-pixel lists in shared memory.  Both end in the same face tests,
+    # depth keys and fragment arithmetic, so every output is identical.
+    w = workloads.workload(4)
+    b = workloads.first_images(w.batch, 2)
+    d = to_dev(b)
+    blur = float(np.float32(w.blur_radius))
+    outs = []
+    for cap in (8192, 8200):
+        p = ops.make_rast_params(b.N, w.image_size, w.K, np.float32(blur), 16, cap, True, True)
+        ws = ops.alloc_workspace(p, b.V, b.F)
+        fr = ops.alloc_fragments(b.N, w.image_size, w.K)
+        ops.rast_mesh_fwd(p, d["verts"], d["faces"], d["first_face"], d["num_faces"], d["cams"], *fr, ws)
+        assert ops.rast_query_status(ws) == 0
+        outs.append(fr)
+        del ws
+    for x, y in zip(*outs):
+        assert torch.equal(x, y)
+    assert (outs[0][0][..., w.K - 1] >= 0).float().mean() > 0.3   # most pixels hold K faces
+
+
 def test_large_k_ring_overflow_is_redone_by_a_warp():
     """30 faces tilted away from the camera: each has one corner at depth 1 (its
     sort key), while at the pixels near its far edge its depth is ~5.  No
