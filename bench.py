@@ -560,7 +560,7 @@ def run_ours(args):
         raise RuntimeError("device status %d after the first step" % st)
     mc, tot = ops.rast_bin_occupancy(pipe.p, b.V, b.F, pipe.ws)
     fine_tests = int(tot) * tuned["bin_size"] ** 2
-    # pixels the large-K streaming fine pass handed to a whole warp (ring overflow)
+    # pixels the large-K streaming fine pass handed to its second pass (ring overflow)
     lay = ops.rast_workspace_bin_layout(pipe.p, b.V, b.F)
     redo_pixels = int(pipe.ws[lay["redo"]:lay["redo"] + 4].cpu().numpy().view(np.uint32)[0])
     pipe.capture()

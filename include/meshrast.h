@@ -324,8 +324,8 @@ typedef struct {
     int64_t capacity;                      /* entries lists can hold */
     int64_t bytes;                         /* = rast_workspace_bytes */
     int64_t redo;                          /* uint32 at this byte offset: pixels the large-K (K > 16)
-                                              fine pass handed to a whole warp (their unsettled
-                                              candidates outgrew the per-pixel ring) */
+                                              fine pass handed to its second pass (their unsettled
+                                              candidates outgrew the 16-entry per-pixel ring) */
     int64_t order;                         /* int32[NB] at this byte offset: the order in which
                                               the block fine pass takes the bins, a permutation
                                               of 0 .. NB-1 with the bit length of eff[b]

@@ -23,6 +23,8 @@ bool ws_layout(const rast_params *p, int64_t V, int64_t F, mr::WsLayout *L) {
     L->total = 8;
     L->maxcount = 16;
     L->redo = 20;
+    L->redo_q = 24;
+    L->redo_head = 28;
     off = 256;
     L->records = off;
     off = align256(off + (size_t)F * sizeof(mr::FaceRec));
@@ -45,6 +47,11 @@ bool ws_layout(const rast_params *p, int64_t V, int64_t F, mr::WsLayout *L) {
         off = align256(off + (size_t)NB * 4);
         L->order = off;
         off = align256(off + (size_t)NB * 4);
+        if (p->faces_per_pixel > 16) {
+            // the streaming pass's queue: one entry per 8 x 4 block at most
+            L->redo_items = off;
+            off = align256(off + (size_t)NB * (size_t)(p->bin_size * p->bin_size / 32) * 8);
+        }
         L->lists = off;
         off = align256(off + (size_t)cap * 8);
     }
@@ -240,6 +247,9 @@ static int forward(const rast_params *p, const float *verts, int64_t V, const in
     ka.order = order;
     ka.queue = reinterpret_cast<unsigned *>(ws + L.queue);
     ka.redo_count = reinterpret_cast<unsigned *>(ws + L.redo);
+    ka.redo_q = reinterpret_cast<unsigned *>(ws + L.redo_q);
+    ka.redo_head = reinterpret_cast<unsigned *>(ws + L.redo_head);
+    ka.redo_items = L.redo_items ? reinterpret_cast<unsigned long long *>(ws + L.redo_items) : nullptr;
     ka.items = (int)L.NB;
     ka.nb = (int)L.nb;
     ka.S = (int)S;

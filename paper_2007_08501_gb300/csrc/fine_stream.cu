@@ -12,14 +12,15 @@
 // whose bound is b, every candidate it holds with depth < b keeps its rank
 // for good: no later face can come before it.  Such entries leave the pixel's
 // list at once, written to their final slot, and only the still-unsettled
-// candidates stay on chip, in a ring of kRing entries per pixel in shared
+// candidates stay on chip, in a ring of kRing1 entries per pixel in shared
 // memory (the settled prefix is a counter).
 //
-// A pixel whose unsettled candidates outgrow the ring (rare: dense, steeply
-// tilted depth overlap) is redone at the end of the bin by a whole warp: the
-// warp walks the bin's sorted list 32 faces at a time and keeps the pixel's K
-// nearest in registers spread over its lanes (two list rows of 32), inserting
-// each admitted face with a ballot (its rank) and lane shuffles (the shift).
+// A pixel whose unsettled candidates outgrow the ring (rare on smooth meshes;
+// common on strongly deformed ones, whose tilted faces lie far behind their
+// nearest corner) is queued with its 8 x 4 block; a second pass walks the
+// queued blocks again for those pixels only, with a ring of 64 entries, more
+// than K, which cannot overflow.  Its shared memory (64 KB per block of 4
+// warps) is paid only by the blocks that need it.
 //
 // The fine pass writes each slot as one 64-bit key: (depth bits << 32) | face
 // id, or -1 for an empty slot, into pix_to_face.  k_frag_attr, one warp per
@@ -37,105 +38,12 @@
 
 namespace mr {
 
-constexpr int kRing = 16;  // unsettled candidates a pixel keeps on chip
+// unsettled candidates a pixel keeps on chip: first pass, second pass (>= K)
+constexpr int kRing1 = 16, kRing2 = 64;
+constexpr int kWarps1 = 8, kWarps2 = 4;  // warps per block of each pass
 
 __device__ __forceinline__ long long pack_key(float z, int f) {
     return (long long)(((unsigned long long)__float_as_uint(z) << 32) | (unsigned)f);
-}
-
-// ---------------------------------------------------------------------------
-// redo of one pixel by a warp: warp-distributed sorted K-list (K <= 64),
-// entry i in row i / 32 of lane i % 32
-// ---------------------------------------------------------------------------
-struct WarpList {
-    float z0, z1;
-    int f0, f1;
-    int m;  // entries held (<= K)
-};
-
-__device__ __forceinline__ void warp_list_insert(WarpList &L, float z, int f, int K) {
-    const int lane = (int)(threadIdx.x & 31u);
-    const unsigned b0 = __ballot_sync(0xffffffffu, key_less(L.z0, L.f0, z, f));
-    const unsigned b1 = __ballot_sync(0xffffffffu, key_less(L.z1, L.f1, z, f));
-    const int rank = __popc(b0) + __popc(b1);   // empty entries (+inf, INT_MAX) never count
-    // entry i of the new list: i < rank the old i, i == rank the new one, i > rank the old i - 1
-    const float pz0 = __shfl_up_sync(0xffffffffu, L.z0, 1), pz1 = __shfl_up_sync(0xffffffffu, L.z1, 1);
-    const int pf0 = __shfl_up_sync(0xffffffffu, L.f0, 1), pf1 = __shfl_up_sync(0xffffffffu, L.f1, 1);
-    const float cz = __shfl_sync(0xffffffffu, L.z0, 31);   // old entry 31 moves to entry 32
-    const int cf = __shfl_sync(0xffffffffu, L.f0, 31);
-    const int i0 = lane, i1 = 32 + lane;
-    if (i0 == rank) { L.z0 = z; L.f0 = f; }
-    else if (i0 > rank) { L.z0 = pz0; L.f0 = pf0; }
-    if (i1 == rank) { L.z1 = z; L.f1 = f; }
-    else if (i1 > rank) { L.z1 = lane == 0 ? cz : pz1; L.f1 = lane == 0 ? cf : pf1; }
-    const float kInf = __int_as_float(0x7f800000);
-    if (i0 >= K) { L.z0 = kInf; L.f0 = 0x7fffffff; }
-    if (i1 >= K) { L.z1 = kInf; L.f1 = 0x7fffffff; }
-    L.m = min(L.m + 1, K);
-}
-
-// K-th entry of the list (valid when m == K)
-__device__ __forceinline__ void warp_list_kth(const WarpList &L, int K, float &z, int &f) {
-    const int i = K - 1;
-    const float a = __shfl_sync(0xffffffffu, L.z0, i & 31), b = __shfl_sync(0xffffffffu, L.z1, i & 31);
-    const int fa = __shfl_sync(0xffffffffu, L.f0, i & 31), fb = __shfl_sync(0xffffffffu, L.f1, i & 31);
-    z = i < 32 ? a : b;
-    f = i < 32 ? fa : fb;
-}
-
-__device__ void redo_pixel(const FineArgs &a, const unsigned long long *ent, int cnt, int n, int r, int c,
-                           const EvalFlags &fl) {
-    const unsigned lane = threadIdx.x & 31u;
-    const int K = a.K;
-    const PixC p = pixel_centre(r, c, a.S);
-    const float kInf = __int_as_float(0x7f800000);
-    WarpList L{kInf, kInf, 0x7fffffff, 0x7fffffff, 0};
-    for (int jb = 0; jb < cnt; jb += 32) {
-        // every later face's depth is at least its key: stop once the K-th is in front
-        if (L.m >= K) {
-            float kz;
-            int kf;
-            warp_list_kth(L, K, kz, kf);
-            if (__uint_as_float((unsigned)(ent[jb] >> 32)) > kz) break;
-        }
-        const int j = jb + (int)lane;
-        bool hit = false;
-        float z = 0.f;
-        int fid = 0;
-        if (j < cnt) {
-            const unsigned long long v = ent[j];
-            fid = (int)(unsigned)(v & 0xffffffffull);
-            const float4 *src = reinterpret_cast<const float4 *>(a.rec + fid);
-            FaceRec R;
-            R.c = __ldg(src + kRecC);
-            if (in_bbox(R, p)) {
-                R.a = __ldg(src + kRecA);
-                R.b = __ldg(src + kRecB);
-                R.d = __ldg(src + kRecD);
-                R.e = __ldg(src + kRecE);
-                R.h = __ldg(src + kRecH);
-                hit = face_key_nobbox(R, p, fl, z);
-            }
-        }
-        unsigned mask = __ballot_sync(0xffffffffu, hit);
-        while (mask) {
-            const int src = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const float zz = __shfl_sync(0xffffffffu, z, src);
-            const int ff = __shfl_sync(0xffffffffu, fid, src);
-            bool admit = L.m < K;
-            if (!admit) {
-                float kz;
-                int kf;
-                warp_list_kth(L, K, kz, kf);
-                admit = key_less(zz, ff, kz, kf);
-            }
-            if (admit) warp_list_insert(L, zz, ff, K);
-        }
-    }
-    const int64_t s0 = (((int64_t)n * a.S + r) * a.S + c) * K;
-    if ((int)lane < K) a.out.pix_to_face[s0 + lane] = (int)lane < L.m ? pack_key(L.z0, L.f0) : -1ll;
-    if (32 + (int)lane < K) a.out.pix_to_face[s0 + 32 + lane] = 32 + (int)lane < L.m ? pack_key(L.z1, L.f1) : -1ll;
 }
 
 // ---------------------------------------------------------------------------
@@ -162,7 +70,6 @@ __global__ void __launch_bounds__(256) k_sort_bins(FineArgs a) {
 // against); the warp walks the bin's sorted list from L2 32 entries at a
 // time, each lane keeping its pixel's unsettled candidates in its own ring.
 // ---------------------------------------------------------------------------
-constexpr int kWarpsPerBlock = 8;
 
 // Whether no point of the rectangle [x0, x1] x [y0, y1] can be within
 // sqrt(blur) of the face: the whole rectangle lies beyond the line of one of
@@ -190,25 +97,42 @@ __device__ __forceinline__ bool rect_beyond_edge(const float4 &ra, const float4 
     return out && sliver <= 64.f;
 }
 
-template <int BS>
-__global__ void __launch_bounds__(256, 4) k_fine_stream(FineArgs a) {
+// First pass (SECOND = false): every item, a ring of RING = 16 per pixel,
+// WARPS = 8 warps per block.  Pixels whose unsettled candidates outgrow it are
+// queued, per item, as a lane mask.  Second pass (SECOND = true): the queued
+// items again, only their queued lanes, with a ring of RING = 64 >= K, which
+// cannot overflow (a pixel never holds more than K - settled candidates).
+template <int BS, int RING, int WARPS, bool SECOND>
+__global__ void __launch_bounds__(WARPS * 32, SECOND ? 3 : 4) k_fine_stream(FineArgs a) {
     constexpr int SUB = BS * BS / 32;  // 8 x 4 pixel blocks per bin
-    // per warp: the rings ([slot][lane])
-    __shared__ float s_rz[kWarpsPerBlock][kRing][32];
-    __shared__ int s_rf[kWarpsPerBlock][kRing][32];
+    // per warp: the rings ([slot][lane]), depths then face ids
+    extern __shared__ float s_ring[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    float (*rz)[32] = s_rz[wib];
-    int (*rf)[32] = s_rf[wib];
+    float (*rz)[32] = reinterpret_cast<float (*)[32]>(s_ring + (size_t)wib * RING * 32);
+    int (*rf)[32] = reinterpret_cast<int (*)[32]>(s_ring + (size_t)(WARPS + wib) * RING * 32);
     EvalFlags fl = a.fl;
     const int nb2 = a.nb * a.nb;
     const int K = a.K;
-    const long long total = (long long)a.items * SUB;
+    const long long total = SECOND ? 0ll : (long long)a.items * SUB;
     const float kInf = __int_as_float(0x7f800000);
     while (true) {
         long long item = 0;
-        if (lane == 0) item = (long long)atomicAdd(a.queue, 1u);
-        item = __shfl_sync(0xffffffffu, item, 0);
-        if (item >= total) break;
+        unsigned lanes = 0xffffffffu;  // the lanes this pass takes
+        if constexpr (SECOND) {
+            unsigned long long e = 0ull;
+            if (lane == 0) {
+                const unsigned j = atomicAdd(a.redo_head, 1u);
+                e = j < *a.redo_q ? a.redo_items[j] : ~0ull;
+            }
+            e = __shfl_sync(0xffffffffu, e, 0);
+            if (e == ~0ull) break;
+            item = (long long)(e >> 32);
+            lanes = (unsigned)e;
+        } else {
+            if (lane == 0) item = (long long)atomicAdd(a.queue, 1u);
+            item = __shfl_sync(0xffffffffu, item, 0);
+            if (item >= total) break;
+        }
         const int qb = (int)(item / SUB), sub = (int)(item - (long long)qb * SUB);
         const int bin = a.order ? __ldg(a.order + qb) : qb;  // longest bins first
         const int n = bin / nb2, rem = bin - n * nb2;
@@ -216,7 +140,7 @@ __global__ void __launch_bounds__(256, 4) k_fine_stream(FineArgs a) {
         const int r = by * BS + (sub / (BS / 8)) * 4 + (lane >> 3);
         const int c = bx * BS + (sub % (BS / 8)) * 8 + (lane & 7);
         fl.znear = __ldg(a.cams + 16 * n + 13);
-        const bool valid = (r < a.S) && (c < a.S);
+        const bool valid = (r < a.S) && (c < a.S) && ((lanes >> lane) & 1u);
         const PixC p = pixel_centre(r, c, a.S);
         float wx0 = 1.f, wx1 = -1.f, wy0 = 1.f, wy1 = -1.f;
         {
@@ -293,7 +217,7 @@ __global__ void __launch_bounds__(256, 4) k_fine_stream(FineArgs a) {
                 if (full && !key_less(z, f, kth_z, kth_f)) continue;
                 // entries in front of this face's key are settled: no later face precedes them
                 while (nr > 0) {
-                    const int h = head & (kRing - 1);
+                    const int h = head & (RING - 1);
                     const float fz = rz[h][lane];
                     if (!(fz < fkey)) break;
                     settle(fz, rf[h][lane]);
@@ -301,27 +225,27 @@ __global__ void __launch_bounds__(256, 4) k_fine_stream(FineArgs a) {
                     --nr;
                 }
                 if (full) --nr;             // the K-th entry is displaced (nr >= 1: not done)
-                if (nr == kRing) {          // no room: this pixel is redone by the warp
+                if (nr == RING) {           // no room: this pixel goes to the second pass
                     redo = true;
                     continue;
                 }
                 int pos = nr;               // insertion from the tail (arrivals are nearly sorted)
                 while (pos > 0) {
-                    const int hp = (head + pos - 1) & (kRing - 1);
+                    const int hp = (head + pos - 1) & (RING - 1);
                     const float pz = rz[hp][lane];
                     const int pf = rf[hp][lane];
                     if (!key_less(z, f, pz, pf)) break;
-                    const int hq = (head + pos) & (kRing - 1);
+                    const int hq = (head + pos) & (RING - 1);
                     rz[hq][lane] = pz;
                     rf[hq][lane] = pf;
                     --pos;
                 }
-                const int hq = (head + pos) & (kRing - 1);
+                const int hq = (head + pos) & (RING - 1);
                 rz[hq][lane] = z;
                 rf[hq][lane] = f;
                 ++nr;
                 if (nfin + nr >= K) {
-                    const int hl = (head + nr - 1) & (kRing - 1);
+                    const int hl = (head + nr - 1) & (RING - 1);
                     kth_z = rz[hl][lane];
                     kth_f = rf[hl][lane];
                 }
@@ -330,21 +254,21 @@ __global__ void __launch_bounds__(256, 4) k_fine_stream(FineArgs a) {
         // everything left in the ring is settled; empty slots get -1
         if (valid && !redo) {
             while (nr > 0) {
-                const int h = head & (kRing - 1);
+                const int h = head & (RING - 1);
                 settle(rz[h][lane], rf[h][lane]);
                 ++head;
                 --nr;
             }
             for (int k = nfin; k < K; ++k) a.out.pix_to_face[s0 + k] = -1ll;
         }
-        // pixels whose unsettled candidates outgrew the ring: the whole warp redoes each
-        unsigned todo = __ballot_sync(0xffffffffu, valid && redo);
-        if (todo && lane == 0) atomicAdd(a.redo_count, (unsigned)__popc(todo));
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int rr = __shfl_sync(0xffffffffu, r, src), cc = __shfl_sync(0xffffffffu, c, src);
-            redo_pixel(a, ent, cnt, n, rr, cc, fl);
+        // pixels whose unsettled candidates outgrew the ring: queued for the
+        // second pass (each item at most once, so the queue never fills)
+        if constexpr (!SECOND) {
+            const unsigned todo = __ballot_sync(0xffffffffu, valid && redo);
+            if (todo && lane == 0) {
+                atomicAdd(a.redo_count, (unsigned)__popc(todo));
+                a.redo_items[atomicAdd(a.redo_q, 1u)] = ((unsigned long long)item << 32) | todo;
+            }
         }
     }
 }
@@ -449,14 +373,32 @@ static cudaError_t launch_sort_bins(const FineArgs &a, cudaStream_t st) {
 
 template <int BS>
 static cudaError_t launch_fine_stream_t(const FineArgs &a, cudaStream_t st) {
-    auto kern = k_fine_stream<BS>;
-    int bps = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, 256, 0);
+    // first pass: every 8 x 4 block of every bin
+    {
+        auto kern = k_fine_stream<BS, kRing1, kWarps1, false>;
+        const size_t dyn = (size_t)2 * kWarps1 * kRing1 * 32 * sizeof(float);  // 32 KB
+        int bps = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kWarps1 * 32, dyn);
+        if (e != cudaSuccess) return e;
+        const long long warps = (long long)a.items * (BS * BS / 32);
+        const long long need = (warps + kWarps1 - 1) / kWarps1;
+        const int grid =
+            (int)std::max(1LL, std::min<long long>(need, (long long)mr_host::num_sms() * std::max(1, bps)));
+        kern<<<grid, kWarps1 * 32, dyn, st>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // second pass: the queued blocks (their count is on the device; warps stop
+    // at the end of the queue)
+    auto kern = k_fine_stream<BS, kRing2, kWarps2, true>;
+    const size_t dyn = (size_t)2 * kWarps2 * kRing2 * 32 * sizeof(float);  // 64 KB
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
-    const long long warps = (long long)a.items * (BS * BS / 32);
-    const long long need = (warps + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    int bps = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kWarps2 * 32, dyn);
+    if (e != cudaSuccess) return e;
+    const long long need = ((long long)a.items * (BS * BS / 32) + kWarps2 - 1) / kWarps2;
     const int grid = (int)std::max(1LL, std::min<long long>(need, (long long)mr_host::num_sms() * std::max(1, bps)));
-    kern<<<grid, 256, 0, st>>>(a);
+    kern<<<grid, kWarps2 * 32, dyn, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -492,7 +492,10 @@ struct WsLayout {
     size_t queue;       // uint32 work-queue head of the fine pass
     size_t total;       // int64 sum of raw bin counts
     size_t maxcount;    // int32 largest raw bin count
-    size_t redo;        // uint32 pixels the large-K streaming fine pass redid with a whole warp
+    size_t redo;        // uint32 pixels the large-K streaming fine pass handed to its second pass
+    size_t redo_q;      // uint32 blocks queued for that second pass
+    size_t redo_head;   // uint32 the second pass's position in its queue
+    size_t redo_items;  // (K > 16) uint64 per 8 x 4 pixel block of every bin: the queue
     size_t records;     // F x FaceRec
     size_t face_mesh;   // F x int32
     size_t counts;      // NB x int32 raw counts

@@ -75,7 +75,10 @@ struct FineArgs {
     const int *eff, *offsets;
     const int *order;           // queue position -> bin (bins by descending work class)
     unsigned *queue;
-    unsigned *redo_count;       // large-K streaming pass: pixels redone by a whole warp
+    unsigned *redo_count;       // large-K streaming pass: pixels handed to its second pass
+    unsigned *redo_q;           // queued 8 x 4 blocks (item << 32 | lane mask) and their count,
+    unsigned long long *redo_items;  //   written by the first pass
+    unsigned *redo_head;        // the second pass's position in that queue
     int items, nb, S, K;
     int sort_cap;  // bin entries sorted at a time (power of two)
     EvalFlags fl;

@@ -96,11 +96,12 @@ def test_streaming_pass_equals_the_block_fine_pass_at_full_size():
     assert (outs[0][0][..., w.K - 1] >= 0).float().mean() > 0.3   # most pixels hold K faces
 
 
-def test_large_k_ring_overflow_is_redone_by_a_warp():
+def test_large_k_ring_overflow_goes_to_the_second_pass():
     """30 faces tilted away from the camera: each has one corner at depth 1 (its
     sort key), while at the pixels near its far edge its depth is ~5.  No
     candidate settles before the bin's list ends, so more than the 16 a pixel
-    keeps on chip are unsettled at once: those pixels are redone by a warp."""
+    keeps on chip in the first pass are unsettled at once: those pixels are
+    queued and done by the second pass (a 64-entry ring)."""
     from _scenes import ndc_triangle, scene
     tris = [ndc_triangle((-0.6 + 0.002 * i, -0.6), (0.6, -0.6 + 0.001 * i), (0.0, 0.9), (5.0 + 0.01 * i, 5.0, 1.0))
             for i in range(30)]
@@ -111,7 +112,7 @@ def test_large_k_ring_overflow_is_redone_by_a_warp():
     assert status == 0
     L = ops.rast_workspace_bin_layout(p, d["verts"].shape[0], d["faces"].shape[0])
     redo = int(ws[L["redo"]:L["redo"] + 4].cpu().numpy().view(np.uint32)[0])
-    print("pixels redone by a warp: %d" % redo)
+    print("pixels handed to the second pass: %d" % redo)
     assert redo > 0
     m = oracle_mesh(sc)
     orc = oracle.rasterize(m, S, K, BLUR, True, True)
