@@ -18,13 +18,13 @@
 // A pixel whose unsettled candidates outgrow the ring (rare on smooth meshes;
 // common on strongly deformed ones, whose tilted faces lie far behind their
 // nearest corner) is queued with its 8 x 4 block; a second pass walks the
-// queued blocks again for those pixels only, with a ring of 64 entries, more
-// than K, which cannot overflow.  Its shared memory (64 KB per block of 4
+// queued blocks again for those pixels only, with a ring of 64 entries, at
+// least K, which cannot overflow.  Its shared memory (64 KB per block of 4
 // warps) is paid only by the blocks that need it.
 //
 // The fine pass writes each slot as one 64-bit key: (depth bits << 32) | face
-// id, or -1 for an empty slot, into pix_to_face.  k_frag_attr, one warp per
-// pixel and one lane per slot (coalesced, full occupancy), expands it into
+// id, or -1 for an empty slot, into pix_to_face.  k_frag_attr, one thread per
+// slot (consecutive slots on consecutive threads: coalesced), expands it into
 // pix_to_face, zbuf, barycentrics and distance, and applies the silhouette
 // blend (Algorithm 1) when asked.
 #include <cuda_runtime.h>
