@@ -108,7 +108,8 @@ __device__ __forceinline__ void scatter_face_dist(const RastBwdArgs &r, int key,
 template <bool RGB, int NA>
 __device__ __forceinline__ void slot_tail(const BlendArgs &a, const RastBwdArgs &r, const PixC &p, int f, float gz,
                                           float gd, float gb0, float gb1, float gb2, const int64_t vi[3],
-                                          float (&acc)[NA], RareQueue rq = RareQueue{nullptr, nullptr}) {
+                                          float (&acc)[NA], RareQueue rq = RareQueue{nullptr, nullptr},
+                                          int tile = 0) {
     const int fr = (f >= 0 && (int64_t)f < r.F) ? f : -1;  // an id outside the batch contributes nothing
     const int nf = fr >= 0 ? __ldg(r.face_mesh + fr) : -1;
     const bool live = nf >= 0 && (gz != 0.f || gd != 0.f || gb0 != 0.f || gb1 != 0.f || gb2 != 0.f);
@@ -131,7 +132,7 @@ __device__ __forceinline__ void slot_tail(const BlendArgs &a, const RastBwdArgs 
         for (int j = 0; j < 9; ++j) g9[j] = 0.f;
         if (live) {
             load_adjoint_rec(r.rec, fr, R);
-            slot_corner_grads(R, p, r.fl, gz, gd, gb0, gb1, gb2, g9, rq, fr, nf);
+            slot_corner_grads(R, p, r.fl, gz, gd, gb0, gb1, gb2, g9, rq, fr, nf, tile);
         }
 #pragma unroll
         for (int j = 0; j < 9; ++j) acc[j] = g9[j];
@@ -159,7 +160,9 @@ constexpr int fused_min_blocks(int km, bool rgb) { return rgb ? (km >= 16 ? 2 : 
 template <int KM, bool RGB>
 __global__ void __launch_bounds__(256, fused_min_blocks(KM, RGB)) k_blend_rast_bwd(BlendArgs a, RastBwdArgs r) {
     constexpr int NA = RGB ? 18 : 6;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    // each warp covers an 8 x 4 block of the 16 x 16 tile: neighbouring pixels
+    // share faces, so the warp's grouping by face finds more peers
+    const int tx = ((threadIdx.x >> 5) & 1) * 8 + (threadIdx.x & 7), ty = (threadIdx.x >> 6) * 4 + ((threadIdx.x >> 3) & 3);
     const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
     const bool valid = row < a.S && col < a.S;
     const int64_t pix = ((int64_t)blockIdx.z * a.S + row) * a.S + col;
@@ -287,7 +290,7 @@ __global__ void __launch_bounds__(256, fused_min_blocks(KM, RGB)) k_blend_rast_b
                 }
             }
         }
-        slot_tail<RGB, NA>(a, r, p, f, gz, gd, gb[0], gb[1], gb[2], vi, acc, rq);
+        slot_tail<RGB, NA>(a, r, p, f, gz, gd, gb[0], gb[1], gb[2], vi, acc, rq, (ty << 4) | tx);
     }
     if constexpr (RGB) flush_rare_slots(rq, r.rec, r.cams, r.faces, r.grad_verts, a.S, r.fl);
 }
@@ -298,7 +301,9 @@ __global__ void __launch_bounds__(256, fused_min_blocks(KM, RGB)) k_blend_rast_b
 template <bool RGB>
 __global__ void __launch_bounds__(256) k_blend_rast_bwd_any(BlendArgs a, RastBwdArgs r) {
     constexpr int NA = RGB ? 18 : 6;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    // each warp covers an 8 x 4 block of the 16 x 16 tile: neighbouring pixels
+    // share faces, so the warp's grouping by face finds more peers
+    const int tx = ((threadIdx.x >> 5) & 1) * 8 + (threadIdx.x & 7), ty = (threadIdx.x >> 6) * 4 + ((threadIdx.x >> 3) & 3);
     const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
     const bool valid = row < a.S && col < a.S;
     const int64_t pix = ((int64_t)blockIdx.z * a.S + row) * a.S + col;
@@ -408,7 +413,7 @@ __global__ void __launch_bounds__(256) k_blend_rast_bwd_any(BlendArgs a, RastBwd
                 }
             }
         }
-        slot_tail<RGB, NA>(a, r, p, f, gz, gd, gb[0], gb[1], gb[2], vi, acc, rq);
+        slot_tail<RGB, NA>(a, r, p, f, gz, gd, gb[0], gb[1], gb[2], vi, acc, rq, (ty << 4) | tx);
     }
     if constexpr (RGB) flush_rare_slots(rq, r.rec, r.cams, r.faces, r.grad_verts, a.S, r.fl);
 }

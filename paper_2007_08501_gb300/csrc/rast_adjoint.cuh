@@ -241,7 +241,7 @@ static __device__ __noinline__ void bary_adjoint_df(const FaceRec &R, const PixC
 // its warp for the whole double-float evaluation.
 constexpr int kRareCap = 256;   // ~1 % of a 16 x 16 tile's slots need it at K = 8
 struct RareSlot {
-    int f, nf, tid;        // face, its image, the thread (pixel of the block's tile) of the slot
+    int f, nf, tile;       // face, its image, the slot's pixel in the block's 16 x 16 tile (row << 4 | column)
     float gz, gb0, gb1, gb2;
 };
 struct RareQueue {
@@ -282,7 +282,7 @@ __device__ __forceinline__ void flush_rare_slots(const RareQueue &q, const FaceR
     const int cnt = min(*q.n, kRareCap);
     for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
         const RareSlot e = q.e[i];
-        const int r = blockIdx.y * 16 + (e.tid >> 4), c = blockIdx.x * 16 + (e.tid & 15);
+        const int r = blockIdx.y * 16 + (e.tile >> 4), c = blockIdx.x * 16 + (e.tile & 15);
         const PixC p = pixel_centre(r, c, S);
         FaceRec R;
         const float4 *src = reinterpret_cast<const float4 *>(rec + e.f);
@@ -312,7 +312,8 @@ __device__ __forceinline__ void flush_rare_slots(const RareQueue &q, const FaceR
 // there is room; without one it is evaluated in fp32.
 __device__ __forceinline__ void slot_corner_grads(const FaceRec &R, const PixC &p, const EvalFlags &fl, float gz,
                                                   float gd, float gbp0, float gbp1, float gbp2, float (&g)[9],
-                                                  RareQueue q = RareQueue{nullptr, nullptr}, int f = 0, int nf = 0) {
+                                                  RareQueue q = RareQueue{nullptr, nullptr}, int f = 0, int nf = 0,
+                                                  int tile = 0) {
     float qx, qy;
     local_q(R, p, qx, qy);
     float b[3];
@@ -334,7 +335,7 @@ __device__ __forceinline__ void slot_corner_grads(const FaceRec &R, const PixC &
         // formula, at fp32 accuracy)
         const int i = (sliver > 64.f && bmax > 8.f && q.e) ? atomicAdd(q.n, 1) : kRareCap;
         if (i < kRareCap) {
-            q.e[i] = RareSlot{f, nf, (int)threadIdx.x, gz, gbp0, gbp1, gbp2};
+            q.e[i] = RareSlot{f, nf, tile, gz, gbp0, gbp1, gbp2};
         } else {
             // near a clip kink the forward's clamped component has the sign of
             // the double-float barycentrics: take those

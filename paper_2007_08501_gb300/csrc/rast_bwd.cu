@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(256) k_rast_bwd(RastBwdArgs a) {
                 gb2 = a.grad_bary[3 * s + 2];
             }
             if (gz != 0.f || gd != 0.f || gb0 != 0.f || gb1 != 0.f || gb2 != 0.f)
-                slot_corner_grads(R, p, a.fl, gz, gd, gb0, gb1, gb2, g, rq, (int)f, nf);
+                slot_corner_grads(R, p, a.fl, gz, gd, gb0, gb1, gb2, g, rq, (int)f, nf, (ty << 4) | tx);
             else
                 f = -1;
         }
