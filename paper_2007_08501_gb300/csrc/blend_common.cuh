@@ -137,7 +137,8 @@ struct FwdBlend {
 
 // pixel of a thread in the 16 x 16 tiled launch used by the backward kernels
 __device__ __forceinline__ bool tile_pixel(const BlendArgs &a, int64_t &pix) {
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    // each warp covers an 8 x 4 block of the 16 x 16 tile
+    const int tx = ((threadIdx.x >> 5) & 1) * 8 + (threadIdx.x & 7), ty = (threadIdx.x >> 6) * 4 + ((threadIdx.x >> 3) & 3);
     const int r = blockIdx.y * 16 + ty, c = blockIdx.x * 16 + tx;
     pix = ((int64_t)blockIdx.z * a.S + r) * a.S + c;
     return r < a.S && c < a.S;

@@ -20,7 +20,9 @@ namespace mr {
 // gradients of lanes that hold the same face, and one lane per face applies
 // the projection Jacobian and R^T and issues the atomics.
 __global__ void __launch_bounds__(256) k_rast_bwd(RastBwdArgs a) {
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    // each warp covers an 8 x 4 block of the 16 x 16 tile: neighbouring pixels
+    // share faces, so the warp's grouping by face finds more peers
+    const int tx = ((threadIdx.x >> 5) & 1) * 8 + (threadIdx.x & 7), ty = (threadIdx.x >> 6) * 4 + ((threadIdx.x >> 3) & 3);
     const int n = blockIdx.z;
     const int r = blockIdx.y * 16 + ty, c = blockIdx.x * 16 + tx;
     const bool valid = (r < a.S) && (c < a.S);
