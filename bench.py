@@ -95,13 +95,13 @@ def mesh_kernels_per_step(w):
 # views.
 TRAFFIC_BYTES = {
     ("1", "fwd", 16): {"kernel": "rast_blend_fwd call: k_stage + k_scan + k_fill + k_fine<8,16,0> + k_blend_fwd<8>",
-                       "bytes": 142300000, "profile": "profiles/launch_list_8x5120faces_256px_K8.md"},
-    ("1", "bwd", 16): {"kernel": "blend_rast_bwd call: k_stage + k_blend_rast_bwd<8,1>", "bytes": 106000000,
+                       "bytes": 141800000, "profile": "profiles/launch_list_8x5120faces_256px_K8.md"},
+    ("1", "bwd", 16): {"kernel": "blend_rast_bwd call: k_stage + k_blend_rast_bwd<8,1>", "bytes": 106100000,
                        "profile": "profiles/launch_list_8x5120faces_256px_K8.md"},
     ("4", "fwd", 16): {"kernel": "rast_blend_fwd call: k_stage + k_scan + k_fill + k_sort_bins + "
-                                 "k_fine_stream<16,16,8,0> + k_fine_stream<16,64,4,1> + k_frag_attr<1>", "bytes": 11631000000,
+                                 "k_fine_stream<16,16,8,0> + k_fine_stream<16,64,4,1> + k_frag_attr<1>", "bytes": 11634000000,
                        "profile": "profiles/launch_list_20x81920faces_512px_K50.md (2 views x 10)"},
-    ("4", "bwd", 16): {"kernel": "blend_rast_bwd call: k_stage + k_blend_rast_bwd_any<0>", "bytes": 4227000000,
+    ("4", "bwd", 16): {"kernel": "blend_rast_bwd call: k_stage + k_blend_rast_bwd_any<0>", "bytes": 4209000000,
                        "profile": "profiles/launch_list_20x81920faces_512px_K50.md (2 views x 10)"},
     ("points", "rast_fwd", 8): {"kernel": "pts_rasterize_fwd call: k_pstage + k_scan + k_pfill + k_pfine<0,8>",
                                 "bytes": 552453578, "profile": "profiles/points_8x200000pts_256px_K50.md"},
