@@ -548,7 +548,9 @@ __global__ void __launch_bounds__(256) k_pcomp_bwd(CompArgs a) {
 // gradient needs no double-float positions), so no staging pass is needed.
 __global__ void __launch_bounds__(256) k_prast_bwd(PtArgs a, const float *grad_zbuf, const float *grad_dists,
                                                  float *grad_points) {
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    // each warp covers an 8 x 4 block of the 16 x 16 tile: neighbouring pixels
+    // share points, so the warp's grouping by point finds more peers
+    const int tx = ((threadIdx.x >> 5) & 1) * 8 + (threadIdx.x & 7), ty = (threadIdx.x >> 6) * 4 + ((threadIdx.x >> 3) & 3);
     const int n = blockIdx.z;
     const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
     const bool valid = row < a.S && col < a.S;

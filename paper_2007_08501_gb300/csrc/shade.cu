@@ -235,7 +235,9 @@ __device__ __forceinline__ void scatter_corners(const ShadeArgs &s, int key, con
 // One thread per pixel of a 16 x 16 tile.  The K shaded colours and weights
 // live in local arrays (K <= 64).
 __global__ void __launch_bounds__(256) k_shade_bwd(ShadeArgs s) {
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    // each warp covers an 8 x 4 block of the 16 x 16 tile: neighbouring pixels
+    // share faces, so the warp's grouping by face finds more peers
+    const int tx = ((threadIdx.x >> 5) & 1) * 8 + (threadIdx.x & 7), ty = (threadIdx.x >> 6) * 4 + ((threadIdx.x >> 3) & 3);
     const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
     const bool valid = row < s.S && col < s.S;
     const int n = blockIdx.z;
