@@ -80,13 +80,6 @@ __device__ __forceinline__ void st_keep(longlong2 *p, longlong2 v, unsigned long
                  : "memory");
 }
 
-// Start the reads of the first 64 bytes of face f's record (a, b, d, e) into
-// L1 ahead of their use: the loads that follow find them there.
-__device__ __forceinline__ void prefetch_rec(const FaceRec *rec, int f) {
-    const float4 *rp = reinterpret_cast<const float4 *>(rec + f);
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(rp + kRecA));
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(rp + kRecD));
-}
 
 // ---------------------------------------------------------------------------
 // double-float (unevaluated sum hi + lo) arithmetic, error-free transforms
