@@ -80,7 +80,6 @@ __device__ __forceinline__ void st_keep(longlong2 *p, longlong2 v, unsigned long
                  : "memory");
 }
 
-
 // ---------------------------------------------------------------------------
 // double-float (unevaluated sum hi + lo) arithmetic, error-free transforms
 // of Knuth (two-sum) and Dekker (two-product via fma).
